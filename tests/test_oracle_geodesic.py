@@ -1,0 +1,244 @@
+"""Pins of the CPU oracle's geodesic distances and tangents (no GPU).
+
+Each test checks the oracle against something fixed independently of its code:
+closed forms (flat, developable tube, cube unfoldings), the definitional
+brute-force solver on tiny meshes, metric invariants, the smooth-sphere limit
+and published Philox vectors.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import brute
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_philox_known_answers():
+    """Philox4x32-10 against the published known-answer vectors (Salmon et al., SC'11)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox4x32_10(v[0:4], v[4:6])
+        assert out.tolist() == v[6:10]
+
+
+def test_normals_moments():
+    z = np.array([O.normal_pair(7, i, 3) for i in range(20000)]).ravel()
+    assert abs(z.mean()) < 0.03 and abs(z.std() - 1.0) < 0.03
+    assert O.normal_pair(7, 1, 3) != O.normal_pair(7, 1, 4)
+
+
+def test_flat_plane_is_euclidean():
+    """Open flat convex mesh: geodesic = straight segment, tangent = unit chord (Sec. 2.1)."""
+    cfg = synth.make_config("flat64")
+    m, face, bary = cfg["mesh"], cfg["face"], cfg["bary"]
+    om = O.OracleMesh(m)
+    x = synth.particles.world_positions(m, face, bary)
+    rs, j, d, t = om.neighbors(face, bary, math.inf)
+    assert rs[-1] == 64 * 63
+    for i in range(64):
+        jj = j[rs[i]:rs[i + 1]]
+        dx = x[jj] - x[i]
+        e = np.linalg.norm(dx, axis=1)
+        np.testing.assert_allclose(d[rs[i]:rs[i + 1]], e, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(t[rs[i]:rs[i + 1]], dx / e[:, None], atol=1e-12)
+
+
+def _tube_coords(m, x):
+    n = m.meta["n_around"]
+    rho = m.meta["radius"]
+    side = 2 * rho * math.sin(math.pi / n)
+    phi = np.mod(np.arctan2(x[:, 1], x[:, 0]), 2 * np.pi)
+    i = np.minimum(np.floor(phi / (2 * np.pi / n)).astype(int), n - 1)
+    a0 = 2 * np.pi * i / n
+    a1 = 2 * np.pi * (i + 1) / n
+    v0 = np.stack([rho * np.cos(a0), rho * np.sin(a0)], 1)
+    v1 = np.stack([rho * np.cos(a1), rho * np.sin(a1)], 1)
+    t = np.linalg.norm(x[:, :2] - v0, axis=1) / side
+    e = (v1 - v0) / side
+    return (i + t) * side, x[:, 2], n * side, np.concatenate([e, np.zeros((len(x), 1))], 1)
+
+
+def test_tube_is_unrolled_with_wraps():
+    """Developable open prism tube: d = min_k |(du + k P, dz)| in the unrolled strip."""
+    m = synth.cylinder_tube(9, 5, 1.0, 2.5)
+    om = O.OracleMesh(m)
+    face, bary = synth.place_uniform(m, 40, 11)
+    x = synth.particles.world_positions(m, face, bary)
+    u, z, P, eside = _tube_coords(m, x)
+    rs, j, d, t = om.neighbors(face, bary, math.inf)
+    for i in range(len(face)):
+        jj = j[rs[i]:rs[i + 1]]
+        du = u[jj] - u[i]
+        cands = np.stack([np.hypot(du + k * P, z[jj] - z[i]) for k in (-1, 0, 1)], 1)
+        kbest = np.argmin(cands, 1)
+        np.testing.assert_allclose(d[rs[i]:rs[i + 1]], cands.min(1), rtol=1e-11)
+        srt = np.sort(cands, 1)
+        clear = srt[:, 1] - srt[:, 0] > 1e-6
+        dub = du + np.array([-1, 0, 1])[kbest] * P
+        tt = (dub[:, None] * eside[i] + (z[jj] - z[i])[:, None] * np.array([0, 0, 1.0])) / cands.min(1)[:, None]
+        np.testing.assert_allclose(t[rs[i]:rs[i + 1]][clear], tt[clear], atol=1e-9)
+
+
+def _locate(m, pt):
+    P = m.verts[m.faces]
+    for f in range(m.nf):
+        A, B, C = P[f]
+        n = np.cross(B - A, C - A)
+        n /= np.linalg.norm(n)
+        if abs(np.dot(pt - A, n)) > 1e-12:
+            continue
+        M = np.stack([B - A, C - A], 1)
+        l = np.linalg.lstsq(M, pt - A, rcond=None)[0]
+        b = np.array([1 - l.sum(), l[0], l[1]])
+        if b.min() > -1e-12:
+            return f, np.clip(b, 0, 1) / np.clip(b, 0, 1).sum()
+    raise ValueError(pt)
+
+
+def test_cube_unfoldings():
+    """Unit cube: lengths of explicit unfoldings; corners (angle sum 3 pi/2) are never crossed."""
+    m = synth.cube(2)
+    om = O.OracleMesh(m)
+    th, ps, bd = om.vertex_info()
+    corners = np.isclose(th, 1.5 * np.pi)
+    assert corners.sum() == 8 and not ps[corners].any() and ps[~corners].all()
+    src = np.array([0.5, 0.4, 1.0])
+    tg = {  # point: closed-form unfolded length
+        (0.5, 0.4, 0.0): 0.4 + 1.0 + 0.4,                 # over the y=0 side
+        (1.0, 0.5, 0.4): math.hypot(1.1, 0.1),            # top + x=1 side
+        (0.4, 0.0, 0.5): math.hypot(0.1, 0.9),            # top + y=0 side
+        (0.5, 0.5, 0.0): 2.0 - 0.1,                        # over y=0: 0.4 + 1 + 0.5
+    }
+    f0, b0 = _locate(m, src)
+    fb = [_locate(m, np.array(p)) for p in tg]
+    d, t = om.query(f0, b0, math.inf, [f for f, _ in fb], [b for _, b in fb])
+    np.testing.assert_allclose(d, list(tg.values()), rtol=1e-13)
+    # face centre to face centre: adjacent sides 1, opposite sides 2 (sources on vertices)
+    c_top, c_side, c_bot = (0.5, 0.5, 1.0), (1.0, 0.5, 0.5), (0.5, 0.5, 0.0)
+    f0, b0 = _locate(m, np.array(c_top))
+    fb = [_locate(m, np.array(c)) for c in (c_side, c_bot)]
+    d, _ = om.query(f0, b0, math.inf, [f for f, _ in fb], [b for _, b in fb])
+    np.testing.assert_allclose(d, [1.0, 2.0], rtol=1e-13)
+
+
+def test_periodic_flat_patch_is_minimum_image():
+    """Periodic flat square: geodesic = minimum-image Euclidean distance below half the period."""
+    m = synth.periodic_heightfield(24, 1, seed=0, A=(0.0, 0.0))
+    om = O.OracleMesh(m)
+    face, bary = synth.place_uniform(m, 30, 5)
+    x = synth.particles.world_positions(m, face, bary)
+    rs, j, d, t = om.neighbors(face, bary, 0.45)
+    n_checked = 0
+    for i in range(len(face)):
+        dx = x - x[i]
+        dx[:, :2] -= np.round(dx[:, :2])
+        e = np.linalg.norm(dx, axis=1)
+        want = np.where((e < 0.45) & (np.arange(len(face)) != i))[0]
+        assert list(j[rs[i]:rs[i + 1]]) == list(want)
+        np.testing.assert_allclose(d[rs[i]:rs[i + 1]], e[want], rtol=1e-12)
+        np.testing.assert_allclose(t[rs[i]:rs[i + 1]], dx[want] / e[want, None], atol=1e-11)
+        n_checked += len(want)
+    assert n_checked > 100
+
+
+TINY = [
+    ("tetra", lambda: synth.tetrahedron()),
+    ("octa", lambda: synth.octahedron()),
+    ("cube1", lambda: synth.cube(1)),
+    ("cube2", lambda: synth.cube(2)),
+    ("torus8x5", lambda: synth.torus(3, 1, 8, 5)),
+    ("noisy_ico1", lambda: synth.icosphere(1, 1.0, noise=0.15, seed=3)),
+    ("plane4", lambda: synth.grid_plane(4, 4, alternate=True)),
+    ("tube6x3", lambda: synth.cylinder_tube(6, 3, 1.0, 2.0)),
+]
+
+
+@pytest.mark.parametrize("name,make", TINY, ids=[t[0] for t in TINY])
+def test_window_propagation_matches_brute_force(name, make):
+    """O-mmp == definitional unfold-and-Dijkstra solver on tiny meshes (Sec. 2.2)."""
+    m = make()
+    om = O.OracleMesh(m)
+    n = 6
+    face, bary = synth.place_uniform(m, n, 0)
+    dmax = 1.5 * synth.bbox_diagonal(m)
+    for i in range(n):
+        db, tb = brute.geodesics(m, face[i], bary[i], list(zip(face, bary)), dmax)
+        do, to = om.query(face[i], bary[i], math.inf, face, bary)
+        mask = np.arange(n) != i
+        np.testing.assert_allclose(do[mask], db[mask], rtol=1e-12)
+        np.testing.assert_allclose(to[mask], tb[mask], atol=1e-9)
+
+
+def test_noisy_sphere_invariants():
+    """Symmetry, triangle inequality, Euclidean lower bound (Sec. 3.1), unit tangents."""
+    m = synth.icosphere(2, 1.0, noise=0.04, seed=9)
+    om = O.OracleMesh(m)
+    th, ps, _ = om.vertex_info()
+    assert ps.sum() > 10                      # saddle vertices exist
+    face, bary = synth.place_uniform(m, 40, 4)
+    x = synth.particles.world_positions(m, face, bary)
+    rs, j, d, t = om.neighbors(face, bary, math.inf)
+    n = len(face)
+    D = np.full((n, n), 0.0)
+    for i in range(n):
+        D[i, j[rs[i]:rs[i + 1]]] = d[rs[i]:rs[i + 1]]
+    np.testing.assert_allclose(D, D.T, rtol=1e-12, atol=1e-14)
+    E = np.linalg.norm(x[:, None] - x[None], axis=2)
+    assert (D >= E - 1e-12).all()
+    tri = D[:, None, :] <= D[:, :, None] + D[None, :, :] + 1e-12
+    assert tri.all()
+    np.testing.assert_allclose(np.linalg.norm(t, axis=1), 1.0, atol=1e-12)
+
+
+def test_cutoff_is_a_filter():
+    """A cutoff only removes pairs (Sec. 3.1 submeshing): same distances below r_c."""
+    m = synth.icosphere(3, 1.0, noise=0.01, seed=2)
+    om = O.OracleMesh(m)
+    face, bary = synth.place_uniform(m, 60, 8)
+    rs0, j0, d0, t0 = om.neighbors(face, bary, math.inf)
+    for rc in (0.3, 0.7):
+        rs, j, d, t = om.neighbors(face, bary, rc)
+        for i in range(len(face)):
+            keep = d0[rs0[i]:rs0[i + 1]] < rc
+            assert list(j[rs[i]:rs[i + 1]]) == list(j0[rs0[i]:rs0[i + 1]][keep])
+            np.testing.assert_allclose(d[rs[i]:rs[i + 1]], d0[rs0[i]:rs0[i + 1]][keep], rtol=1e-13)
+            np.testing.assert_allclose(t[rs[i]:rs[i + 1]], t0[rs0[i]:rs0[i + 1]][keep], atol=1e-12)
+
+
+def test_sphere_converges_to_great_circle():
+    """Icosphere distances approach great-circle arcs as the mesh refines (Sec. 2.2, O(h^2))."""
+    errs = []
+    for level in (2, 3, 4):
+        m = synth.icosphere(level, 1.0)
+        om = O.OracleMesh(m)
+        face, bary = synth.place_uniform(m, 12, 1)
+        x = synth.particles.world_positions(m, face, bary)
+        u = x / np.linalg.norm(x, axis=1, keepdims=True)
+        rs, j, d, t = om.neighbors(face, bary, 1.5)
+        e = 0.0
+        for i in range(len(face)):
+            jj = j[rs[i]:rs[i + 1]]
+            arc = np.arccos(np.clip(u[jj] @ u[i], -1, 1))
+            e = max(e, np.max(np.abs(d[rs[i]:rs[i + 1]] - arc)))
+        errs.append(e)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] / errs[2] > 2.5           # close to 4 for a second-order error
+
+
+def test_mesh_validation():
+    m = synth.tetrahedron()
+    bad = m.faces.copy()
+    bad[0] = bad[0][[0, 2, 1]]               # one face flipped
+    with pytest.raises(ValueError):
+        O.OracleMesh(synth.meshes.Mesh(m.verts, bad))
+    three = np.concatenate([m.faces, [[0, 1, 3]]])  # edge (0,1) used three times
+    with pytest.raises(ValueError):
+        O.OracleMesh(synth.meshes.Mesh(m.verts, three))
