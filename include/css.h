@@ -1,0 +1,183 @@
+/*
+ * css.h -- C ABI of the curved-surface geodesic molecular-dynamics library
+ * (GB300 / sm_103a CUDA).
+ *
+ * The library implements the per-timestep hot path of particle simulations on
+ * triangulated surfaces (Webb & Sussman, "curvedSpaceSim", arXiv:2404.19751):
+ *   - exact polyhedral geodesic distances l_ij and initial tangents from every
+ *     particle to every particle within a cutoff, by continuous window
+ *     propagation over planar unfoldings of the mesh          (Sec. 2.2, 3.1)
+ *   - pair forces  F_i = sum_j -U'(l_ij) grad_{x_i} l_ij      (Sec. 2.1, 3.1)
+ *   - the straightest face-walk "shift" with parallel transport, driving
+ *     velocity-Verlet NVE, Brownian and active Brownian dynamics (Sec. 2.1, 3.2)
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: CSS_OK (0) or a negative CSS_ERR_*
+ *     code; none aborts.  css_last_error() gives a one-line message.
+ *   - Pointers are plain host or CUDA device pointers; the library detects which
+ *     (cudaPointerGetAttributes).  Inputs are copied into library-owned device
+ *     memory; outputs go to caller-owned buffers.  A call that writes to host
+ *     memory synchronises the context stream before returning.
+ *   - All GPU work is enqueued on the stream given to css_create (NULL: the
+ *     legacy default stream).  Objects must not be used from two host threads
+ *     at once.
+ *   - Positions are (face index, barycentric triple); vectors (velocities,
+ *     orientations, forces, tangents) are world-frame 3-vectors lying in the
+ *     plane of the particle's current face (Sec. 3.2).
+ *   - Faces are vertex-index triples, counter-clockwise seen from the side the
+ *     surface normal points to; the mesh must be an oriented 2-manifold,
+ *     optionally with boundary (Sec. 2.2 assumes closed surfaces; open edges
+ *     reflect the face walk) or periodic in x and y.
+ */
+#ifndef CSS_H
+#define CSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define CSS_OK                    0
+#define CSS_ERR_INVALID_ARG      -1   /* bad size, index, NaN, null pointer        */
+#define CSS_ERR_NONMANIFOLD      -2   /* edge in >2 faces, flipped face, zero area  */
+#define CSS_ERR_OOM              -3   /* device allocation failed                   */
+#define CSS_ERR_CUDA             -4   /* a CUDA runtime call failed                 */
+#define CSS_ERR_CAPACITY         -5   /* caller buffer too small (see n_pairs)      */
+#define CSS_ERR_QUEUE_OVERFLOW   -6   /* window workspace exhausted after retries   */
+#define CSS_ERR_ITER_LIMIT       -7   /* a device loop reached its iteration cap    */
+#define CSS_ERR_NO_DEVICE        -8   /* no CUDA device / wrong architecture        */
+
+/* ---------------------------------------------------------------- enums */
+#define CSS_FP64 0   /* every window, distance and walk operation in FP64            */
+#define CSS_FP32 1   /* FP32 window arithmetic; FP64 kept for unfolded source
+                        coordinates, near-degenerate predicates and the face walk  */
+
+#define CSS_POT_HARMONIC 0   /* U = eps (1 - l/sigma)^2            for l < r_cut     */
+#define CSS_POT_WCA      1   /* U = 4 eps ((s/l)^12 - (s/l)^6) + eps for l < r_cut   */
+#define CSS_POT_GAUSSIAN 2   /* U = A exp(-l^2 / (2 sigma^2))      for l < r_cut     */
+
+#define CSS_INT_NVE 0   /* velocity Verlet: v += dt/2m F; shift by dt v; F(x); v += dt/2m F */
+#define CSS_INT_BD  1   /* lambda dr = dt F + sqrt(2 kT lambda dt) eta                      */
+#define CSS_INT_ABP 2   /* dr = dt (v0 n + F / lambda); n rotated by sqrt(2 Dr dt) xi       */
+
+typedef struct css_ctx css_ctx;
+typedef struct css_mesh css_mesh;
+typedef struct css_parts css_parts;
+typedef struct css_batch css_batch;
+
+typedef struct {
+    int32_t kind;          /* CSS_POT_*                                     */
+    double eps, sigma;     /* energy scale, length scale                    */
+    double r_cut;          /* U = 0 for l >= r_cut                          */
+    double A;              /* Gaussian amplitude                            */
+} css_potential;
+
+typedef struct {
+    int32_t kind;          /* CSS_INT_*                                     */
+    double dt, kT, lambda; /* time step, temperature, friction              */
+    double v0, Dr;         /* self-propulsion speed, rotational diffusion   */
+    double mass;           /* particle mass (NVE)                           */
+    double max_disp;       /* cap on |dr| per step (INFINITY: none)         */
+} css_integrator;
+
+/* ---------------------------------------------------------------- context
+ * css_create: bind to CUDA device `device` and the cudaStream_t `stream`
+ * (may be NULL).  Fails with CSS_ERR_NO_DEVICE when no sm_103-class device
+ * is present.  css_destroy frees the context's workspace (objects created
+ * from it must be freed first). */
+int css_create(css_ctx** out, int device, void* stream);
+int css_destroy(css_ctx* ctx);
+const char* css_last_error(const css_ctx* ctx);
+/* Device-side counters of the last neighbour / force evaluation:
+ * [0] sources, [1] windows created, [2] windows propagated, [3] pairs found,
+ * [4] vertex emissions, [5] workspace retries. */
+int css_last_counters(const css_ctx* ctx, int64_t out[6]);
+
+/* ---------------------------------------------------------------- mesh (Sec. 2.2)
+ * Upload a triangulated surface and precompute its intrinsic geometry on the
+ * device: edges and adjacency, per-face planar layouts, half-edge frames and
+ * the rigid maps between neighbouring faces, vertex angle sums, and the
+ * pseudo-source vertices (boundary, flat or saddle: angle sum >= 2 pi - 1e-9).
+ *   verts  nv x 3 doubles, faces nf x 3 int32 (row major), host or device.
+ *   period NULL, or host pointer to {Lx, Ly}: x and y wrap with these periods
+ *          and edge vectors use the minimum image.
+ * Errors: CSS_ERR_INVALID_ARG (sizes, indices out of range, NaN),
+ *         CSS_ERR_NONMANIFOLD (edge shared by >2 faces, inconsistent
+ *         orientation, degenerate face). */
+int css_mesh_upload(css_ctx* ctx, const double* verts, int64_t nv, const int32_t* faces,
+                    int64_t nf, const double* period, css_mesh** out);
+int css_mesh_free(css_mesh* mesh);
+/* counts: nv, nf, number of undirected edges, number of pseudo-source vertices */
+int css_mesh_counts(const css_mesh* mesh, int64_t out[4]);
+
+/* ---------------------------------------------------------------- particles (Sec. 3)
+ * A particle set bound to a mesh.  face: n int32; bary: n x 3 doubles summing
+ * to 1 (each >= -1e-12); vel / orient: n x 3 world tangent vectors or NULL
+ * (zero).  seed keys the Philox4x32-10 noise stream (counter = particle, step).
+ * Errors: CSS_ERR_INVALID_ARG for a face index out of range, a barycentric
+ * triple that does not sum to 1, or non-finite values. */
+int css_particles_set(css_ctx* ctx, css_mesh* mesh, int64_t n, const int32_t* face,
+                      const double* bary, const double* vel, const double* orient,
+                      uint64_t seed, css_parts** out);
+/* Copy state out (any pointer may be NULL): face n, bary n x 3, vel n x 3,
+ * orient n x 3, force n x 3 (the last force evaluation), and the step counter. */
+int css_particles_get(css_parts* parts, int32_t* face, double* bary, double* vel,
+                      double* orient, double* force, int64_t* step);
+int css_particles_free(css_parts* parts);
+
+/* ---------------------------------------------------------------- hot path
+ * css_geodesic_neighbors (Sec. 3.1 "displacement"): every ordered pair (i, j),
+ * i != j, with geodesic distance l_ij < r_c (r_c may be INFINITY: all pairs),
+ * returned as CSR rows in source order with columns in increasing j:
+ *   row_start n+1 int64, nbr_j int32, dist double, tangent 3 doubles per pair
+ *   (unit initial direction at i of the geodesic towards j, world frame).
+ * capacity is the length of nbr_j / dist (tangent holds 3 x capacity).  If it
+ * is too small the call returns CSS_ERR_CAPACITY with *n_pairs set to the
+ * needed count and writes nothing else.  Pairs with l_ij within 1e-9 r_c of
+ * r_c may appear or not. */
+int css_geodesic_neighbors(css_parts* parts, double r_c, int precision, int64_t capacity,
+                           int64_t* n_pairs, int64_t* row_start, int32_t* nbr_j,
+                           double* dist, double* tangent);
+
+/* css_compute_forces (Sec. 3.1): F_i = sum_{l_ij < r_c} U'(l_ij) t_ij where t_ij is the
+ * unit tangent at i towards j (so U' < 0 repels), and E_pot = 1/2 sum_ij U(l_ij).
+ * forces: n x 3 doubles (world, in each particle's face plane) or NULL;
+ * e_pot: one double or NULL.  The result is also stored in the particle set. */
+int css_compute_forces(css_parts* parts, const css_potential* pot, double r_c, int precision,
+                       double* forces, double* e_pot);
+
+/* css_integrate_step (Sec. 2.1 + Sec. 3.2 "shift"): n_steps steps of the chosen
+ * dynamics, each a complete pass: neighbour search within r_c, forces, and the
+ * straightest face walk that moves every particle and parallel-transports its
+ * velocity / orientation.  NVE reuses the force of the previous step (computed
+ * on the first call).  noise: NULL (Philox stream) or a device/host array of
+ * n_steps x n x 2 standard normals used instead (test mode).  The steps are
+ * replayed from a captured CUDA graph when n_steps > 1 and noise is NULL.
+ * e_pot (may be NULL) receives the potential energy of the last force pass. */
+int css_integrate_step(css_parts* parts, const css_potential* pot, const css_integrator* integ,
+                       double r_c, int precision, int64_t n_steps, const double* noise,
+                       double* e_pot);
+
+/* ---------------------------------------------------------------- batched form
+ * Many independent particle sets (each on its own mesh) advanced together: the
+ * neighbour/force work of all sets runs in one persistent launch per step whose
+ * warps pull (set, source) items from a device work queue ordered by estimated
+ * cost, and the whole n_steps sequence is captured once into a CUDA graph.
+ * The sets must come from the same context; they share pot/integ/r_c. */
+int css_batch_create(css_ctx* ctx, css_parts* const* parts, int32_t n_sets, css_batch** out);
+int css_batch_step(css_batch* batch, const css_potential* pot, const css_integrator* integ,
+                   double r_c, int precision, int64_t n_steps);
+int css_batch_free(css_batch* batch);
+
+/* ---------------------------------------------------------------- tuning
+ * Launch shape of the neighbour/force kernel: warps per CTA (1..16) and the
+ * per-warp window-workspace capacity (windows; rounded up to a power of two).
+ * 0 keeps the current value.  The batched form's autotuner calls this. */
+int css_set_launch(css_ctx* ctx, int32_t warps_per_cta, int32_t window_capacity);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSS_H */

@@ -1,0 +1,424 @@
+// dynamics.cu -- per-step particle kernels: face bucketing, the face-walk "shift" and
+// the equations of motion (Sec. 2.1 and Sec. 3.2 of the paper).
+//
+// Face walk (Sec. 3.2): a displacement in the tangent plane of the particle's face
+// is followed across faces.  Each iteration finds, in barycentric coordinates, the
+// first side the straight path meets; the particle moves there, the face changes to
+// the neighbour across that side, and the rest of the displacement and every carried
+// vector (velocity, orientation) are rotated into the neighbour's plane (the rigid
+// unfolding map, i.e. the rotation about the shared edge).  A path through a vertex
+// continues along the straightest direction, half the vertex's total angle from the
+// incoming one; a boundary vertex sends the path back; an open boundary side
+// reflects it.  All of it in FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "css_internal.h"
+
+namespace {
+
+using css::DMesh;
+using css::HeRec;
+
+constexpr int WALK_MAX = 100000;
+constexpr double WPI = 3.141592653589793238462643383279503;
+
+// ------------------------------------------------------------------ exclusive scans
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <class Ti, class To>
+__device__ To block_excl_scan(To v, To* sh, To& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    To x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        To t = __shfl_up_sync(CSS_FULL, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        To y = lane < SCAN_THREADS / 32 ? sh[lane] : (To)0;
+        for (int o = 1; o < 32; o <<= 1) {
+            To t = __shfl_up_sync(CSS_FULL, y, o);
+            if (lane >= o) y += t;
+        }
+        if (lane < SCAN_THREADS / 32) sh[lane] = y;
+    }
+    __syncthreads();
+    total = sh[SCAN_THREADS / 32 - 1];
+    const To before = w > 0 ? sh[w - 1] : (To)0;
+    __syncthreads();
+    return before + x - v;
+}
+
+template <class Ti, class To>
+__global__ void k_tile_sums(const Ti* in, int64_t n, To* sums) {
+    __shared__ To sh[SCAN_THREADS / 32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    To s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) if (base + k < n) s += (To)in[base + k];
+    To tot;
+    block_excl_scan<Ti, To>(s, sh, tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <class To>
+__global__ void k_scan_sums(To* sums, int nt) {
+    __shared__ To sh[SCAN_THREADS / 32];
+    To carry = 0;
+    for (int base = 0; base < nt; base += SCAN_THREADS) {
+        const int i = base + threadIdx.x;
+        const To v = i < nt ? sums[i] : (To)0;
+        To tot;
+        const To ex = block_excl_scan<To, To>(v, sh, tot);
+        if (i < nt) sums[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+template <class Ti, class To>
+__global__ void k_tile_apply(const Ti* in, int64_t n_in, int64_t n, const To* sums, To* out) {
+    __shared__ To sh[SCAN_THREADS / 32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    To loc[SCAN_ITEMS];
+    To s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) { loc[k] = (base + k < n_in) ? (To)in[base + k] : (To)0; s += loc[k]; }
+    To tot;
+    To ex = block_excl_scan<Ti, To>(s, sh, tot) + sums[blockIdx.x];
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) out[base + k] = ex;
+        ex += loc[k];
+    }
+}
+
+// ------------------------------------------------------------------ bucketing (face CSR)
+__global__ void k_count(int32_t n, const int32_t* face, int32_t* cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(cnt + face[i], 1);
+}
+
+// decrements the counts back to zero while placing particles
+__global__ void k_scatter(int32_t n, const int32_t* face, int32_t* cnt, const int32_t* start, int32_t* items) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int f = face[i];
+    const int p = atomicSub(cnt + f, 1) - 1;
+    items[start[f] + p] = i;
+}
+
+// ------------------------------------------------------------------ face walk
+__device__ __forceinline__ void corner(const DMesh& m, int f, int k, double& x, double& y) {
+    css::face_corner(m, f, k, x, y);
+}
+
+__device__ __forceinline__ void rot(double co, double si, double& x, double& y) {
+    const double a = co * x - si * y, b = si * x + co * y;
+    x = a; y = b;
+}
+
+// straightest continuation through corner cw of face f (interior vertex: leave at half the
+// total angle from the incoming direction; boundary vertex: turn back)
+__device__ void through_vertex(const DMesh& m, int& f, int cw, double& px, double& py, double& dx, double& dy,
+                               int nc, double* cx, double* cy) {
+    const int v = m.fv[3 * f + cw];
+    const double len = sqrt(dx * dx + dy * dy);
+    const double ux = dx / len, uy = dy / len;
+    double phi[2], mag[2];
+    for (int q = 0; q < nc; ++q) {
+        mag[q] = sqrt(cx[q] * cx[q] + cy[q] * cy[q]);
+        phi[q] = atan2(ux * cy[q] - uy * cx[q], ux * cx[q] + uy * cy[q]);
+    }
+    double wx, wy;
+    corner(m, f, cw, wx, wy);
+    if (m.bnd[v]) {
+        px = wx; py = wy; dx = -dx; dy = -dy;
+        for (int q = 0; q < nc; ++q) { cx[q] = -cx[q]; cy[q] = -cy[q]; }
+        return;
+    }
+    double nx, ny;
+    corner(m, f, cw + 1, nx, ny);
+    double ex = nx - wx, ey = ny - wy, el = sqrt(ex * ex + ey * ey);
+    ex /= el; ey /= el;
+    double beta = atan2(ex * (-uy) - ey * (-ux), ex * (-ux) + ey * (-uy));
+    if (beta < 0.0) beta = 0.0;
+    double rem = beta + 0.5 * m.theta[v];
+    for (int guard = 0; guard < 64; ++guard) {
+        const HeRec r = m.he[3 * f + cw];
+        const double ang = atan2(r.cy, r.cx);
+        if (rem <= ang) break;
+        rem -= ang;
+        const int hop = 3 * f + (cw == 0 ? 2 : cw - 1);
+        const int tw = m.twin[hop];
+        if (tw < 0) break;
+        f = tw / 3;
+        cw = tw - 3 * f;
+    }
+    corner(m, f, cw, wx, wy);
+    corner(m, f, cw + 1, nx, ny);
+    ex = nx - wx; ey = ny - wy; el = sqrt(ex * ex + ey * ey);
+    ex /= el; ey /= el;
+    double ox = ex, oy = ey;
+    rot(cos(rem), sin(rem), ox, oy);
+    px = wx; py = wy;
+    dx = len * ox; dy = len * oy;
+    for (int q = 0; q < nc; ++q) {
+        double vx = ox, vy = oy;
+        rot(cos(phi[q]), sin(phi[q]), vx, vy);
+        cx[q] = mag[q] * vx; cy[q] = mag[q] * vy;
+    }
+}
+
+// walk from (f, p) by d (face-frame components), carrying nc vectors; false on iteration cap
+__device__ bool face_walk(const DMesh& m, int& f, double& px, double& py, double dx, double dy, int nc, double* cx,
+                          double* cy) {
+    int entry = -1;
+    for (int it = 0; it < WALK_MAX; ++it) {
+        const double L01 = m.lay[3 * f], x2 = m.lay[3 * f + 1], y2 = m.lay[3 * f + 2];
+        double lam[3], rate[3];
+        lam[2] = py / y2; lam[1] = (px - lam[2] * x2) / L01; lam[0] = 1.0 - lam[1] - lam[2];
+        rate[2] = dy / y2; rate[1] = (dx - rate[2] * x2) / L01; rate[0] = -rate[1] - rate[2];
+        double tmin = __longlong_as_double(0x7ff0000000000000ll);
+        int imin = -1;
+        for (int q = 0; q < 3; ++q) {
+            if (!(rate[q] < 0.0)) continue;
+            const int side = q == 2 ? 0 : q + 1;   // side opposite corner q
+            if (side == entry) continue;
+            double t = -lam[q] / rate[q];
+            if (t < 0.0) t = 0.0;
+            if (t < tmin) { tmin = t; imin = q; }
+        }
+        if (!(tmin < 1.0)) { px += dx; py += dy; return true; }
+        const int k = imin == 2 ? 0 : imin + 1;
+        const int k1 = k == 2 ? 0 : k + 1;
+        const double hx = px + tmin * dx, hy = py + tmin * dy;
+        double rx = (1.0 - tmin) * dx, ry = (1.0 - tmin) * dy;
+        double lh[3];
+        lh[2] = hy / y2; lh[1] = (hx - lh[2] * x2) / L01; lh[0] = 1.0 - lh[1] - lh[2];
+        int vc = -1;
+        if (lh[k1] < 1e-12) vc = k;
+        else if (lh[k] < 1e-12) vc = k1;
+        if (vc >= 0) {
+            px = hx; py = hy;
+            through_vertex(m, f, vc, px, py, rx, ry, nc, cx, cy);
+            dx = rx; dy = ry; entry = -1;
+            continue;
+        }
+        const int h = 3 * f + k;
+        const int tw = m.twin[h];
+        double ax, ay, bx, by;
+        corner(m, f, k, ax, ay);
+        corner(m, f, k1, bx, by);
+        const double L = m.he[h].L;
+        const double ux = (bx - ax) / L, uy = (by - ay) / L;
+        if (tw < 0) {
+            const double pr = rx * ux + ry * uy;
+            rx = 2.0 * pr * ux - rx; ry = 2.0 * pr * uy - ry;
+            for (int q = 0; q < nc; ++q) {
+                const double pc = cx[q] * ux + cy[q] * uy;
+                cx[q] = 2.0 * pc * ux - cx[q]; cy[q] = 2.0 * pc * uy - cy[q];
+            }
+            px = hx; py = hy; dx = rx; dy = ry; entry = k;
+            continue;
+        }
+        const int g = tw / 3, k2 = tw - 3 * g;
+        double qax, qay, qbx, qby;
+        corner(m, g, k2 + 1, qax, qay);   // image of corner k
+        corner(m, g, k2, qbx, qby);       // image of corner k+1
+        const double Lg = sqrt((qbx - qax) * (qbx - qax) + (qby - qay) * (qby - qay));
+        const double vx = (qbx - qax) / Lg, vy = (qby - qay) / Lg;
+        const double co = ux * vx + uy * vy, si = ux * vy - uy * vx;
+        double ox = hx - ax, oy = hy - ay;
+        rot(co, si, ox, oy);
+        px = qax + ox; py = qay + oy;
+        rot(co, si, rx, ry);
+        for (int q = 0; q < nc; ++q) rot(co, si, cx[q], cy[q]);
+        dx = rx; dy = ry; f = g; entry = k2;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void to_face(const DMesh& m, int f, const double* v, double& x, double& y) {
+    const double* fr = m.frame + 9 * (size_t)f;
+    x = v[0] * fr[3] + v[1] * fr[4] + v[2] * fr[5];
+    y = v[0] * fr[6] + v[1] * fr[7] + v[2] * fr[8];
+}
+__device__ __forceinline__ void to_world(const DMesh& m, int f, double x, double y, double* v) {
+    const double* fr = m.frame + 9 * (size_t)f;
+    v[0] = x * fr[3] + y * fr[6];
+    v[1] = x * fr[4] + y * fr[7];
+    v[2] = x * fr[5] + y * fr[8];
+}
+
+__device__ bool shift_particle(const DMesh& m, int& f, double* bary, const double* d3, int nc, double* c3a,
+                               double* c3b) {
+    double px = bary[1] * m.lay[3 * f] + bary[2] * m.lay[3 * f + 1];
+    double py = bary[2] * m.lay[3 * f + 2];
+    double dx, dy, cx[2], cy[2];
+    to_face(m, f, d3, dx, dy);
+    if (nc > 0) to_face(m, f, c3a, cx[0], cy[0]);
+    if (nc > 1) to_face(m, f, c3b, cx[1], cy[1]);
+    const bool ok = face_walk(m, f, px, py, dx, dy, nc, cx, cy);
+    const double L01 = m.lay[3 * f], x2 = m.lay[3 * f + 1], y2 = m.lay[3 * f + 2];
+    double l2 = py / y2, l1 = (px - l2 * x2) / L01, l0 = 1.0 - l1 - l2;
+    l0 = l0 < 0.0 ? 0.0 : l0; l1 = l1 < 0.0 ? 0.0 : l1; l2 = l2 < 0.0 ? 0.0 : l2;
+    const double s = l0 + l1 + l2;
+    bary[0] = l0 / s; bary[1] = l1 / s; bary[2] = l2 / s;
+    if (nc > 0) to_world(m, f, cx[0], cy[0], c3a);
+    if (nc > 1) to_world(m, f, cx[1], cy[1], c3b);
+    return ok;
+}
+
+__device__ __forceinline__ void clamp_disp(double* d, double maxd) {
+    const double n = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (n > maxd) { const double s = maxd / n; d[0] *= s; d[1] *= s; d[2] *= s; }
+}
+
+// ------------------------------------------------------------------ Philox4x32-10 (Salmon et al., SC'11)
+__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a0 = c[0], a2 = c[2];
+        const uint32_t hi0 = __umulhi(0xD2511F53u, a0), lo0 = 0xD2511F53u * a0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, a2), lo1 = 0xCD9E8D57u * a2;
+        c[0] = hi1 ^ c[1] ^ k0;
+        c[1] = lo1;
+        c[2] = hi0 ^ c[3] ^ k1;
+        c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+__device__ __forceinline__ void normal_pair(uint64_t seed, uint64_t particle, uint64_t step, double& z0, double& z1) {
+    uint32_t c[4] = {(uint32_t)particle, (uint32_t)(particle >> 32), (uint32_t)step, (uint32_t)(step >> 32)};
+    philox(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double u1 = ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6) + 0.5) / 9007199254740992.0;
+    const double u2 = ((double)(c[2] >> 5) * 67108864.0 + (double)(c[3] >> 6) + 0.5) / 9007199254740992.0;
+    const double r = sqrt(-2.0 * log(u1));
+    z0 = r * cos(2.0 * WPI * u2);
+    z1 = r * sin(2.0 * WPI * u2);
+}
+
+// ------------------------------------------------------------------ integrators
+__global__ void k_nve_kick_drift(DMesh m, int32_t n, int32_t* face, double* bary, double* vel, const double* force,
+                                 css_integrator it, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double h = 0.5 * it.dt / it.mass;
+    double v[3], d[3];
+    for (int a = 0; a < 3; ++a) { v[a] = vel[3 * i + a] + h * force[3 * i + a]; d[a] = it.dt * v[a]; }
+    clamp_disp(d, it.max_disp);
+    int f = face[i];
+    double b[3] = {bary[3 * i], bary[3 * i + 1], bary[3 * i + 2]};
+    if (!shift_particle(m, f, b, d, 1, v, nullptr)) atomicOr(status, css::ST_WALK_LIMIT);
+    face[i] = f;
+    for (int a = 0; a < 3; ++a) { bary[3 * i + a] = b[a]; vel[3 * i + a] = v[a]; }
+}
+
+__global__ void k_nve_kick(int32_t n, double* vel, const double* force, double h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    vel[i] += h * force[i];
+}
+
+__global__ void k_overdamped(DMesh m, int32_t n, int32_t* face, double* bary, double* orient, const double* force,
+                             css_integrator it, uint64_t seed, const int64_t* dstep, const double* noise, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double z0, z1;
+    if (noise) { z0 = noise[2 * (size_t)i]; z1 = noise[2 * (size_t)i + 1]; }
+    else normal_pair(seed, (uint64_t)i, (uint64_t)*dstep, z0, z1);
+    int f = face[i];
+    const double* fr = m.frame + 9 * (size_t)f;
+    double b[3] = {bary[3 * i], bary[3 * i + 1], bary[3 * i + 2]};
+    double d[3];
+    bool ok;
+    if (it.kind == CSS_INT_BD) {
+        const double amp = sqrt(2.0 * it.kT * it.dt / it.lambda);
+        for (int a = 0; a < 3; ++a) d[a] = it.dt / it.lambda * force[3 * i + a] + amp * (z0 * fr[3 + a] + z1 * fr[6 + a]);
+        clamp_disp(d, it.max_disp);
+        ok = shift_particle(m, f, b, d, 0, nullptr, nullptr);
+    } else {
+        double o[3] = {orient[3 * i], orient[3 * i + 1], orient[3 * i + 2]};
+        for (int a = 0; a < 3; ++a) d[a] = it.dt * (it.v0 * o[a] + force[3 * i + a] / it.lambda);
+        clamp_disp(d, it.max_disp);
+        ok = shift_particle(m, f, b, d, 1, o, nullptr);
+        double ox, oy;
+        to_face(m, f, o, ox, oy);
+        const double on = sqrt(ox * ox + oy * oy);
+        ox /= on; oy /= on;
+        const double ang = sqrt(2.0 * it.Dr * it.dt) * z0;
+        rot(cos(ang), sin(ang), ox, oy);
+        to_world(m, f, ox, oy, o);
+        for (int a = 0; a < 3; ++a) orient[3 * i + a] = o[a];
+    }
+    if (!ok) atomicOr(status, css::ST_WALK_LIMIT);
+    face[i] = f;
+    for (int a = 0; a < 3; ++a) bary[3 * i + a] = b[a];
+}
+
+__global__ void k_step_inc(int64_t* dstep) { *dstep += 1; }
+
+inline unsigned nb(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+namespace cssi {
+
+size_t scan_tmp_ints(int64_t count) { return (size_t)((count + SCAN_TILE - 1) / SCAN_TILE) + 1; }
+
+cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t count, int32_t* tmp, cudaStream_t st) {
+    const int nt = (int)((count + SCAN_TILE - 1) / SCAN_TILE);
+    k_tile_sums<int32_t, int32_t><<<nt, SCAN_THREADS, 0, st>>>(in, count, tmp);
+    k_scan_sums<int32_t><<<1, SCAN_THREADS, 0, st>>>(tmp, nt);
+    k_tile_apply<int32_t, int32_t><<<nt, SCAN_THREADS, 0, st>>>(in, count, count, tmp, out_excl);
+    return cudaGetLastError();
+}
+
+// row_start[0..n] (int64) from n counts: the tile sums live at the end of row_start's
+// scratch tail, so the caller passes row_start with n + 1 + scan_tmp_ints(n + 1) slots
+cudaError_t launch_scan_rows(const int32_t* cnt, int64_t* row_start, int32_t n, cudaStream_t st) {
+    const int64_t count = (int64_t)n + 1;
+    const int nt = (int)((count + SCAN_TILE - 1) / SCAN_TILE);
+    int64_t* tmp = row_start + count;
+    k_tile_sums<int32_t, int64_t><<<nt, SCAN_THREADS, 0, st>>>(cnt, n, tmp);
+    k_scan_sums<int64_t><<<1, SCAN_THREADS, 0, st>>>(tmp, nt);
+    k_tile_apply<int32_t, int64_t><<<nt, SCAN_THREADS, 0, st>>>(cnt, n, count, tmp, row_start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket(int32_t n, int32_t nf, const int32_t* face, int32_t* fcnt, int32_t* fstart, int32_t* fitems,
+                          int32_t* scan_tmp, cudaStream_t st) {
+    k_count<<<nb(n), 256, 0, st>>>(n, face, fcnt);
+    cudaError_t e = launch_scan_i32(fcnt, fstart, (int64_t)nf + 1, scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    k_scatter<<<nb(n), 256, 0, st>>>(n, face, fcnt, fstart, fitems);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nve_kick_drift(const DMesh& m, int32_t n, int32_t* face, double* bary, double* vel,
+                                  const double* force, css_integrator it, int* status, cudaStream_t st) {
+    k_nve_kick_drift<<<nb(n, 128), 128, 0, st>>>(m, n, face, bary, vel, force, it, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nve_kick(int32_t n, double* vel, const double* force, css_integrator it, cudaStream_t st) {
+    k_nve_kick<<<nb(3 * (int64_t)n), 256, 0, st>>>(n, vel, force, 0.5 * it.dt / it.mass);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overdamped_move(const DMesh& m, int32_t n, int32_t* face, double* bary, double* orient,
+                                   const double* force, css_integrator it, uint64_t seed, const int64_t* dstep,
+                                   const double* noise, int* status, cudaStream_t st) {
+    k_overdamped<<<nb(n, 128), 128, 0, st>>>(m, n, face, bary, orient, force, it, seed, dstep, noise, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_inc(int64_t* dstep, cudaStream_t st) {
+    k_step_inc<<<1, 1, 0, st>>>(dstep);
+    return cudaGetLastError();
+}
+
+}  // namespace cssi

@@ -1,0 +1,887 @@
+// geodesic.cu -- cutoff geodesic neighbours and forces, one warp per source particle.
+//
+// Method (Sec. 2.2 and Sec. 3.1 of the paper): exact polyhedral geodesics from a
+// source point by continuous window propagation.  A window is an interval of an
+// edge together with a pseudo-source s (the source, or a boundary / flat / saddle
+// vertex where shortest paths may bend) unfolded into the plane of that edge and
+// the geodesic length sigma from the source to s; it carries the distance
+// sigma + |x - s| to the points x it sees.  Each window is unfolded into the next
+// face, its cone is cut by the two far edges into at most two child windows, each
+// child is intersected with the windows already on its edge so every point keeps
+// the smaller distance, vertices reached receive distance candidates, and
+// pseudo-source vertices start windows on their opposite edges.  Windows whose
+// smallest distance is >= r_c are dropped (the Euclidean-lower-bound submesh of
+// Sec. 3.1 becomes this cutoff stop).  Afterwards every particle in a reached face
+// is evaluated: minimum over the direct segment, the windows entering its face
+// whose cone contains it, and paths through the face's vertices; the force
+// F_i = sum_j U'(l_ij) t_ij is accumulated in the same pass.
+//
+// GPU organisation: one warp owns one source at a time (persistent grid pulling
+// sources from a device counter).  The warp pops up to 32 windows per wave (FIFO
+// over the window pool = creation order, a relaxed label-correcting order that is
+// exact because every window only ever carries the length of a real path and
+// trimming keeps the pointwise minimum), unfolds them in parallel, then inserts
+// the children: lanes that target the same edge are grouped with __match_any_sync
+// and take turns, lanes on different edges trim in parallel.  Per-warp state
+// (edge, vertex and face hash tables with generation tags, the window pool)
+// lives in a global-memory workspace slice that stays L1/L2 resident.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "css_internal.h"
+
+namespace {
+
+using css::DMesh;
+using css::HeRec;
+
+constexpr int WIN_ALIVE = 1;
+constexpr int WIN_DONE = 2;    // already unfolded
+constexpr int WIN_FIXED = 4;   // tangent fixed (descends from a pseudo-source vertex)
+constexpr int MAXP = 6;        // interval pieces one insertion may hold
+constexpr int MAX_WARPS_CTA = 16;
+
+template <class R>
+struct Win {
+    double sx, sy;     // pseudo-source in the frame of half-edge `he` (FP64 in both forms)
+    R b0, b1;          // interval along the half-edge
+    R sig;             // geodesic length source -> pseudo-source
+    R ta, tb;          // image of the source-face x axis (direct) or fixed tangent
+    int32_t he, next, flags;
+};
+
+template <class R>
+struct Tol;
+template <>
+struct Tol<double> {
+    static constexpr double w = 1e-12;   // relative interval width / endpoint tolerance
+};
+template <>
+struct Tol<float> {
+    static constexpr float w = 2e-6f;
+};
+
+struct WarpSm {
+    int nwin, head, nface, nemit, err;
+};
+
+template <class R>
+struct Ws {
+    unsigned long long* ekey;
+    int32_t* ehead;
+    unsigned long long* vkey;
+    double* vdist;
+    R* vtan;
+    int32_t* vvid;
+    int32_t* vflag;
+    unsigned long long* fkey;
+    int32_t* flist;
+    Win<R>* win;
+    int32_t* emit;
+    int log_eh, log_vh, log_fh, wcap, fcap, emcap;
+    uint32_t gen;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <class R>
+__host__ __device__ inline size_t ws_layout(int log_eh, int log_vh, int log_fh, int wcap, int fcap, int emcap,
+                                            size_t* off) {
+    size_t o = 0;
+    const size_t EH = 1ull << log_eh, VH = 1ull << log_vh, FH = 1ull << log_fh;
+    off[0] = o; o = al16(o + EH * 8);          // ekey
+    off[1] = o; o = al16(o + EH * 4);          // ehead
+    off[2] = o; o = al16(o + VH * 8);          // vkey
+    off[3] = o; o = al16(o + VH * 8);          // vdist
+    off[4] = o; o = al16(o + VH * 2 * sizeof(R));  // vtan
+    off[5] = o; o = al16(o + VH * 4);          // vvid
+    off[6] = o; o = al16(o + VH * 4);          // vflag
+    off[7] = o; o = al16(o + FH * 8);          // fkey
+    off[8] = o; o = al16(o + (size_t)fcap * 4);   // flist
+    off[9] = o; o = al16(o + (size_t)wcap * sizeof(Win<R>));
+    off[10] = o; o = al16(o + (size_t)emcap * 4);
+    return o;
+}
+
+template <class R>
+__device__ inline Ws<R> ws_bind(const cssi::GeoWs& g, int warp) {
+    size_t off[11];
+    ws_layout<R>(g.log_eh, g.log_vh, g.log_fh, g.wcap, g.fcap, g.emcap, off);
+    char* b = g.base + (size_t)warp * g.stride;
+    Ws<R> w;
+    w.ekey = (unsigned long long*)(b + off[0]);
+    w.ehead = (int32_t*)(b + off[1]);
+    w.vkey = (unsigned long long*)(b + off[2]);
+    w.vdist = (double*)(b + off[3]);
+    w.vtan = (R*)(b + off[4]);
+    w.vvid = (int32_t*)(b + off[5]);
+    w.vflag = (int32_t*)(b + off[6]);
+    w.fkey = (unsigned long long*)(b + off[7]);
+    w.flist = (int32_t*)(b + off[8]);
+    w.win = (Win<R>*)(b + off[9]);
+    w.emit = (int32_t*)(b + off[10]);
+    w.log_eh = g.log_eh; w.log_vh = g.log_vh; w.log_fh = g.log_fh;
+    w.wcap = g.wcap; w.fcap = g.fcap; w.emcap = g.emcap;
+    w.gen = 0;
+    return w;
+}
+
+// ------------------------------------------------------------------ window geometry
+template <class R>
+__device__ __forceinline__ R win_key(const Win<R>& w) {
+    double x = w.sx < (double)w.b0 ? (double)w.b0 : (w.sx > (double)w.b1 ? (double)w.b1 : w.sx);
+    double dx = x - w.sx;
+    return w.sig + (R)sqrt((R)(dx * dx + w.sy * w.sy));
+}
+
+// distance carried to the point (px, py) of the window frame
+template <class R>
+__device__ __forceinline__ R win_dist(const Win<R>& w, double px, double py) {
+    R dx = (R)(px - w.sx), dy = (R)(py - w.sy);
+    return w.sig + sqrt(dx * dx + dy * dy);
+}
+
+template <class R>
+__device__ __forceinline__ void win_tangent(const Win<R>& w, double px, double py, R& tx, R& ty) {
+    if (w.flags & WIN_FIXED) { tx = w.ta; ty = w.tb; return; }
+    R dx = (R)(px - w.sx), dy = (R)(py - w.sy);
+    R n = sqrt(dx * dx + dy * dy);
+    dx /= n; dy /= n;
+    tx = dx * w.ta + dy * w.tb;
+    ty = -dx * w.tb + dy * w.ta;
+}
+
+// a pseudo-source on the edge line sees the face beyond only through its own position
+template <class R>
+__device__ __forceinline__ bool win_degen(const Win<R>& w, double L) { return w.sy > -1e-13 * L; }
+template <class R>
+__device__ __forceinline__ bool win_degen_sees(const Win<R>& w, double L) {
+    double tol = 1e-12 * L;
+    return w.sx >= (double)w.b0 - tol && w.sx <= (double)w.b1 + tol;
+}
+
+// parameter in [0,1] along A->B hit by the ray from s through (X, 0)
+template <class R>
+__device__ __forceinline__ R ray_hit(double sx, double sy, R X, double ax, double ay, double bx, double by) {
+    R dx = (R)((double)X - sx), dy = (R)(-sy);
+    R ex = (R)(bx - ax), ey = (R)(by - ay);
+    R den = ex * dy - ey * dx;
+    R qx = (R)(sx - ax), qy = (R)(sy - ay);
+    R mu = den != (R)0 ? (qx * dy - qy * dx) / den : (R)0;
+    return mu < (R)0 ? (R)0 : (mu > (R)1 ? (R)1 : mu);
+}
+
+template <class R>
+struct VCand {
+    int32_t v;
+    R d, tx, ty;
+};
+
+// Unfold window W into the next face: vertex candidates and at most two children.
+template <class R>
+__device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* vc, int& nvc, Win<R>* ch,
+                          int& nch) {
+    nvc = 0;
+    nch = 0;
+    const int h = W.he;
+    const int f = h / 3;
+    const int k = h - 3 * f;
+    const HeRec r = m.he[h];
+    const int k1 = (k == 2) ? 0 : k + 1, k2 = (k == 0) ? 2 : k - 1;
+    const int32_t vu = m.fv[h], vv = m.fv[3 * f + k1], vcid = m.fv[3 * f + k2];
+    const double L = r.L;
+    const R tolv = (R)(Tol<R>::w * L);
+    if (W.b0 <= tolv) {
+        VCand<R>& c = vc[nvc++];
+        c.v = vu; c.d = win_dist(W, 0.0, 0.0); win_tangent(W, 0.0, 0.0, c.tx, c.ty);
+    }
+    if ((double)W.b1 >= L - (double)tolv) {
+        VCand<R>& c = vc[nvc++];
+        c.v = vv; c.d = win_dist(W, L, 0.0); win_tangent(W, L, 0.0, c.tx, c.ty);
+    }
+    const bool degen = win_degen(W, L);
+    if (degen && !win_degen_sees(W, L)) return;
+    // occlusion predicate (FP64 in both forms): where the ray s -> c crosses the edge line
+    const double xc = degen ? 0.0 : W.sx + (r.cx - W.sx) * (-W.sy) / (r.cy - W.sy);
+    if (degen || (xc >= (double)W.b0 && xc <= (double)W.b1)) {
+        VCand<R>& c = vc[nvc++];
+        c.v = vcid; c.d = win_dist(W, r.cx, r.cy); win_tangent(W, r.cx, r.cy, c.tx, c.ty);
+    }
+    if (r.tl >= 0 && (degen || xc > (double)W.b0)) {
+        R mu0 = (R)0, mu1 = (R)1;
+        if (!degen) {
+            mu0 = ray_hit<R>(W.sx, W.sy, W.b0, 0.0, 0.0, r.cx, r.cy);
+            mu1 = ((double)W.b1 >= xc) ? (R)1 : ray_hit<R>(W.sx, W.sy, W.b1, 0.0, 0.0, r.cx, r.cy);
+        }
+        Win<R>& c = ch[nch];
+        c = W;
+        c.he = r.tl;
+        c.sx = W.sx * r.cl + W.sy * r.sl;           // rotate by -angle(c), origin at u
+        c.sy = -W.sx * r.sl + W.sy * r.cl;
+        if (!(W.flags & WIN_FIXED)) {
+            c.ta = W.ta * (R)r.cl + W.tb * (R)r.sl;
+            c.tb = -W.ta * (R)r.sl + W.tb * (R)r.cl;
+        }
+        const R Lc = (R)(r.cx * r.cl + r.cy * r.sl);
+        c.b0 = mu0 * Lc; c.b1 = mu1 * Lc;
+        if (c.sy > 0.0) c.sy = 0.0;
+        c.flags = (W.flags & WIN_FIXED) | WIN_ALIVE;
+        if (win_key(c) < (R)rc) ++nch;
+    }
+    if (r.tr >= 0 && (degen || xc < (double)W.b1)) {
+        R mu0 = (R)0, mu1 = (R)1;
+        if (!degen) {
+            mu0 = ((double)W.b0 <= xc) ? (R)0 : ray_hit<R>(W.sx, W.sy, W.b0, r.cx, r.cy, L, 0.0);
+            mu1 = ray_hit<R>(W.sx, W.sy, W.b1, r.cx, r.cy, L, 0.0);
+        }
+        Win<R>& c = ch[nch];
+        c = W;
+        c.he = r.tr;
+        const double px = W.sx - r.cx, py = W.sy - r.cy;   // rotate by -angle(v - c), origin at c
+        c.sx = px * r.cr + py * r.sr;
+        c.sy = -px * r.sr + py * r.cr;
+        if (!(W.flags & WIN_FIXED)) {
+            c.ta = W.ta * (R)r.cr + W.tb * (R)r.sr;
+            c.tb = -W.ta * (R)r.sr + W.tb * (R)r.cr;
+        }
+        const R Ld = (R)((L - r.cx) * r.cr - r.cy * r.sr);
+        c.b0 = mu0 * Ld; c.b1 = mu1 * Ld;
+        if (c.sy > 0.0) c.sy = 0.0;
+        c.flags = (W.flags & WIN_FIXED) | WIN_ALIVE;
+        if (win_key(c) < (R)rc) ++nch;
+    }
+}
+
+// Points x in (lo, hi) where two windows carry equal distance: |x-a| - |x-b| = sb - sa squared
+// twice (FP64 in both forms: this is the near-degenerate intersection predicate).  Spurious
+// roots only add breakpoints; the winner of each piece is decided by evaluation.
+__device__ int equal_points(double ax, double ay, double sa, double bx, double by, double sb, double lo, double hi,
+                            double* r) {
+    const double del = sb - sa;
+    const double al = bx - ax;
+    const double be = (ax * ax + ay * ay) - (bx * bx + by * by) - del * del;
+    const double c2 = del * del - al * al;
+    const double c1 = -(2.0 * del * del * bx + al * be);
+    const double c0 = del * del * (bx * bx + by * by) - 0.25 * be * be;
+    double cand0 = 0.0, cand1 = 0.0;
+    int nc = 0;
+    const double scale = fabs(c2) + fabs(c1) / (fabs(hi) + fabs(lo) + 1e-300) + 1e-300;
+    if (fabs(c2) <= 1e-14 * scale) {
+        if (c1 != 0.0) { cand0 = -c0 / c1; nc = 1; }
+    } else {
+        double disc = c1 * c1 - 4.0 * c2 * c0;
+        if (disc < 0.0) disc = 0.0;
+        const double sq = sqrt(disc);
+        const double q = -0.5 * (c1 + (c1 >= 0.0 ? sq : -sq));
+        if (q != 0.0) { cand0 = q / c2; cand1 = c0 / q; nc = 2; }
+        else { cand0 = -c1 / (2.0 * c2); nc = 1; }
+    }
+    int n = 0;
+    if (nc > 0 && cand0 > lo && cand0 < hi) r[n++] = cand0;
+    if (nc > 1 && cand1 > lo && cand1 < hi) r[n++] = cand1;
+    if (n == 2 && r[0] > r[1]) { double t = r[0]; r[0] = r[1]; r[1] = t; }
+    return n;
+}
+
+template <class R>
+__device__ __forceinline__ void ivl_add(R (*iv)[2], int& n, R x0, R x1, int& err) {
+    if (!(x1 > x0)) return;
+    if (n > 0 && x0 <= iv[n - 1][1]) { if (x1 > iv[n - 1][1]) iv[n - 1][1] = x1; return; }
+    if (n < MAXP) { iv[n][0] = x0; iv[n][1] = x1; ++n; }
+    else err |= css::ST_PIECES;
+}
+
+template <class R>
+__device__ __forceinline__ void face_add(Ws<R>& ws, WarpSm& sm, int32_t f) {
+    bool claimed;
+    int s = css::ht_insert(ws.fkey, ws.log_fh, ws.gen, f, claimed);
+    if (s < 0) { atomicOr(&sm.err, css::ST_HASH_OVERFLOW); return; }
+    if (claimed) {
+        int p = atomicAdd(&sm.nface, 1);
+        if (p < ws.fcap) ws.flist[p] = f;
+        else atomicOr(&sm.err, css::ST_HASH_OVERFLOW);
+    }
+}
+
+template <class R>
+__device__ __forceinline__ int win_alloc(WarpSm& sm, int wcap) {
+    int p = atomicAdd(&sm.nwin, 1);
+    if (p >= wcap) { atomicOr(&sm.err, css::ST_WIN_OVERFLOW); return -1; }
+    return p;
+}
+
+// Insert candidate window c on its edge (list slot es), intersecting it with every window
+// already on the edge from either side: on each overlap both keep only where they carry
+// the smaller distance (ties to the existing window).  Executed by one lane per edge.
+template <class R>
+__device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win<R> c, double rc) {
+    const double L = m.he[c.he].L;
+    const R Lr = (R)L;
+    const R tolw = (R)(Tol<R>::w * L);
+    if (c.b0 < (R)0) c.b0 = (R)0;
+    if (c.b1 > Lr) c.b1 = Lr;
+    if (!(c.b1 - c.b0 > tolw) || !(win_key(c) < (R)rc)) return;
+    int err = 0;
+    R pc[MAXP][2];
+    int np = 1;
+    pc[0][0] = c.b0; pc[0][1] = c.b1;
+    int prev = -1;
+    int oi = ws.ehead[es];
+    int guard = 0;
+    while (oi >= 0 && np > 0) {
+        if (++guard > ws.wcap) { err |= css::ST_ITER_LIMIT; break; }
+        Win<R> o = ws.win[oi];
+        const int onext = o.next;
+        if (!(o.flags & WIN_ALIVE)) {                       // unlink dead windows
+            if (prev < 0) ws.ehead[es] = onext; else ws.win[prev].next = onext;
+            oi = onext;
+            continue;
+        }
+        const bool same = (o.he == c.he);
+        const R o0 = same ? o.b0 : Lr - o.b1, o1 = same ? o.b1 : Lr - o.b0;
+        const double osx = same ? o.sx : L - o.sx, osy = same ? o.sy : -o.sy;
+        R npc[MAXP][2];
+        int nn = 0;
+        R lost[MAXP][2];
+        int nl = 0;
+        for (int p = 0; p < np; ++p) {
+            const R a0 = pc[p][0], a1 = pc[p][1];
+            const R lo = a0 > o0 ? a0 : o0, hi = a1 < o1 ? a1 : o1;
+            if (!(hi - lo > tolw)) { ivl_add(npc, nn, a0, a1, err); continue; }
+            double bp[4];
+            int nb = 0;
+            bp[nb++] = (double)lo;
+            double rr[2];
+            const int nr = equal_points(c.sx, c.sy, (double)c.sig, osx, osy, (double)o.sig, (double)lo, (double)hi, rr);
+            for (int q = 0; q < nr; ++q) bp[nb++] = rr[q];
+            bp[nb++] = (double)hi;
+            ivl_add(npc, nn, a0, lo, err);
+            for (int q = 0; q + 1 < nb; ++q) {
+                const double xm = 0.5 * (bp[q] + bp[q + 1]);
+                const double dc = (double)c.sig + sqrt((xm - c.sx) * (xm - c.sx) + c.sy * c.sy);
+                const double dox = xm - osx;
+                const double dd = dc - ((double)o.sig + sqrt(dox * dox + osy * osy));
+                if (dd < 0.0) {
+                    ivl_add(npc, nn, (R)bp[q], (R)bp[q + 1], err);
+                    ivl_add(lost, nl, (R)bp[q], (R)bp[q + 1], err);
+                }
+            }
+            ivl_add(npc, nn, hi, a1, err);
+        }
+        np = 0;
+        for (int p = 0; p < nn; ++p)
+            if (npc[p][1] - npc[p][0] > tolw) { pc[np][0] = npc[p][0]; pc[np][1] = npc[p][1]; ++np; }
+        bool o_alive = true;
+        if (nl > 0) {
+            R keep[MAXP][2];
+            int nk = 0;
+            R cur = o0;
+            for (int q = 0; q < nl; ++q) {
+                if (lost[q][0] - cur > tolw) ivl_add(keep, nk, cur, lost[q][0], err);
+                if (lost[q][1] > cur) cur = lost[q][1];
+            }
+            if (o1 - cur > tolw) ivl_add(keep, nk, cur, o1, err);
+            if (nk == 0) {
+                ws.win[oi].flags = o.flags & ~WIN_ALIVE;
+                if (prev < 0) ws.ehead[es] = onext; else ws.win[prev].next = onext;
+                o_alive = false;
+            } else {
+                int tail = oi;
+                for (int q = 0; q < nk; ++q) {
+                    const R k0 = same ? keep[q][0] : Lr - keep[q][1];
+                    const R k1 = same ? keep[q][1] : Lr - keep[q][0];
+                    if (q == 0) { ws.win[oi].b0 = k0; ws.win[oi].b1 = k1; }
+                    else {
+                        const int pid = win_alloc<R>(sm, ws.wcap);
+                        if (pid < 0) break;
+                        Win<R> piece = o;
+                        piece.b0 = k0; piece.b1 = k1;
+                        piece.next = onext;
+                        ws.win[pid] = piece;
+                        ws.win[tail].next = pid;          // keep the list order, skip the pieces
+                        tail = pid;
+                    }
+                }
+                prev = tail;
+            }
+        } else {
+            prev = oi;
+        }
+        if (!o_alive) { oi = onext; continue; }
+        oi = onext;
+    }
+    if (err) atomicOr(&sm.err, err);
+    bool added = false;
+    for (int p = 0; p < np; ++p) {
+        Win<R> w = c;
+        w.b0 = pc[p][0]; w.b1 = pc[p][1];
+        w.flags = (c.flags & WIN_FIXED) | WIN_ALIVE;
+        if (!(win_key(w) < (R)rc)) continue;
+        const int id = win_alloc<R>(sm, ws.wcap);
+        if (id < 0) break;
+        w.next = ws.ehead[es];
+        ws.win[id] = w;
+        ws.ehead[es] = id;
+        added = true;
+    }
+    if (added) face_add(ws, sm, c.he / 3);
+}
+
+// ------------------------------------------------------------------ warp-cooperative rounds
+__device__ __forceinline__ int group_rounds(bool has, int key, int lane, int& rank) {
+    const int k = has ? key : (-1 - lane);
+    const unsigned grp = __match_any_sync(CSS_FULL, k);
+    rank = __popc(grp & css::lanemask_lt());
+    return (int)__reduce_max_sync(CSS_FULL, (unsigned)__popc(grp));
+}
+
+template <class R>
+__device__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, const VCand<R>& c, double rc,
+                             int lane) {
+    bool claimed = false;
+    int slot = -1;
+    if (has) {
+        slot = css::ht_insert(ws.vkey, ws.log_vh, ws.gen, c.v, claimed);
+        if (slot < 0) { atomicOr(&sm.err, css::ST_HASH_OVERFLOW); has = false; }
+    }
+    if (claimed) { ws.vdist[slot] = __longlong_as_double(0x7ff0000000000000ll); ws.vflag[slot] = 0; ws.vvid[slot] = c.v; }
+    __syncwarp();
+    int rank;
+    const int rounds = group_rounds(has, slot, lane, rank);
+    for (int q = 0; q < rounds; ++q) {
+        if (has && rank == q) {
+            const double d = (double)c.d;
+            if (d < ws.vdist[slot]) {
+                ws.vdist[slot] = d;
+                ws.vtan[2 * slot] = c.tx;
+                ws.vtan[2 * slot + 1] = c.ty;
+                if (m.pseudo[c.v] && d < rc && !(ws.vflag[slot] & 1)) {
+                    ws.vflag[slot] |= 1;
+                    const int p = atomicAdd(&sm.nemit, 1);
+                    if (p < ws.emcap) ws.emit[p] = slot;
+                    else atomicOr(&sm.err, css::ST_HASH_OVERFLOW);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <class R>
+__device__ void child_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, const Win<R>& c, double rc, int lane) {
+    bool claimed = false;
+    int slot = -1;
+    if (has) {
+        slot = css::ht_insert(ws.ekey, ws.log_eh, ws.gen, m.edge[c.he], claimed);
+        if (slot < 0) { atomicOr(&sm.err, css::ST_HASH_OVERFLOW); has = false; }
+    }
+    if (claimed) ws.ehead[slot] = -1;
+    __syncwarp();
+    int rank;
+    const int rounds = group_rounds(has, slot, lane, rank);
+    for (int q = 0; q < rounds; ++q) {
+        if (has && rank == q) insert_window(m, ws, sm, slot, c, rc);
+        __syncwarp();
+    }
+}
+
+// Pseudo-source vertices reached this wave start windows on every edge opposite them;
+// their one-ring faces join the target faces (paths may bend there, Sec. 2.2).
+template <class R>
+__device__ void emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, int lane) {
+    __syncwarp();
+    const int ne = min(sm.nemit, ws.emcap);
+    for (int base = 0; base < ne; base += 32) {
+        const int it = base + lane;
+        const bool has = it < ne;
+        int vid = 0, rs = 0, len = 0;
+        double dv = 0.0;
+        R tx = (R)0, ty = (R)0;
+        if (has) {
+            const int vs = ws.emit[it];
+            vid = ws.vvid[vs];
+            dv = ws.vdist[vs];
+            tx = ws.vtan[2 * vs];
+            ty = ws.vtan[2 * vs + 1];
+            ws.vflag[vs] &= ~1;
+            rs = m.ring_start[vid];
+            len = m.ring_start[vid + 1] - rs;
+        }
+        const int maxlen = (int)__reduce_max_sync(CSS_FULL, (unsigned)len);
+        for (int q = 0; q < maxlen; ++q) {
+            bool hh = q < len;
+            Win<R> c;
+            if (hh) {
+                const int hc = m.ring[rs + q];
+                const int f = hc / 3, k = hc - 3 * f;
+                const int hop = 3 * f + (k == 2 ? 0 : k + 1);
+                face_add(ws, sm, f);
+                const int tw = m.twin[hop];
+                if (tw < 0) hh = false;
+                else {
+                    const HeRec r = m.he[hop];
+                    c.he = tw;
+                    c.b0 = (R)0;
+                    c.b1 = (R)r.L;
+                    c.sx = r.L - r.cx;
+                    c.sy = -r.cy;
+                    c.sig = (R)dv;
+                    c.ta = tx;
+                    c.tb = ty;
+                    c.flags = WIN_FIXED | WIN_ALIVE;
+                    c.next = -1;
+                }
+            }
+            child_round(m, ws, sm, hh, c, rc, lane);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) sm.nemit = 0;
+    __syncwarp();
+}
+
+__device__ __forceinline__ double pot_dudl(const css_potential& p, double l) {
+    if (!(l < p.r_cut)) return 0.0;
+    if (p.kind == CSS_POT_HARMONIC) return -2.0 * p.eps * (1.0 - l / p.sigma) / p.sigma;
+    if (p.kind == CSS_POT_WCA) {
+        const double q = p.sigma / l, q2 = q * q, q6 = q2 * q2 * q2;
+        return 24.0 * p.eps * (q6 - 2.0 * q6 * q6) / l;
+    }
+    return -(l / (p.sigma * p.sigma)) * p.A * exp(-l * l / (2.0 * p.sigma * p.sigma));
+}
+
+__device__ __forceinline__ double pot_u(const css_potential& p, double l) {
+    if (!(l < p.r_cut)) return 0.0;
+    if (p.kind == CSS_POT_HARMONIC) { const double u = 1.0 - l / p.sigma; return p.eps * u * u; }
+    if (p.kind == CSS_POT_WCA) {
+        const double q = p.sigma / l, q2 = q * q, q6 = q2 * q2 * q2;
+        return 4.0 * p.eps * (q6 * q6 - q6) + p.eps;
+    }
+    return p.A * exp(-l * l / (2.0 * p.sigma * p.sigma));
+}
+
+// distance + source tangent (source-face layout) of particle j of face fl
+template <class R>
+__device__ double query(const DMesh& m, const Ws<R>& ws, int f0, double qx, double qy, int fl, const double* bj,
+                        R& tx, R& ty) {
+    const double L01 = m.lay[3 * fl], x2 = m.lay[3 * fl + 1], y2 = m.lay[3 * fl + 2];
+    const double px = bj[1] * L01 + bj[2] * x2, py = bj[2] * y2;
+    double best = __longlong_as_double(0x7ff0000000000000ll);
+    tx = (R)0; ty = (R)0;
+    if (fl == f0) {
+        const double dx = px - qx, dy = py - qy;
+        best = sqrt(dx * dx + dy * dy);
+        if (best > 0.0) { tx = (R)(dx / best); ty = (R)(dy / best); }
+    }
+    for (int k = 0; k < 3; ++k) {
+        const int h = 3 * fl + k;
+        const int slot = css::ht_find(ws.ekey, ws.log_eh, ws.gen, m.edge[h]);
+        if (slot < 0) continue;
+        double ax, ay, bx, by;
+        css::face_corner(m, fl, k, ax, ay);
+        css::face_corner(m, fl, k + 1, bx, by);
+        const double L = m.he[h].L;
+        const double dx = (bx - ax) / L, dy = (by - ay) / L;
+        const double hx = (px - ax) * dx + (py - ay) * dy;
+        const double hy = dx * (py - ay) - dy * (px - ax);
+        const double tol = 1e-12 * L;
+        int guard = 0;
+        for (int wi = ws.ehead[slot]; wi >= 0 && guard < ws.wcap; ++guard) {
+            const Win<R> w = ws.win[wi];
+            wi = w.next;
+            if (!(w.flags & WIN_ALIVE) || w.he != h) continue;
+            bool inside;
+            if (win_degen(w, L)) inside = win_degen_sees(w, L);
+            else {
+                const double X = w.sx + (hx - w.sx) * (-w.sy) / (hy - w.sy);
+                inside = X >= (double)w.b0 - tol && X <= (double)w.b1 + tol;
+            }
+            if (!inside) continue;
+            const double d = (double)win_dist(w, hx, hy);
+            if (d < best) { best = d; win_tangent(w, hx, hy, tx, ty); }
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        const int slot = css::ht_find(ws.vkey, ws.log_vh, ws.gen, m.fv[3 * fl + k]);
+        if (slot < 0) continue;
+        double vx, vy;
+        css::face_corner(m, fl, k, vx, vy);
+        const double d = ws.vdist[slot] + sqrt((px - vx) * (px - vx) + (py - vy) * (py - vy));
+        if (d < best) { best = d; tx = ws.vtan[2 * slot]; ty = ws.vtan[2 * slot + 1]; }
+    }
+    return best;
+}
+
+template <class R>
+__device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, int lane, int* status,
+                           unsigned long long* counters) {
+    const DMesh& m = J.m;
+    const double rc = J.rc;
+    const int f0 = J.face[i];
+    const double* b = J.bary + 3 * (size_t)i;
+    const double qx = b[1] * m.lay[3 * f0] + b[2] * m.lay[3 * f0 + 1];
+    const double qy = b[2] * m.lay[3 * f0 + 2];
+    if (lane == 0) { sm.nwin = 0; sm.head = 0; sm.nface = 0; sm.nemit = 0; sm.err = 0; }
+    __syncwarp();
+    if (lane == 0) face_add(ws, sm, f0);
+    {   // the source's own corners
+        VCand<R> c;
+        const bool has = lane < 3;
+        if (has) {
+            double vx, vy;
+            css::face_corner(m, f0, lane, vx, vy);
+            const double dx = vx - qx, dy = vy - qy, d = sqrt(dx * dx + dy * dy);
+            c.v = m.fv[3 * f0 + lane];
+            c.d = (R)d;
+            c.tx = (R)(d > 0.0 ? dx / d : 1.0);
+            c.ty = (R)(d > 0.0 ? dy / d : 0.0);
+        }
+        vertex_round(m, ws, sm, has, c, rc, lane);
+    }
+    {   // one window per edge of the source face, covering the whole edge
+        Win<R> c;
+        bool has = false;
+        if (lane < 3) {
+            const int h = 3 * f0 + lane;
+            const int tw = m.twin[h];
+            if (tw >= 0) {
+                has = true;
+                double ax, ay, bx, by;
+                css::face_corner(m, f0, lane, ax, ay);
+                css::face_corner(m, f0, lane + 1, bx, by);
+                const double L = m.he[h].L;
+                const double dx = (bx - ax) / L, dy = (by - ay) / L;
+                const double hx = (qx - ax) * dx + (qy - ay) * dy;
+                const double hy = dx * (qy - ay) - dy * (qx - ax);
+                c.he = tw;
+                c.b0 = (R)0;
+                c.b1 = (R)m.he[tw].L;
+                c.sx = L - hx;
+                c.sy = hy > 0.0 ? -hy : 0.0;
+                c.sig = (R)0;
+                c.ta = (R)(-dx);
+                c.tb = (R)dy;
+                c.flags = WIN_ALIVE;
+                c.next = -1;
+            }
+        }
+        child_round(m, ws, sm, has, c, rc, lane);
+    }
+    emit_round(m, ws, sm, rc, lane);
+    unsigned long long n_prop = 0;
+    for (int wave = 0;; ++wave) {
+        __syncwarp();
+        const int head = sm.head, nwin = min(sm.nwin, ws.wcap);
+        if (head >= nwin || sm.err) break;
+        __syncwarp();
+        if (lane == 0) sm.head = min(head + 32, nwin);
+        const int idx = head + lane;
+        Win<R> w;
+        bool act = false;
+        if (idx < nwin) {
+            w = ws.win[idx];
+            act = (w.flags & WIN_ALIVE) && !(w.flags & WIN_DONE) && win_key(w) < (R)rc;
+            if (act) ws.win[idx].flags = w.flags | WIN_DONE;
+        }
+        VCand<R> vc[3];
+        Win<R> ch[2];
+        int nvc = 0, nch = 0;
+        if (act) propagate(m, w, rc, vc, nvc, ch, nch);
+        n_prop += __popc(__ballot_sync(CSS_FULL, act));
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 3; ++q) vertex_round(m, ws, sm, q < nvc, vc[q], rc, lane);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) child_round(m, ws, sm, q < nch, ch[q], rc, lane);
+        emit_round(m, ws, sm, rc, lane);
+    }
+    __syncwarp();
+    const int err = sm.err;
+    const int nface = min(sm.nface, ws.fcap);
+    // ---- target evaluation (+ forces)
+    double fx = 0.0, fy = 0.0, en = 0.0;
+    int npair = 0;
+    const bool wp = J.want_pairs != 0;
+    for (int fb = 0; fb < nface; fb += 32) {
+        const int fi = fb + lane;
+        int fl = -1, st = 0, cnt = 0;
+        if (fi < nface) { fl = ws.flist[fi]; st = J.fstart[fl]; cnt = J.fstart[fl + 1] - st; }
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(CSS_FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(CSS_FULL, incl, 31);
+        for (int tb = 0; tb < total; tb += 32) {
+            const int t = tb + lane;
+            int owner = 0;
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int v = __shfl_sync(CSS_FULL, incl, owner + step - 1);
+                if (v <= t) owner += step;
+            }
+            owner = min(owner, 31);
+            const int o_fl = __shfl_sync(CSS_FULL, fl, owner);
+            const int o_st = __shfl_sync(CSS_FULL, st, owner);
+            const int o_ex = __shfl_sync(CSS_FULL, incl - cnt, owner);
+            bool ispair = false;
+            double d = 0.0;
+            R tx = (R)0, ty = (R)0;
+            int j = -1;
+            if (t < total) {
+                j = J.fitems[o_st + (t - o_ex)];
+                if (j != i) {
+                    d = query(m, ws, f0, qx, qy, o_fl, J.bary + 3 * (size_t)j, tx, ty);
+                    ispair = d < rc;
+                }
+            }
+            const unsigned pm = __ballot_sync(CSS_FULL, ispair);
+            if (wp && ispair) {
+                const int pos = npair + __popc(pm & css::lanemask_lt());
+                if (pos < J.pair_cap) {
+                    const size_t o = (size_t)i * J.pair_cap + pos;
+                    J.pj[o] = j;
+                    J.pd[o] = d;
+                    const double* fr = m.frame + 9 * (size_t)f0;
+                    J.pt[3 * o] = (double)tx * fr[3] + (double)ty * fr[6];
+                    J.pt[3 * o + 1] = (double)tx * fr[4] + (double)ty * fr[7];
+                    J.pt[3 * o + 2] = (double)tx * fr[5] + (double)ty * fr[8];
+                }
+            }
+            npair += __popc(pm);
+            if (ispair && J.want_forces) {
+                const double du = pot_dudl(J.pot, d);
+                fx += du * (double)tx;
+                fy += du * (double)ty;
+                en += 0.5 * pot_u(J.pot, d);
+            }
+        }
+    }
+    fx = css::warp_sum(fx);
+    fy = css::warp_sum(fy);
+    en = css::warp_sum(en);
+    if (lane == 0) {
+        if (J.want_forces) {
+            const double* fr = m.frame + 9 * (size_t)f0;
+            J.force[3 * (size_t)i] = fx * fr[3] + fy * fr[6];
+            J.force[3 * (size_t)i + 1] = fx * fr[4] + fy * fr[7];
+            J.force[3 * (size_t)i + 2] = fx * fr[5] + fy * fr[8];
+            if (J.epot) atomicAdd(J.epot, en);
+        }
+        if (J.pcnt) J.pcnt[i] = npair;
+        int st = err;
+        if (wp && npair > J.pair_cap) st |= css::ST_PAIR_OVERFLOW;
+        if (st) atomicOr(status, st);
+        atomicAdd(counters + 0, 1ull);
+        atomicAdd(counters + 1, (unsigned long long)min(sm.nwin, ws.wcap));
+        atomicAdd(counters + 2, n_prop);
+        atomicAdd(counters + 3, (unsigned long long)npair);
+    }
+    __syncwarp();
+}
+
+template <class R>
+__global__ void __launch_bounds__(512) k_geodesic(cssi::GeoJob job0, const cssi::GeoJob* jobs,
+                                                  const int32_t* job_of_item, const int32_t* src_of_item,
+                                                  int32_t nitems, cssi::GeoWs g, int* work, int* status,
+                                                  unsigned long long* counters) {
+    __shared__ WarpSm smem[MAX_WARPS_CTA];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (gw >= g.nwarps) return;
+    WarpSm& sm = smem[wib];
+    Ws<R> ws = ws_bind<R>(g, gw);
+    uint32_t gen = 0;
+    if (lane == 0) gen = g.gen[gw];
+    gen = __shfl_sync(CSS_FULL, gen, 0);
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(work, 1);
+        item = __shfl_sync(CSS_FULL, item, 0);
+        if (item >= nitems) break;
+        const int jid = job_of_item ? job_of_item[item] : 0;
+        const cssi::GeoJob& J = jobs ? jobs[jid] : job0;
+        const int src = src_of_item ? src_of_item[item] : (J.order ? J.order[item] : item);
+        ++gen;
+        if (gen == 0) gen = 1;   // 0 marks never-used entries
+        ws.gen = gen;
+        run_source<R>(J, src, ws, sm, lane, status, counters);
+    }
+    if (lane == 0) g.gen[gw] = gen;
+}
+
+// CSR compaction: rows sorted by neighbour index
+__global__ void k_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd, const double* pt,
+                          int pair_cap, const int64_t* row_start, int32_t* oj, double* od, double* ot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = min(pcnt[i], pair_cap);
+    const int64_t o = row_start[i];
+    const size_t s = (size_t)i * pair_cap;
+    for (int a = 0; a < c; ++a) { oj[o + a] = pj[s + a]; od[o + a] = pd[s + a];
+        ot[3 * (o + a)] = pt[3 * (s + a)]; ot[3 * (o + a) + 1] = pt[3 * (s + a) + 1]; ot[3 * (o + a) + 2] = pt[3 * (s + a) + 2]; }
+    for (int a = 1; a < c; ++a) {           // insertion sort by j (rows are short)
+        const int32_t kj = oj[o + a];
+        const double kd = od[o + a], k0 = ot[3 * (o + a)], k1 = ot[3 * (o + a) + 1], k2 = ot[3 * (o + a) + 2];
+        int b = a - 1;
+        while (b >= 0 && oj[o + b] > kj) {
+            oj[o + b + 1] = oj[o + b]; od[o + b + 1] = od[o + b];
+            ot[3 * (o + b + 1)] = ot[3 * (o + b)]; ot[3 * (o + b + 1) + 1] = ot[3 * (o + b) + 1]; ot[3 * (o + b + 1) + 2] = ot[3 * (o + b) + 2];
+            --b;
+        }
+        oj[o + b + 1] = kj; od[o + b + 1] = kd; ot[3 * (o + b + 1)] = k0; ot[3 * (o + b + 1) + 1] = k1; ot[3 * (o + b + 1) + 2] = k2;
+    }
+}
+
+}  // namespace
+
+namespace cssi {
+
+size_t geo_ws_bytes_per_warp(int precision, int win_cap, int* log_eh, int* log_vh, int* log_fh, int* fcap,
+                             int* emcap) {
+    // hash tables sized from the window capacity: roughly one edge per 2 windows,
+    // one vertex per 4, one face per 2; load factor <= 1/2
+    int le = 6, lv = 6, lf = 6;
+    while ((1 << le) < win_cap) ++le;
+    while ((1 << lv) < win_cap / 2) ++lv;
+    while ((1 << lf) < win_cap) ++lf;
+    *log_eh = le; *log_vh = lv; *log_fh = lf;
+    *fcap = 1 << (lf - 1);
+    *emcap = 1 << lv;
+    size_t off[11];
+    return precision == CSS_FP32 ? ws_layout<float>(le, lv, lf, win_cap, *fcap, *emcap, off)
+                                 : ws_layout<double>(le, lv, lf, win_cap, *fcap, *emcap, off);
+}
+
+cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const int32_t* job_of_item,
+                            const int32_t* src_of_item, int32_t nitems, int precision, const GeoWs& ws,
+                            int warps_per_cta, int nctas, int* work_counter, int* status,
+                            unsigned long long* counters, cudaStream_t st) {
+    const dim3 block(32 * warps_per_cta);
+    if (precision == CSS_FP32)
+        k_geodesic<float><<<nctas, block, 0, st>>>(job0, djobs, job_of_item, src_of_item, nitems, ws, work_counter,
+                                                   status, counters);
+    else
+        k_geodesic<double><<<nctas, block, 0, st>>>(job0, djobs, job_of_item, src_of_item, nitems, ws, work_counter,
+                                                    status, counters);
+    return cudaGetLastError();
+}
+
+int geodesic_blocks_per_sm(int precision, int warps_per_cta) {
+    int nb = 0;
+    if (precision == CSS_FP32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<float>, 32 * warps_per_cta, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<double>, 32 * warps_per_cta, 0);
+    return nb;
+}
+
+cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd,
+                                 const double* pt, int pair_cap, const int64_t* row_start, int32_t* out_j,
+                                 double* out_d, double* out_t, cudaStream_t st) {
+    k_compact<<<(n + 127) / 128, 128, 0, st>>>(n, pcnt, pj, pd, pt, pair_cap, row_start, out_j, out_d, out_t);
+    return cudaGetLastError();
+}
+
+}  // namespace cssi

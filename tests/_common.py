@@ -1,0 +1,39 @@
+"""Helpers shared by the GPU parity tests."""
+import math
+
+import numpy as np
+
+FP64_RTOL = 1e-9        # FP64 path vs oracle: relative, on distances and forces
+FP32_REL_DIAM = 1e-5    # FP32 path vs oracle: absolute error / mesh diameter
+
+
+def csr_to_dict(rs, j, d, t):
+    out = {}
+    for i in range(len(rs) - 1):
+        for q in range(rs[i], rs[i + 1]):
+            out[(i, int(j[q]))] = (float(d[q]), t[q])
+    return out
+
+
+def compare_pairs(gpu, ref, r_c, dist_tol, tan_tol, rel=True, band=None):
+    """Compare two CSR neighbour sets.  Pairs within `band` of the cutoff may be missing on
+    either side.  Returns (n_compared, max_dist_err, max_tan_err)."""
+    G = csr_to_dict(*gpu)
+    R = csr_to_dict(*ref)
+    if band is None:
+        band = 1e-9 * r_c if math.isfinite(r_c) else 0.0
+    for k in set(G) ^ set(R):
+        d = G[k][0] if k in G else R[k][0]
+        assert math.isfinite(r_c) and abs(d - r_c) <= band, f"pair {k} only on one side (d={d}, r_c={r_c})"
+    md = mt = 0.0
+    n = 0
+    for k in set(G) & set(R):
+        dg, tg = G[k]
+        dr, tr = R[k]
+        err = abs(dg - dr) / (dr if rel else 1.0)
+        md = max(md, err)
+        mt = max(mt, float(np.linalg.norm(tg - tr)))
+        n += 1
+    assert md <= dist_tol, f"distance error {md} > {dist_tol}"
+    assert mt <= tan_tol, f"tangent error {mt} > {tan_tol}"
+    return n, md, mt

@@ -1,0 +1,281 @@
+"""CUDA path vs CPU oracle, element by element, through the C ABI (needs a GB300)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import oracle as O
+from tests._common import FP32_REL_DIAM, FP64_RTOL, compare_pairs
+
+css = pytest.importorskip("paper_2404_19751_gb300")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = css.create(0)
+    yield c
+    c.close()
+
+
+def _setup(ctx, m, face, bary, vel=None, orient=None, seed=0):
+    mesh = css.mesh_upload(ctx, m.verts, m.faces, m.period)
+    parts = css.particles_set(ctx, mesh, face, bary, vel, orient, seed=seed)
+    return mesh, parts
+
+
+def _noisy5():
+    m = synth.icosphere(5, 1.0, noise=0.016, seed=7)
+    face, bary = synth.place_uniform(m, 2048, 8)
+    return m, face, bary
+
+
+def _hfield_small():
+    m = synth.periodic_heightfield(64, 32, seed=3)
+    face, bary = synth.place_uniform(m, 1024, 13)
+    return m, face, bary
+
+
+WORKLOADS = {
+    "flat64": lambda: (lambda c: (c["mesh"], c["face"], c["bary"], c["r_c"]))(synth.make_config("flat64")),
+    "ico5_n1024": lambda: (lambda c: (c["mesh"], c["face"], c["bary"], c["r_c"]))(synth.make_config("ico5_n1024")),
+    "noisy_ico5_n2048": lambda: _noisy5() + (0.15,),
+    "hfield64_n1024": lambda: _hfield_small() + (0.12,),
+}
+
+
+def test_mesh_counts_match_oracle(ctx):
+    for m in (synth.icosphere(4, 1.0, noise=0.01, seed=2), synth.grid_plane(21, 21), synth.torus(3, 1, 30, 12),
+              synth.periodic_heightfield(32, 8, seed=1)):
+        mesh = css.mesh_upload(ctx, m.verts, m.faces, m.period)
+        om = O.OracleMesh(m)
+        th, ps, bd = om.vertex_info()
+        cnt = mesh.counts()
+        assert cnt["nv"] == m.nv and cnt["nf"] == m.nf
+        assert cnt["ne"] == om.num_edges
+        assert cnt["npseudo"] == int(ps.sum())
+        mesh.free()
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_neighbors_fp64_match_oracle(ctx, name):
+    m, face, bary, r_c = WORKLOADS[name]()
+    mesh, parts = _setup(ctx, m, face, bary)
+    g = css.geodesic_neighbors(parts, r_c, css.FP64)
+    r = O.OracleMesh(m).neighbors(face, bary, r_c)
+    n, md, mt = compare_pairs(g, r, r_c, FP64_RTOL, 1e-7)
+    assert n > 0
+    parts.free()
+    mesh.free()
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_neighbors_fp32_within_tolerance(ctx, name):
+    m, face, bary, r_c = WORKLOADS[name]()
+    mesh, parts = _setup(ctx, m, face, bary)
+    diam = synth.bbox_diagonal(m)
+    g = css.geodesic_neighbors(parts, r_c, css.FP32)
+    r = O.OracleMesh(m).neighbors(face, bary, r_c)
+    compare_pairs(g, r, r_c, FP32_REL_DIAM * diam, 1e-3, rel=False, band=FP32_REL_DIAM * diam)
+    parts.free()
+    mesh.free()
+
+
+TINY = [
+    ("tetra", lambda: synth.tetrahedron()),
+    ("octa", lambda: synth.octahedron()),
+    ("cube2", lambda: synth.cube(2)),
+    ("torus8x5", lambda: synth.torus(3, 1, 8, 5)),
+    ("noisy_ico1", lambda: synth.icosphere(1, 1.0, noise=0.15, seed=3)),
+    ("tube6x3", lambda: synth.cylinder_tube(6, 3, 1.0, 2.0)),
+    ("plane4_alt", lambda: synth.grid_plane(4, 4, alternate=True)),
+]
+
+
+@pytest.mark.parametrize("name,make", TINY, ids=[t[0] for t in TINY])
+def test_tiny_meshes_all_pairs(ctx, name, make):
+    m = make()
+    face, bary = synth.place_uniform(m, 20, 1)
+    mesh, parts = _setup(ctx, m, face, bary)
+    for prec, tol in ((css.FP64, FP64_RTOL), (css.FP32, None)):
+        g = css.geodesic_neighbors(parts, math.inf, prec)
+        r = O.OracleMesh(m).neighbors(face, bary, math.inf)
+        if prec == css.FP64:
+            compare_pairs(g, r, math.inf, tol, 1e-7)
+        else:
+            compare_pairs(g, r, math.inf, FP32_REL_DIAM * synth.bbox_diagonal(m), 1e-3, rel=False)
+    parts.free()
+    mesh.free()
+
+
+def test_sources_on_vertices_and_edges(ctx):
+    """Degenerate sources: barycentrics with zeros (on a vertex or an edge)."""
+    m = synth.icosphere(3, 1.0, noise=0.01, seed=5)
+    face, bary = synth.place_uniform(m, 60, 2)
+    bary[:10] = [1.0, 0.0, 0.0]
+    bary[10:20, 0] = 0.0
+    bary[10:20] /= bary[10:20].sum(1, keepdims=True)
+    mesh, parts = _setup(ctx, m, face, bary)
+    g = css.geodesic_neighbors(parts, 0.6, css.FP64)
+    r = O.OracleMesh(m).neighbors(face, bary, 0.6)
+    compare_pairs(g, r, 0.6, FP64_RTOL, 1e-6)
+    parts.free()
+    mesh.free()
+
+
+def test_edge_cases(ctx):
+    m = synth.icosphere(3, 1.0)
+    # a single particle: no pairs, zero force
+    mesh, parts = _setup(ctx, m, np.array([5], np.int32), np.array([[0.2, 0.3, 0.5]]))
+    rs, j, d, t = css.geodesic_neighbors(parts, 0.5, css.FP64)
+    assert rs.tolist() == [0, 0] and len(j) == 0
+    F, E = css.compute_forces(parts, dict(kind=0, eps=1.0, sigma=0.5, r_cut=0.5), 0.5)
+    assert np.all(F == 0) and E == 0
+    parts.free()
+    # all particles in one face, tiny cutoff leaves only same-face pairs
+    rng = np.random.default_rng(0)
+    b = rng.dirichlet([2, 2, 2], 12)
+    f = np.full(12, 7, np.int32)
+    parts = css.particles_set(ctx, mesh, f, b)
+    g = css.geodesic_neighbors(parts, 1e-3, css.FP64)
+    r = O.OracleMesh(m).neighbors(f, b, 1e-3)
+    compare_pairs(g, r, 1e-3, FP64_RTOL, 1e-7)
+    g = css.geodesic_neighbors(parts, 1.0, css.FP64)
+    assert g[0][-1] == 12 * 11
+    parts.free()
+    mesh.free()
+
+
+def test_errors_are_reported(ctx):
+    t = synth.tetrahedron()
+    bad = t.faces.copy()
+    bad[0] = bad[0][[0, 2, 1]]
+    with pytest.raises(css.CssError) as e:
+        css.mesh_upload(ctx, t.verts, bad)
+    assert e.value.code == -2
+    three = np.concatenate([t.faces, [[0, 1, 3]]])
+    with pytest.raises(css.CssError) as e:
+        css.mesh_upload(ctx, t.verts, three)
+    assert e.value.code == -2
+    with pytest.raises(css.CssError) as e:
+        css.mesh_upload(ctx, t.verts, t.faces + 10)
+    assert e.value.code == -1
+    mesh = css.mesh_upload(ctx, t.verts, t.faces)
+    with pytest.raises(css.CssError) as e:
+        css.particles_set(ctx, mesh, np.array([9], np.int32), np.array([[0.3, 0.3, 0.4]]))
+    assert e.value.code == -1
+    with pytest.raises(css.CssError) as e:
+        css.particles_set(ctx, mesh, np.array([1], np.int32), np.array([[0.3, 0.3, 0.5]]))
+    assert e.value.code == -1
+    mesh.free()
+
+
+@pytest.mark.parametrize("name", ["ico5_n1024", "hfield64_n1024", "noisy_ico5_n2048"])
+def test_forces_match_oracle(ctx, name):
+    m, face, bary, r_c = WORKLOADS[name]()
+    pot = dict(kind=css.POT_WCA, eps=1.0, sigma=r_c / 2 ** (1 / 6), r_cut=r_c) if "hfield" in name else \
+        dict(kind=css.POT_HARMONIC, eps=1.0, sigma=r_c, r_cut=r_c)
+    mesh, parts = _setup(ctx, m, face, bary)
+    F0, E0 = O.OracleMesh(m).forces(face, bary, r_c, pot)
+    F, E = css.compute_forces(parts, pot, r_c, css.FP64)
+    scale = np.max(np.abs(F0))
+    assert np.max(np.abs(F - F0)) <= FP64_RTOL * scale
+    assert E == pytest.approx(E0, rel=1e-10)
+    F32, E32 = css.compute_forces(parts, pot, r_c, css.FP32)
+    # FP32 form: distances within 1e-5 of the diameter; forces follow through U'
+    assert np.max(np.abs(F32 - F0)) <= 2e-3 * scale
+    parts.free()
+    mesh.free()
+
+
+def test_nve_flat64_ten_steps(ctx):
+    cfg = synth.make_config("flat64")
+    m, face, bary, vel = cfg["mesh"], cfg["face"], cfg["bary"], cfg["vel"]
+    pot, integ, r_c = cfg["pot"], cfg["integ"], cfg["r_c"]
+    mesh, parts = _setup(ctx, m, face, bary, vel)
+    om = O.OracleMesh(m)
+    F0, _ = om.forces(face, bary, r_c, pot)
+    o = om.integrate(face, bary, vel, None, F0, pot, integ, r_c, cfg["steps"])
+    css.integrate_step(parts, pot, integ, r_c, css.FP64, cfg["steps"])
+    s = css.particles_get(parts)
+    assert np.array_equal(s["face"], o["face"])
+    np.testing.assert_allclose(s["bary"], o["bary"], atol=1e-9)
+    np.testing.assert_allclose(s["vel"], o["vel"], atol=1e-9)
+    np.testing.assert_allclose(s["force"], o["force"], atol=1e-9 * np.max(np.abs(o["force"])))
+    parts.free()
+    mesh.free()
+
+
+def test_nve_ico5_one_step(ctx):
+    cfg = synth.make_config("ico5_n1024")
+    m, face, bary, vel = cfg["mesh"], cfg["face"], cfg["bary"], cfg["vel"]
+    pot, integ, r_c = cfg["pot"], cfg["integ"], cfg["r_c"]
+    mesh, parts = _setup(ctx, m, face, bary, vel)
+    om = O.OracleMesh(m)
+    F0, _ = om.forces(face, bary, r_c, pot)
+    o = om.integrate(face, bary, vel, None, F0, pot, integ, r_c, 1)
+    e = css.integrate_step(parts, pot, integ, r_c, css.FP64, 1)
+    s = css.particles_get(parts)
+    assert np.array_equal(s["face"], o["face"])
+    np.testing.assert_allclose(s["bary"], o["bary"], atol=1e-10)
+    np.testing.assert_allclose(s["vel"], o["vel"], atol=1e-10)
+    assert e == pytest.approx(o["epot"], rel=1e-9)
+    parts.free()
+    mesh.free()
+
+
+@pytest.mark.parametrize("kind", [css.INT_BD, css.INT_ABP])
+def test_overdamped_injected_and_philox(ctx, kind):
+    m, face, bary = _hfield_small()
+    r_c = 0.12
+    pot = dict(kind=css.POT_WCA, eps=1.0, sigma=r_c / 2 ** (1 / 6), r_cut=r_c)
+    integ = dict(kind=kind, dt=1e-5, kT=1.0, lam=1.0, v0=1.0, Dr=0.1, mass=1.0, max_disp=0.5 * r_c)
+    orient = synth.random_tangent_units(m, face, 9) if kind == css.INT_ABP else None
+    om = O.OracleMesh(m)
+    rng = np.random.default_rng(2)
+    noise = rng.standard_normal((2, len(face), 2))
+    mesh, parts = _setup(ctx, m, face, bary, None, orient, seed=77)
+    css.integrate_step(parts, pot, integ, r_c, css.FP64, 2, noise=noise)
+    s = css.particles_get(parts)
+    o = om.integrate(face, bary, None, orient, None, pot, integ, r_c, 2, noise=noise.reshape(-1, 2))
+    assert np.array_equal(s["face"], o["face"])
+    np.testing.assert_allclose(s["bary"], o["bary"], atol=1e-9)
+    if orient is not None:
+        np.testing.assert_allclose(s["orient"], o["orient"], atol=1e-9)
+    parts.free()
+    # Philox stream: same counter-based generator on both sides
+    parts = css.particles_set(ctx, mesh, face, bary, None, orient, seed=77)
+    css.integrate_step(parts, pot, integ, r_c, css.FP64, 3)
+    s = css.particles_get(parts)
+    o = om.integrate(face, bary, None, orient, None, pot, integ, r_c, 3, seed=77)
+    assert np.array_equal(s["face"], o["face"])
+    np.testing.assert_allclose(s["bary"], o["bary"], atol=1e-9)
+    parts.free()
+    mesh.free()
+
+
+def test_batch_equals_single_sets(ctx):
+    sets = []
+    singles = []
+    for k in range(3):
+        m = synth.configs.torus_for_faces(2000 + 1500 * k, 2.0 + 0.3 * k, 0.5 + 0.1 * k)
+        face, bary = synth.place_uniform(m, 200 + 100 * k, 40 + k)
+        vel = synth.gaussian_tangent_velocities(m, face, 0.1, 1.0, 50 + k)
+        mesh = css.mesh_upload(ctx, m.verts, m.faces)
+        sets.append((mesh, css.particles_set(ctx, mesh, face, bary, vel)))
+        singles.append((mesh, css.particles_set(ctx, mesh, face, bary, vel)))
+    pot = dict(kind=css.POT_HARMONIC, eps=1.0, sigma=0.1, r_cut=0.1)
+    integ = dict(kind=css.INT_NVE, dt=0.002, kT=0.1, lam=1.0, v0=0.0, Dr=0.0, mass=1.0, max_disp=math.inf)
+    for prec in (css.FP64, css.FP32):
+        b = css.batch_create(ctx, [p for _, p in sets])
+        css.batch_step(b, pot, integ, 0.1, prec, 5)
+        for (_, pb), (_, ps) in zip(sets, singles):
+            css.integrate_step(ps, pot, integ, 0.1, prec, 5)
+            a, c = css.particles_get(pb), css.particles_get(ps)
+            assert np.array_equal(a["face"], c["face"])
+            np.testing.assert_allclose(a["bary"], c["bary"], atol=1e-12)
+            np.testing.assert_allclose(a["vel"], c["vel"], atol=1e-12)
+        b.free()
+    for mesh, p in sets + singles:
+        p.free()
