@@ -19,8 +19,9 @@
  *     memory; outputs go to caller-owned buffers.  A call that writes to host
  *     memory synchronises the context stream before returning.
  *   - All GPU work is enqueued on the stream given to css_create (NULL: the
- *     legacy default stream).  Objects must not be used from two host threads
- *     at once.
+ *     library creates and owns a non-blocking stream; the legacy default stream
+ *     cannot hold a graph capture).  Objects must not be used from two host
+ *     threads at once.
  *   - Positions are (face index, barycentric triple); vectors (velocities,
  *     orientations, forces, tangents) are world-frame 3-vectors lying in the
  *     plane of the particle's current face (Sec. 3.2).
@@ -84,7 +85,7 @@ typedef struct {
 
 /* ---------------------------------------------------------------- context
  * css_create: bind to CUDA device `device` and the cudaStream_t `stream`
- * (may be NULL).  Fails with CSS_ERR_NO_DEVICE when no sm_103-class device
+ * (NULL: an owned non-blocking stream).  Fails with CSS_ERR_NO_DEVICE when no sm_103-class device
  * is present.  css_destroy frees the context's workspace (objects created
  * from it must be freed first). */
 int css_create(css_ctx** out, int device, void* stream);
@@ -125,6 +126,12 @@ int css_particles_set(css_ctx* ctx, css_mesh* mesh, int64_t n, const int32_t* fa
  * orient n x 3, force n x 3 (the last force evaluation), and the step counter. */
 int css_particles_get(css_parts* parts, int32_t* face, double* bary, double* vel,
                       double* orient, double* force, int64_t* step);
+/* Overwrite the state of an existing set (same n, same mesh) from host or device
+ * buffers; any pointer may be NULL to keep that field.  No validation beyond the
+ * face range is done on device inputs.  Used for checkpoint/resume and to feed a
+ * simulation from host memory. */
+int css_particles_update(css_parts* parts, const int32_t* face, const double* bary,
+                         const double* vel, const double* orient);
 int css_particles_free(css_parts* parts);
 
 /* ---------------------------------------------------------------- hot path
@@ -170,6 +177,16 @@ int css_batch_create(css_ctx* ctx, css_parts* const* parts, int32_t n_sets, css_
 int css_batch_step(css_batch* batch, const css_potential* pot, const css_integrator* integ,
                    double r_c, int precision, int64_t n_steps);
 int css_batch_free(css_batch* batch);
+
+/* ---------------------------------------------------------------- measurement
+ * css_last_kernel_ms: device time (ms) between CUDA events recorded on the context
+ * stream immediately before and after the last neighbour/force kernel launch
+ * (inside captured graphs too).  CSS_ERR_INVALID_ARG before any launch.
+ * css_fma_peak: measured dense FMA throughput (flop/s, 2 per FMA) of this GPU's
+ * FP32 or FP64 pipes, from an FMA-chain kernel filling every SM; it has no
+ * counterpart in the paper and serves as the ALU roofline denominator. */
+int css_last_kernel_ms(css_ctx* ctx, double* ms);
+int css_fma_peak(css_ctx* ctx, int precision, double* flops_per_s);
 
 /* ---------------------------------------------------------------- tuning
  * Launch shape of the neighbour/force kernel: warps per CTA (1..16) and the

@@ -617,11 +617,25 @@ static void run_source(ows* s, int32_t f0, const double* b) {
     }
 }
 
+/* candidate (length, tangent) list of one query, to report how far the runner-up with a
+ * different tangent is (a near-tie marks a cut-locus point where the tangent is set-valued) */
+#define OM_MAXCAND 64
+typedef struct { int n; double d[OM_MAXCAND], tx[OM_MAXCAND], ty[OM_MAXCAND]; } ocand;
+static void cand_add(ocand* c, double d, double tx, double ty) {
+    if (c && c->n < OM_MAXCAND) { c->d[c->n] = d; c->tx[c->n] = tx; c->ty[c->n] = ty; c->n++; }
+}
+static double cand_gap(const ocand* c, double best, double tx, double ty) {
+    double g = OM_INF;
+    for (int i = 0; i < c->n; ++i)
+        if (hypot(c->tx[i] - tx, c->ty[i] - ty) > 1e-9 && c->d[i] - best < g) g = c->d[i] - best;
+    return g;
+}
+
 /* Distance and source tangent (source-face layout) of a target point: the minimum over
  * the direct segment (same face), windows entering the face whose cone contains the
  * point, and paths through the face's vertices (Sec. 3.1: query the cached structure). */
-static double query_point(ows* s, int32_t f0, double qx, double qy, int32_t f, const double* b,
-                          double* tx, double* ty) {
+static double query_point_c(ows* s, int32_t f0, double qx, double qy, int32_t f, const double* b,
+                            double* tx, double* ty, ocand* cands) {
     const om_mesh* m = s->m;
     s->st.queries++;
     double px, py;
@@ -630,6 +644,7 @@ static double query_point(ows* s, int32_t f0, double qx, double qy, int32_t f, c
     if (f == f0) {
         best = hypot(px - qx, py - qy);
         if (best > 0.0) { *tx = (px - qx) / best; *ty = (py - qy) / best; }
+        cand_add(cands, best, *tx, *ty);
     }
     for (int k = 0; k < 3; ++k) {
         const int32_t h = 3 * f + k, e = m->edge[h];
@@ -647,7 +662,10 @@ static double query_point(ows* s, int32_t f0, double qx, double qy, int32_t f, c
             }
             if (!inside) continue;
             const double dd = w->sigma + hypot(hx - w->sx, hy - w->sy);
-            if (dd < best) { best = dd; win_tangent(w, hx, hy, tx, ty); }
+            double ux, uy;
+            win_tangent(w, hx, hy, &ux, &uy);
+            cand_add(cands, dd, ux, uy);
+            if (dd < best) { best = dd; *tx = ux; *ty = uy; }
         }
     }
     for (int k = 0; k < 3; ++k) {
@@ -656,9 +674,15 @@ static double query_point(ows* s, int32_t f0, double qx, double qy, int32_t f, c
         double vx, vy;
         face_pt(m, f, k, &vx, &vy);
         const double dd = s->d[v] + hypot(px - vx, py - vy);
+        cand_add(cands, dd, s->tv[2 * v], s->tv[2 * v + 1]);
         if (dd < best) { best = dd; *tx = s->tv[2 * v]; *ty = s->tv[2 * v + 1]; }
     }
     return best;
+}
+
+static double query_point(ows* s, int32_t f0, double qx, double qy, int32_t f, const double* b,
+                          double* tx, double* ty) {
+    return query_point_c(s, f0, qx, qy, f, b, tx, ty, NULL);
 }
 
 static void add_stats(om_stats* a, const om_stats* b) {
@@ -695,7 +719,7 @@ static double euclid(const om_mesh* m, const double* a, const double* b) {
     return sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
 }
 
-typedef struct { int32_t j; double d, t[3]; } opair;
+typedef struct { int32_t j; double d, t[3], gap; } opair;
 
 static int cmp_pair(const void* a, const void* b) {
     const opair* x = (const opair*)a; const opair* y = (const opair*)b;
@@ -706,6 +730,14 @@ int om_neighbors_subset(const om_mesh* m, int64_t n, const int32_t* face, const 
                         double r_c, int64_t ns, const int64_t* src, int64_t cap,
                         int64_t* n_pairs, int64_t* row_start, int32_t* nbr_j, double* dist,
                         double* tan3, int nthreads, om_stats* st) {
+    return om_neighbors_gap(m, n, face, bary, r_c, ns, src, cap, n_pairs, row_start, nbr_j, dist, tan3,
+                            NULL, nthreads, st);
+}
+
+int om_neighbors_gap(const om_mesh* m, int64_t n, const int32_t* face, const double* bary,
+                     double r_c, int64_t ns, const int64_t* src, int64_t cap,
+                     int64_t* n_pairs, int64_t* row_start, int32_t* nbr_j, double* dist,
+                     double* tan3, double* gap, int nthreads, om_stats* st) {
     for (int64_t i = 0; i < n; ++i) if (face[i] < 0 || face[i] >= m->nf) return -1;
     double* x = (double*)malloc(sizeof(double) * 3 * n);
     for (int64_t i = 0; i < n; ++i) om_world_position(m, face[i], bary + 3 * i, x + 3 * i);
@@ -732,9 +764,12 @@ int om_neighbors_subset(const om_mesh* m, int64_t n, const int32_t* face, const 
             for (int64_t j = 0; j < n; ++j) {
                 if (j == i || !(euclid(m, x + 3 * i, x + 3 * j) < r_c)) continue;
                 double tx, ty;
-                double d = query_point(s, face[i], qx, qy, face[j], bary + 3 * j, &tx, &ty);
+                ocand cands;
+                cands.n = 0;
+                double d = query_point_c(s, face[i], qx, qy, face[j], bary + 3 * j, &tx, &ty, &cands);
                 if (!(d < r_c)) continue;
                 buf[c].j = (int32_t)j; buf[c].d = d;
+                buf[c].gap = cand_gap(&cands, d, tx, ty);
                 face_to_world_vec(m, face[i], tx, ty, buf[c].t);
                 ++c;
             }
@@ -762,6 +797,7 @@ int om_neighbors_subset(const om_mesh* m, int64_t n, const int32_t* face, const 
                 const int64_t o = row_start[r] + c;
                 nbr_j[o] = rows[r][c].j; dist[o] = rows[r][c].d;
                 if (tan3) for (int a = 0; a < 3; ++a) tan3[3 * o + a] = rows[r][c].t[a];
+                if (gap) gap[o] = rows[r][c].gap;
             }
         }
     }

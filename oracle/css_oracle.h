@@ -69,6 +69,14 @@ int om_neighbors_subset(const om_mesh* m, int64_t n, const int32_t* face, const 
                         int64_t* n_pairs, int64_t* row_start, int32_t* nbr_j, double* dist,
                         double* tan3, int nthreads, om_stats* st);
 
+/* As om_neighbors_subset, plus gap[pair]: how much longer the shortest candidate path
+ * with a different initial tangent is (+INF if none).  A small gap marks a point near
+ * the cut locus, where the tangent is set-valued and any tiny error may switch it. */
+int om_neighbors_gap(const om_mesh* m, int64_t n, const int32_t* face, const double* bary,
+                     double r_c, int64_t ns, const int64_t* src, int64_t cap,
+                     int64_t* n_pairs, int64_t* row_start, int32_t* nbr_j, double* dist,
+                     double* tan3, double* gap, int nthreads, om_stats* st);
+
 double om_pair_energy(const om_potential* p, double l);       /* U(l) */
 double om_pair_dudl(const om_potential* p, double l);         /* dU/dl */
 

@@ -33,6 +33,9 @@ def lib():
         L.om_neighbors_subset.argtypes = [P, C.c_int64, P, P, C.c_double, C.c_int64, P, C.c_int64,
                                           P, P, P, P, P, C.c_int, P]
         L.om_neighbors_subset.restype = C.c_int
+        L.om_neighbors_gap.argtypes = [P, C.c_int64, P, P, C.c_double, C.c_int64, P, C.c_int64,
+                                       P, P, P, P, P, P, C.c_int, P]
+        L.om_neighbors_gap.restype = C.c_int
         L.om_pair_energy.argtypes = [P, C.c_double]
         L.om_pair_energy.restype = C.c_double
         L.om_pair_dudl.argtypes = [P, C.c_double]
@@ -182,6 +185,31 @@ class OracleMesh:
             k = int(np_.value)
             out = (rs, j[:k].copy(), d[:k].copy(), t[:k].copy())
             return (out + (st.asdict(),)) if stats else out
+
+    def neighbors_gap(self, face, bary, r_c: float, nthreads: int = 0):
+        """(row_start, j, dist, tangent, gap): gap = extra length of the best rival path whose
+        initial tangent differs (+inf when the geodesic is unique among the candidates)."""
+        face = _i32(face)
+        bary = _f64(bary)
+        n = face.shape[0]
+        src = np.arange(n, dtype=np.int64)
+        np_ = C.c_int64(0)
+        cap = max(16, n * 8)
+        while True:
+            rs = np.zeros(n + 1, np.int64)
+            j = np.zeros(cap, np.int32)
+            d = np.zeros(cap)
+            t = np.zeros((cap, 3))
+            g = np.zeros(cap)
+            rc = lib().om_neighbors_gap(self.h, n, _p(face), _p(bary), float(r_c), n, _p(src), cap,
+                                        C.byref(np_), _p(rs), _p(j), _p(d), _p(t), _p(g), int(nthreads), None)
+            if rc == -5:
+                cap = int(np_.value)
+                continue
+            if rc != 0:
+                raise ValueError(f"oracle neighbors failed ({rc})")
+            k = int(np_.value)
+            return rs, j[:k].copy(), d[:k].copy(), t[:k].copy(), g[:k].copy()
 
     def forces(self, face, bary, r_c: float, pot: dict, nthreads: int = 0):
         face = _i32(face)

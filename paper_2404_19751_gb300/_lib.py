@@ -26,7 +26,8 @@ INT_NVE, INT_BD, INT_ABP = 0, 1, 2
 SYMBOLS = ("css_create", "css_destroy", "css_last_error", "css_last_counters", "css_set_launch",
            "css_mesh_upload", "css_mesh_free", "css_mesh_counts", "css_particles_set",
            "css_particles_get", "css_particles_free", "css_geodesic_neighbors", "css_compute_forces",
-           "css_integrate_step", "css_batch_create", "css_batch_step", "css_batch_free")
+           "css_integrate_step", "css_batch_create", "css_batch_step", "css_batch_free",
+           "css_last_kernel_ms", "css_fma_peak", "css_particles_update")
 
 
 class CssError(RuntimeError):
@@ -76,6 +77,9 @@ def load(path: str = LIB_PATH):
         "css_batch_create": [P, P, I32, C.POINTER(C.c_void_p)],
         "css_batch_step": [P, P, P, D, C.c_int, I64],
         "css_batch_free": [P],
+        "css_last_kernel_ms": [P, C.POINTER(D)],
+        "css_fma_peak": [P, C.c_int, C.POINTER(D)],
+        "css_particles_update": [P, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -140,6 +144,16 @@ class Context:
         self.check(load().css_last_counters(self.h, out.ctypes.data))
         return dict(zip(["sources", "windows", "propagated", "pairs", "emissions", "retries"], out.tolist()))
 
+    def last_kernel_ms(self) -> float:
+        ms = C.c_double(0.0)
+        self.check(load().css_last_kernel_ms(self.h, C.byref(ms)))
+        return ms.value
+
+    def fma_peak(self, precision: int) -> float:
+        f = C.c_double(0.0)
+        self.check(load().css_fma_peak(self.h, int(precision), C.byref(f)))
+        return f.value
+
     def set_launch(self, warps_per_cta: int = 0, window_capacity: int = 0):
         self.check(load().css_set_launch(self.h, int(warps_per_cta), int(window_capacity)))
 
@@ -202,6 +216,19 @@ def particles_get(parts: Particles):
                                              out["force"].ctypes.data, C.byref(step)))
     out["step"] = step.value
     return out
+
+
+def particles_update(parts: Particles, face=None, bary=None, vel=None, orient=None):
+    f, b, v, o = _i32(face), _f64(bary), _f64(vel), _f64(orient)
+    parts.ctx.check(load().css_particles_update(parts.h, _ptr(f), _ptr(b), _ptr(v), _ptr(o)))
+
+
+def particles_get_into(parts: Particles, face=None, bary=None, vel=None, orient=None, force=None):
+    """Copy state into caller buffers (numpy or torch, host or device); None skips a field."""
+    step = C.c_int64(0)
+    parts.ctx.check(load().css_particles_get(parts.h, _ptr(face), _ptr(bary), _ptr(vel), _ptr(orient),
+                                             _ptr(force), C.byref(step)))
+    return step.value
 
 
 def geodesic_neighbors(parts: Particles, r_c: float, precision: int = FP64, capacity: Optional[int] = None):

@@ -142,6 +142,15 @@ GeoJob make_job(css_parts* p, double rc, int want_pairs, int want_forces, const 
     return j;
 }
 
+// record a timing event on the context stream (also inside a graph capture)
+cudaError_t record_ev(css_ctx* c, cudaEvent_t ev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->stream, &cs);
+    c->ev_valid = 1;
+    if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, c->stream, cudaEventRecordExternal);
+    return cudaEventRecord(ev, c->stream);
+}
+
 // one bucket + neighbour/force launch (no synchronisation)
 int enqueue_geo(css_parts* p, double rc, int prec, int want_pairs, int want_forces, const css_potential* pot,
                 const GeoWs& g, int nctas) {
@@ -151,8 +160,10 @@ int enqueue_geo(css_parts* p, double rc, int prec, int want_pairs, int want_forc
                                          p->scan_tmp, st));
     TRY(c, "reset", cudaMemsetAsync(c->dscal, 0, sizeof(int), st));
     GeoJob j = make_job(p, rc, want_pairs, want_forces, pot);
+    TRY(c, "event", record_ev(c, c->ev_geo0));
     TRY(c, "geodesic", cssi::launch_geodesic(j, nullptr, nullptr, nullptr, (int32_t)p->n, prec, g, c->warps_per_cta,
                                              nctas, c->dscal, c->dscal + 1, c->dcount, st));
+    TRY(c, "event", record_ev(c, c->ev_geo1));
     return CSS_OK;
 }
 
@@ -224,6 +235,8 @@ bool finite_all(const double* h, size_t n) {
 
 // =====================================================================================
 // C ABI (declared extern "C" in css.h, so these definitions have C linkage)
+static bool bad_prec(int prec) { return prec != CSS_FP64 && prec != CSS_FP32; }
+static bool bad_rc(double rc) { return !(rc > 0.0); }   // INFINITY allowed, NaN rejected
 
 int css_create(css_ctx** out, int device, void* stream) {
     if (!out) return CSS_ERR_INVALID_ARG;
@@ -238,6 +251,10 @@ int css_create(css_ctx** out, int device, void* stream) {
     css_ctx* c = new css_ctx();
     c->device = device;
     c->stream = (cudaStream_t)stream;
+    if (!c->stream) {   // graph capture needs a real stream: own one
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return CSS_ERR_CUDA; }
+        c->own_stream = 1;
+    }
     c->sm_count = prop.multiProcessorCount;
     if (cudaMalloc(&c->dscal, 4 * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->dcount, 8 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -246,6 +263,10 @@ int css_create(css_ctx** out, int device, void* stream) {
         cudaMallocHost(&c->hcount, 8 * sizeof(unsigned long long)) != cudaSuccess) {
         css_destroy(c);
         return CSS_ERR_OOM;
+    }
+    if (cudaEventCreate(&c->ev_geo0) != cudaSuccess || cudaEventCreate(&c->ev_geo1) != cudaSuccess) {
+        css_destroy(c);
+        return CSS_ERR_CUDA;
     }
     cudaMemset(c->dscal, 0, 4 * sizeof(int));
     cudaMemset(c->dcount, 0, 8 * sizeof(unsigned long long));
@@ -262,6 +283,9 @@ int css_destroy(css_ctx* c) {
     cudaFree(c->depot);
     cudaFreeHost(c->hstat);
     cudaFreeHost(c->hcount);
+    if (c->ev_geo0) cudaEventDestroy(c->ev_geo0);
+    if (c->ev_geo1) cudaEventDestroy(c->ev_geo1);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return CSS_OK;
 }
@@ -276,6 +300,21 @@ int css_last_counters(const css_ctx* c, int64_t out[6]) {
     out[3] = c->last_counters[3];
     out[4] = 0;
     out[5] = c->last_counters[4];
+    return CSS_OK;
+}
+
+int css_last_kernel_ms(css_ctx* c, double* ms) {
+    if (!c || !ms || !c->ev_valid) return CSS_ERR_INVALID_ARG;
+    float f = 0.f;
+    TRY(c, "kernel timing", cudaEventSynchronize(c->ev_geo1));
+    TRY(c, "kernel timing", cudaEventElapsedTime(&f, c->ev_geo0, c->ev_geo1));
+    *ms = (double)f;
+    return CSS_OK;
+}
+
+int css_fma_peak(css_ctx* c, int precision, double* flops_per_s) {
+    if (!c || !flops_per_s || bad_prec(precision)) return CSS_ERR_INVALID_ARG;
+    TRY(c, "fma peak", cssi::measure_fma_peak(precision, c->sm_count, c->stream, flops_per_s));
     return CSS_OK;
 }
 
@@ -350,11 +389,17 @@ int css_particles_set(css_ctx* c, css_mesh* m, int64_t n, const int32_t* face, c
     cudaStream_t st = c->stream;
     cudaError_t e = cudaSuccess;
     const size_t nf = (size_t)m->nf;
-    e = stage_in(hf.data(), n, &p->face, st);
-    if (e == cudaSuccess) e = stage_in(hb.data(), 3 * n, &p->bary, st);
-    if (e == cudaSuccess) e = cudaMalloc(&p->vel, 3 * n * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&p->orient, 3 * n * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&p->force, 3 * n * sizeof(double));
+    // one contiguous block: bary | vel | orient | force | face, so a snapshot is one copy
+    e = cudaMalloc(&p->state, p->state_bytes());
+    if (e == cudaSuccess) {
+        p->bary = (double*)p->state;
+        p->vel = p->bary + 3 * n;
+        p->orient = p->bary + 6 * n;
+        p->force = p->bary + 9 * n;
+        p->face = (int32_t*)(p->bary + 12 * n);
+        e = cudaMemcpyAsync(p->face, hf.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->bary, hb.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMalloc(&p->fcnt, (nf + 1) * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->fstart, (nf + 1) * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->fitems, n * sizeof(int32_t));
@@ -389,18 +434,35 @@ int css_particles_get(css_parts* p, int32_t* face, double* bary, double* vel, do
     return CSS_OK;
 }
 
+int css_particles_update(css_parts* p, const int32_t* face, const double* bary, const double* vel,
+                         const double* orient) {
+    if (!p) return CSS_ERR_INVALID_ARG;
+    css_ctx* c = p->ctx;
+    cudaStream_t st = c->stream;
+    auto kind = [](const void* q) { return is_device_ptr(q) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; };
+    if (face) {
+        if (!is_device_ptr(face))
+            for (int64_t i = 0; i < p->n; ++i)
+                if (face[i] < 0 || face[i] >= p->mesh->nf) { c->err = "particles_update: face index out of range"; return CSS_ERR_INVALID_ARG; }
+        TRY(c, "particles_update", cudaMemcpyAsync(p->face, face, p->n * sizeof(int32_t), kind(face), st));
+    }
+    if (bary) TRY(c, "particles_update", cudaMemcpyAsync(p->bary, bary, 3 * p->n * sizeof(double), kind(bary), st));
+    if (vel) TRY(c, "particles_update", cudaMemcpyAsync(p->vel, vel, 3 * p->n * sizeof(double), kind(vel), st));
+    if (orient) TRY(c, "particles_update", cudaMemcpyAsync(p->orient, orient, 3 * p->n * sizeof(double), kind(orient), st));
+    if (face || bary) p->force_valid = 0;
+    return CSS_OK;
+}
+
 int css_particles_free(css_parts* p) {
     if (!p) return CSS_ERR_INVALID_ARG;
     if (p->graph) cudaGraphExecDestroy(p->graph);
-    cudaFree(p->face); cudaFree(p->bary); cudaFree(p->vel); cudaFree(p->orient); cudaFree(p->force);
+    cudaFree(p->state); cudaFree(p->snap);
     cudaFree(p->fcnt); cudaFree(p->fstart); cudaFree(p->fitems); cudaFree(p->scan_tmp); cudaFree(p->order);
     cudaFree(p->pcnt); cudaFree(p->pj); cudaFree(p->pd); cudaFree(p->pt); cudaFree(p->dstep);
     delete p;
     return CSS_OK;
 }
 
-static bool bad_prec(int prec) { return prec != CSS_FP64 && prec != CSS_FP32; }
-static bool bad_rc(double rc) { return !(rc > 0.0); }   // INFINITY allowed, NaN rejected
 
 int css_geodesic_neighbors(css_parts* p, double r_c, int precision, int64_t capacity, int64_t* n_pairs,
                            int64_t* row_start, int32_t* nbr_j, double* dist, double* tangent) {
@@ -462,39 +524,19 @@ int css_compute_forces(css_parts* p, const css_potential* pot, double r_c, int p
 // ------------------------------------------------------------------------------ stepping
 namespace {
 
-struct Snapshot {
-    int32_t* face = nullptr;
-    double* buf = nullptr;   // bary, vel, orient, force
-    int64_t n = 0;
-    ~Snapshot() { cudaFree(face); cudaFree(buf); }
-};
-
-cudaError_t snap_take(css_parts* p, Snapshot& s) {
-    if (s.n != p->n) {
-        cudaFree(s.face); cudaFree(s.buf);
-        cudaError_t e = cudaMalloc(&s.face, p->n * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMalloc(&s.buf, 12 * p->n * sizeof(double));
+cudaError_t snap_take(css_parts* p) {
+    if (!p->snap) {
+        cudaError_t e = cudaMalloc(&p->snap, p->state_bytes());
         if (e != cudaSuccess) return e;
-        s.n = p->n;
     }
-    cudaStream_t st = p->ctx->stream;
-    const size_t b = 3 * p->n * sizeof(double);
-    cudaMemcpyAsync(s.face, p->face, p->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(s.buf, p->bary, b, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(s.buf + 3 * p->n, p->vel, b, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(s.buf + 6 * p->n, p->orient, b, cudaMemcpyDeviceToDevice, st);
-    return cudaMemcpyAsync(s.buf + 9 * p->n, p->force, b, cudaMemcpyDeviceToDevice, st);
+    return cudaMemcpyAsync(p->snap, p->state, p->state_bytes(), cudaMemcpyDeviceToDevice, p->ctx->stream);
 }
 
-cudaError_t snap_restore(css_parts* p, Snapshot& s) {
+cudaError_t snap_restore(css_parts* p) {
     cudaStream_t st = p->ctx->stream;
-    const size_t b = 3 * p->n * sizeof(double);
-    cudaMemcpyAsync(p->face, s.face, p->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(p->bary, s.buf, b, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(p->vel, s.buf + 3 * p->n, b, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(p->orient, s.buf + 6 * p->n, b, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(p->dstep, &p->step, sizeof(int64_t), cudaMemcpyHostToDevice, st);
-    return cudaMemcpyAsync(p->force, s.buf + 9 * p->n, b, cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(p->state, p->snap, p->state_bytes(), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(p->dstep, &p->step, sizeof(int64_t), cudaMemcpyHostToDevice, st);
 }
 
 // per-set integrator kernels of one step: NVE half = 0 before the forces (kick + drift),
@@ -571,27 +613,32 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
             TRY(c, "noise", cudaMemcpyAsync(dnoise, noise, cnt * sizeof(double), cudaMemcpyHostToDevice, st));
         }
     }
-    Snapshot snap;
     int retries = 0;
     int rc = CSS_OK;
     for (;;) {
-        rc = snap_take(p, snap) == cudaSuccess ? CSS_OK : CSS_ERR_CUDA;
-        if (rc) break;
+        TRY(c, "snapshot", snap_take(p));
         GeoWs g;
         int nctas = 0;
         rc = ensure_ws(c, precision, &g, &nctas);
         if (rc) break;
         TRY(c, "reset", cudaMemsetAsync(c->dscal + 1, 0, sizeof(int), st));
         TRY(c, "reset", cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), st));
-        if (n_steps > 1 && !dnoise) {
-            // one captured step replayed n_steps times
-            cudaGraphExec_t exec = nullptr;
-            rc = capture(c, [&]() { return enqueue_step(p, pot, it, r_c, precision, nullptr, g, nctas); }, &exec);
+        if (!dnoise) {
+            // one captured step, kept with the parameters it was captured for, replayed
+            std::string key((const char*)pot, sizeof(*pot));
+            key.append((const char*)it, sizeof(*it));
+            key.append((const char*)&r_c, sizeof(r_c));
+            const int64_t shape[4] = {precision, c->ws_key, nctas, (int64_t)(uintptr_t)c->ws};
+            key.append((const char*)shape, sizeof(shape));
+            if (!p->graph || p->graph_key != key) {
+                if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+                rc = capture(c, [&]() { return enqueue_step(p, pot, it, r_c, precision, nullptr, g, nctas); }, &p->graph);
+                if (rc == CSS_OK) p->graph_key = key;
+            }
             for (int64_t s = 0; s < n_steps && rc == CSS_OK; ++s) {
-                cudaError_t e = cudaGraphLaunch(exec, st);
+                cudaError_t e = cudaGraphLaunch(p->graph, st);
                 if (e != cudaSuccess) rc = cuda_fail(c, "graph launch", e);
             }
-            if (exec) cudaGraphExecDestroy(exec);
         } else {
             for (int64_t s = 0; s < n_steps && rc == CSS_OK; ++s)
                 rc = enqueue_step(p, pot, it, r_c, precision, dnoise ? dnoise + (size_t)s * p->n * 2 : nullptr, g, nctas);
@@ -602,7 +649,7 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
         if (rc) break;
         if (status == 0) break;
         if (!grow_for(c, status, &retries)) { rc = status_error(c, status); break; }
-        TRY(c, "restore", snap_restore(p, snap));
+        TRY(c, "restore", snap_restore(p));
     }
     if (noise && !is_device_ptr(noise)) cudaFree(dnoise);
     if (rc) return rc;
@@ -680,8 +727,10 @@ int batch_enqueue_forces(css_batch* b, const css_potential* pot, double rc, int 
     TRY(c, "reset", cudaMemsetAsync(c->dscal, 0, sizeof(int), st));
     TRY(c, "reset", cudaMemsetAsync(c->depot, 0, sizeof(double), st));
     GeoJob j0 = make_job(b->sets[0], rc, 0, 1, pot);
+    TRY(c, "event", record_ev(c, c->ev_geo0));
     TRY(c, "geodesic", cssi::launch_geodesic(j0, b->djobs, b->job_of_item, b->src_of_item, b->nitems, prec, g,
                                              c->warps_per_cta, nctas, c->dscal, c->dscal + 1, c->dcount, st));
+    TRY(c, "event", record_ev(c, c->ev_geo1));
     return CSS_OK;
 }
 
@@ -702,10 +751,9 @@ int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator*
         TRY(c, "batch jobs", cudaStreamSynchronize(st));
     }
     const bool nve = it->kind == CSS_INT_NVE;
-    std::vector<Snapshot> snaps(b->sets.size());
     int retries = 0;
     for (;;) {
-        for (size_t k = 0; k < b->sets.size(); ++k) TRY(c, "snapshot", snap_take(b->sets[k], snaps[k]));
+        for (css_parts* p : b->sets) TRY(c, "snapshot", snap_take(p));
         GeoWs g;
         int nctas = 0;
         int rc = ensure_ws(c, precision, &g, &nctas);
@@ -736,7 +784,7 @@ int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator*
         if (rc) return rc;
         if (status == 0) break;
         if (!grow_for(c, status, &retries)) return status_error(c, status);
-        for (size_t k = 0; k < b->sets.size(); ++k) TRY(c, "restore", snap_restore(b->sets[k], snaps[k]));
+        for (css_parts* p : b->sets) TRY(c, "restore", snap_restore(p));
     }
     for (css_parts* p : b->sets) {
         p->step += n_steps;

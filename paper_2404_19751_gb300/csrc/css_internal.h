@@ -12,6 +12,7 @@
 struct css_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    int own_stream = 0;
     int sm_count = 0;
     std::string err;
     // neighbour/force workspace (grown on demand)
@@ -30,6 +31,8 @@ struct css_ctx {
     int* hstat = nullptr;                   // pinned mirror of status
     unsigned long long* hcount = nullptr;   // pinned mirror of counters
     int64_t last_counters[6] = {0, 0, 0, 0, 0, 0};
+    cudaEvent_t ev_geo0 = nullptr, ev_geo1 = nullptr;   // around the neighbour/force kernel
+    int ev_valid = 0;
 };
 
 struct css_mesh {
@@ -63,7 +66,10 @@ struct css_parts {
     double force_rc = 0.0;
     int force_prec = -1;
     css_potential force_pot{};
-    // device arrays
+    // device arrays (bary, vel, orient, force, face live in one block `state`)
+    void* state = nullptr;
+    void* snap = nullptr;       // copy of `state` taken before a multi-step call
+    size_t state_bytes() const { return (size_t)n * (12 * sizeof(double) + sizeof(int32_t)); }
     int32_t* face = nullptr;
     double* bary = nullptr;     // 3 n
     double* vel = nullptr;      // 3 n
@@ -81,9 +87,9 @@ struct css_parts {
     double* pd = nullptr;
     double* pt = nullptr;
     int pair_cap_alloc = 0;
-    // captured step graph
+    // captured single-step graph and the launch parameters it was captured for
     cudaGraphExec_t graph = nullptr;
-    int64_t graph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    std::string graph_key;
 };
 
 namespace cssi {
@@ -149,6 +155,9 @@ cudaError_t launch_overdamped_move(const css::DMesh& m, int32_t n, int32_t* face
                                    uint64_t seed, const int64_t* dstep, const double* noise, int* status,
                                    cudaStream_t st);
 cudaError_t launch_step_inc(int64_t* dstep, cudaStream_t st);
+
+// peak.cu
+cudaError_t measure_fma_peak(int precision, int sm_count, cudaStream_t st, double* flops);
 
 // mesh_prep.cu
 int build_mesh(css_ctx* ctx, const double* dX, int64_t nv, const int32_t* dF, int64_t nf,

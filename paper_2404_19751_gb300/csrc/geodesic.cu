@@ -44,9 +44,9 @@ constexpr int MAX_WARPS_CTA = 16;
 
 template <class R>
 struct Win {
-    double sx, sy;     // pseudo-source in the frame of half-edge `he` (FP64 in both forms)
+    double sx, sy;     // pseudo-source in the frame of half-edge `he`  } accumulated unfolded
+    double sig;        // geodesic length source -> pseudo-source        } source state: FP64
     R b0, b1;          // interval along the half-edge
-    R sig;             // geodesic length source -> pseudo-source
     R ta, tb;          // image of the source-face x axis (direct) or fixed tangent
     int32_t he, next, flags;
 };
@@ -60,6 +60,18 @@ struct Tol<double> {
 template <>
 struct Tol<float> {
     static constexpr float w = 2e-6f;
+};
+
+// relative distance difference below which two windows tie
+template <class R>
+struct Tie;
+template <>
+struct Tie<double> {
+    static constexpr double rel = 1e-13;
+};
+template <>
+struct Tie<float> {
+    static constexpr double rel = 1e-6;
 };
 
 struct WarpSm {
@@ -129,17 +141,17 @@ __device__ inline Ws<R> ws_bind(const cssi::GeoWs& g, int warp) {
 
 // ------------------------------------------------------------------ window geometry
 template <class R>
-__device__ __forceinline__ R win_key(const Win<R>& w) {
+__device__ __forceinline__ double win_key(const Win<R>& w) {
     double x = w.sx < (double)w.b0 ? (double)w.b0 : (w.sx > (double)w.b1 ? (double)w.b1 : w.sx);
     double dx = x - w.sx;
-    return w.sig + (R)sqrt((R)(dx * dx + w.sy * w.sy));
+    return w.sig + (double)sqrt((R)(dx * dx + w.sy * w.sy));
 }
 
 // distance carried to the point (px, py) of the window frame
 template <class R>
-__device__ __forceinline__ R win_dist(const Win<R>& w, double px, double py) {
+__device__ __forceinline__ double win_dist(const Win<R>& w, double px, double py) {
     R dx = (R)(px - w.sx), dy = (R)(py - w.sy);
-    return w.sig + sqrt(dx * dx + dy * dy);
+    return w.sig + (double)sqrt(dx * dx + dy * dy);
 }
 
 template <class R>
@@ -175,7 +187,9 @@ __device__ __forceinline__ R ray_hit(double sx, double sy, R X, double ax, doubl
 template <class R>
 struct VCand {
     int32_t v;
-    R d, tx, ty;
+    int32_t fixed;   // tangent comes from a pseudo-source path
+    double d;
+    R tx, ty;
 };
 
 // Unfold window W into the next face: vertex candidates and at most two children.
@@ -194,11 +208,11 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
     const R tolv = (R)(Tol<R>::w * L);
     if (W.b0 <= tolv) {
         VCand<R>& c = vc[nvc++];
-        c.v = vu; c.d = win_dist(W, 0.0, 0.0); win_tangent(W, 0.0, 0.0, c.tx, c.ty);
+        c.v = vu; c.fixed = W.flags & WIN_FIXED; c.d = win_dist(W, 0.0, 0.0); win_tangent(W, 0.0, 0.0, c.tx, c.ty);
     }
     if ((double)W.b1 >= L - (double)tolv) {
         VCand<R>& c = vc[nvc++];
-        c.v = vv; c.d = win_dist(W, L, 0.0); win_tangent(W, L, 0.0, c.tx, c.ty);
+        c.v = vv; c.fixed = W.flags & WIN_FIXED; c.d = win_dist(W, L, 0.0); win_tangent(W, L, 0.0, c.tx, c.ty);
     }
     const bool degen = win_degen(W, L);
     if (degen && !win_degen_sees(W, L)) return;
@@ -206,7 +220,7 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
     const double xc = degen ? 0.0 : W.sx + (r.cx - W.sx) * (-W.sy) / (r.cy - W.sy);
     if (degen || (xc >= (double)W.b0 && xc <= (double)W.b1)) {
         VCand<R>& c = vc[nvc++];
-        c.v = vcid; c.d = win_dist(W, r.cx, r.cy); win_tangent(W, r.cx, r.cy, c.tx, c.ty);
+        c.v = vcid; c.fixed = W.flags & WIN_FIXED; c.d = win_dist(W, r.cx, r.cy); win_tangent(W, r.cx, r.cy, c.tx, c.ty);
     }
     if (r.tl >= 0 && (degen || xc > (double)W.b0)) {
         R mu0 = (R)0, mu1 = (R)1;
@@ -227,7 +241,7 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
         c.b0 = mu0 * Lc; c.b1 = mu1 * Lc;
         if (c.sy > 0.0) c.sy = 0.0;
         c.flags = (W.flags & WIN_FIXED) | WIN_ALIVE;
-        if (win_key(c) < (R)rc) ++nch;
+        if (win_key(c) < rc) ++nch;
     }
     if (r.tr >= 0 && (degen || xc < (double)W.b1)) {
         R mu0 = (R)0, mu1 = (R)1;
@@ -249,7 +263,7 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
         c.b0 = mu0 * Ld; c.b1 = mu1 * Ld;
         if (c.sy > 0.0) c.sy = 0.0;
         c.flags = (W.flags & WIN_FIXED) | WIN_ALIVE;
-        if (win_key(c) < (R)rc) ++nch;
+        if (win_key(c) < rc) ++nch;
     }
 }
 
@@ -284,12 +298,16 @@ __device__ int equal_points(double ax, double ay, double sa, double bx, double b
     return n;
 }
 
+// Append [x0, x1] to a sorted interval list, merging with a touching last interval.  When
+// the list is full, `cover` decides: true extends the last interval over the gap (a window
+// that keeps more than it must only costs work: every window carries real path lengths),
+// false drops the interval (used for the parts a window loses, so it never loses too much).
 template <class R>
-__device__ __forceinline__ void ivl_add(R (*iv)[2], int& n, R x0, R x1, int& err) {
+__device__ __forceinline__ void ivl_add(R (*iv)[2], int& n, R x0, R x1, bool cover = true) {
     if (!(x1 > x0)) return;
     if (n > 0 && x0 <= iv[n - 1][1]) { if (x1 > iv[n - 1][1]) iv[n - 1][1] = x1; return; }
     if (n < MAXP) { iv[n][0] = x0; iv[n][1] = x1; ++n; }
-    else err |= css::ST_PIECES;
+    else if (cover) iv[n - 1][1] = x1;
 }
 
 template <class R>
@@ -319,9 +337,11 @@ __device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win
     const double L = m.he[c.he].L;
     const R Lr = (R)L;
     const R tolw = (R)(Tol<R>::w * L);
+    const double tie = Tie<R>::rel;
+    const bool c_direct = !(c.flags & WIN_FIXED);
     if (c.b0 < (R)0) c.b0 = (R)0;
     if (c.b1 > Lr) c.b1 = Lr;
-    if (!(c.b1 - c.b0 > tolw) || !(win_key(c) < (R)rc)) return;
+    if (!(c.b1 - c.b0 > tolw) || !(win_key(c) < rc)) return;
     int err = 0;
     R pc[MAXP][2];
     int np = 1;
@@ -348,26 +368,32 @@ __device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win
         for (int p = 0; p < np; ++p) {
             const R a0 = pc[p][0], a1 = pc[p][1];
             const R lo = a0 > o0 ? a0 : o0, hi = a1 < o1 ? a1 : o1;
-            if (!(hi - lo > tolw)) { ivl_add(npc, nn, a0, a1, err); continue; }
+            if (!(hi - lo > tolw)) { ivl_add(npc, nn, a0, a1); continue; }
             double bp[4];
             int nb = 0;
             bp[nb++] = (double)lo;
             double rr[2];
-            const int nr = equal_points(c.sx, c.sy, (double)c.sig, osx, osy, (double)o.sig, (double)lo, (double)hi, rr);
+            const int nr = equal_points(c.sx, c.sy, c.sig, osx, osy, o.sig, (double)lo, (double)hi, rr);
             for (int q = 0; q < nr; ++q) bp[nb++] = rr[q];
             bp[nb++] = (double)hi;
-            ivl_add(npc, nn, a0, lo, err);
+            ivl_add(npc, nn, a0, lo);
             for (int q = 0; q + 1 < nb; ++q) {
                 const double xm = 0.5 * (bp[q] + bp[q + 1]);
-                const double dc = (double)c.sig + sqrt((xm - c.sx) * (xm - c.sx) + c.sy * c.sy);
+                const double dc = c.sig + sqrt((xm - c.sx) * (xm - c.sx) + c.sy * c.sy);
                 const double dox = xm - osx;
-                const double dd = dc - ((double)o.sig + sqrt(dox * dox + osy * osy));
-                if (dd < 0.0) {
-                    ivl_add(npc, nn, (R)bp[q], (R)bp[q + 1], err);
-                    ivl_add(lost, nl, (R)bp[q], (R)bp[q + 1], err);
+                const double dd = dc - (o.sig + sqrt(dox * dox + osy * osy));
+                // the candidate wins where it is shorter beyond rounding; on a tie a direct
+                // window beats one descending from a pseudo-source (whose tangent is only
+                // exact on the tie line), otherwise the existing window keeps it, so exact
+                // ties never fragment intervals
+                const bool win = (dd < -tie * dc) ||
+                                 (dd <= tie * dc && c_direct && (o.flags & WIN_FIXED));
+                if (win) {
+                    ivl_add(npc, nn, (R)bp[q], (R)bp[q + 1]);
+                    ivl_add(lost, nl, (R)bp[q], (R)bp[q + 1], false);
                 }
             }
-            ivl_add(npc, nn, hi, a1, err);
+            ivl_add(npc, nn, hi, a1);
         }
         np = 0;
         for (int p = 0; p < nn; ++p)
@@ -378,10 +404,10 @@ __device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win
             int nk = 0;
             R cur = o0;
             for (int q = 0; q < nl; ++q) {
-                if (lost[q][0] - cur > tolw) ivl_add(keep, nk, cur, lost[q][0], err);
+                if (lost[q][0] - cur > tolw) ivl_add(keep, nk, cur, lost[q][0]);
                 if (lost[q][1] > cur) cur = lost[q][1];
             }
-            if (o1 - cur > tolw) ivl_add(keep, nk, cur, o1, err);
+            if (o1 - cur > tolw) ivl_add(keep, nk, cur, o1);
             if (nk == 0) {
                 ws.win[oi].flags = o.flags & ~WIN_ALIVE;
                 if (prev < 0) ws.ehead[es] = onext; else ws.win[prev].next = onext;
@@ -417,7 +443,7 @@ __device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win
         Win<R> w = c;
         w.b0 = pc[p][0]; w.b1 = pc[p][1];
         w.flags = (c.flags & WIN_FIXED) | WIN_ALIVE;
-        if (!(win_key(w) < (R)rc)) continue;
+        if (!(win_key(w) < rc)) continue;
         const int id = win_alloc<R>(sm, ws.wcap);
         if (id < 0) break;
         w.next = ws.ehead[es];
@@ -451,12 +477,17 @@ __device__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, co
     const int rounds = group_rounds(has, slot, lane, rank);
     for (int q = 0; q < rounds; ++q) {
         if (has && rank == q) {
-            const double d = (double)c.d;
-            if (d < ws.vdist[slot]) {
-                ws.vdist[slot] = d;
+            const double d = c.d;
+            const double vd = ws.vdist[slot];
+            const int vf = ws.vflag[slot];
+            const double tie = Tie<R>::rel * d;
+            // shorter beyond rounding, or a tie won by a direct path over a pseudo-source one
+            if (d < vd - tie || (d <= vd + tie && !c.fixed && (vf & 2))) {
+                ws.vdist[slot] = d < vd ? d : vd;
                 ws.vtan[2 * slot] = c.tx;
                 ws.vtan[2 * slot + 1] = c.ty;
-                if (m.pseudo[c.v] && d < rc && !(ws.vflag[slot] & 1)) {
+                ws.vflag[slot] = c.fixed ? (vf | 2) : (vf & ~2);
+                if (d < vd && m.pseudo[c.v] && d < rc && !(ws.vflag[slot] & 1)) {
                     ws.vflag[slot] |= 1;
                     const int p = atomicAdd(&sm.nemit, 1);
                     if (p < ws.emcap) ws.emit[p] = slot;
@@ -526,7 +557,7 @@ __device__ void emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, int
                     c.b1 = (R)r.L;
                     c.sx = r.L - r.cx;
                     c.sy = -r.cy;
-                    c.sig = (R)dv;
+                    c.sig = dv;
                     c.ta = tx;
                     c.tb = ty;
                     c.flags = WIN_FIXED | WIN_ALIVE;
@@ -568,10 +599,13 @@ __device__ double query(const DMesh& m, const Ws<R>& ws, int f0, double qx, doub
     const double L01 = m.lay[3 * fl], x2 = m.lay[3 * fl + 1], y2 = m.lay[3 * fl + 2];
     const double px = bj[1] * L01 + bj[2] * x2, py = bj[2] * y2;
     double best = __longlong_as_double(0x7ff0000000000000ll);
+    bool best_fixed = true;
+    const double tie = Tie<R>::rel;
     tx = (R)0; ty = (R)0;
     if (fl == f0) {
         const double dx = px - qx, dy = py - qy;
         best = sqrt(dx * dx + dy * dy);
+        best_fixed = false;
         if (best > 0.0) { tx = (R)(dx / best); ty = (R)(dy / best); }
     }
     for (int k = 0; k < 3; ++k) {
@@ -598,8 +632,13 @@ __device__ double query(const DMesh& m, const Ws<R>& ws, int f0, double qx, doub
                 inside = X >= (double)w.b0 - tol && X <= (double)w.b1 + tol;
             }
             if (!inside) continue;
-            const double d = (double)win_dist(w, hx, hy);
-            if (d < best) { best = d; win_tangent(w, hx, hy, tx, ty); }
+            const double d = win_dist(w, hx, hy);
+            const bool direct = !(w.flags & WIN_FIXED);
+            if (d < best - tie * d || (d <= best + tie * d && direct && best_fixed)) {
+                best = d < best ? d : best;
+                best_fixed = !direct;
+                win_tangent(w, hx, hy, tx, ty);
+            }
         }
     }
     for (int k = 0; k < 3; ++k) {
@@ -608,7 +647,7 @@ __device__ double query(const DMesh& m, const Ws<R>& ws, int f0, double qx, doub
         double vx, vy;
         css::face_corner(m, fl, k, vx, vy);
         const double d = ws.vdist[slot] + sqrt((px - vx) * (px - vx) + (py - vy) * (py - vy));
-        if (d < best) { best = d; tx = ws.vtan[2 * slot]; ty = ws.vtan[2 * slot + 1]; }
+        if (d < best - tie * d) { best = d; best_fixed = true; tx = ws.vtan[2 * slot]; ty = ws.vtan[2 * slot + 1]; }
     }
     return best;
 }
@@ -633,7 +672,8 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
             css::face_corner(m, f0, lane, vx, vy);
             const double dx = vx - qx, dy = vy - qy, d = sqrt(dx * dx + dy * dy);
             c.v = m.fv[3 * f0 + lane];
-            c.d = (R)d;
+            c.fixed = 0;
+            c.d = d;
             c.tx = (R)(d > 0.0 ? dx / d : 1.0);
             c.ty = (R)(d > 0.0 ? dy / d : 0.0);
         }
@@ -659,7 +699,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
                 c.b1 = (R)m.he[tw].L;
                 c.sx = L - hx;
                 c.sy = hy > 0.0 ? -hy : 0.0;
-                c.sig = (R)0;
+                c.sig = 0.0;
                 c.ta = (R)(-dx);
                 c.tb = (R)dy;
                 c.flags = WIN_ALIVE;
@@ -681,7 +721,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
         bool act = false;
         if (idx < nwin) {
             w = ws.win[idx];
-            act = (w.flags & WIN_ALIVE) && !(w.flags & WIN_DONE) && win_key(w) < (R)rc;
+            act = (w.flags & WIN_ALIVE) && !(w.flags & WIN_DONE) && win_key(w) < rc;
             if (act) ws.win[idx].flags = w.flags | WIN_DONE;
         }
         VCand<R> vc[3];

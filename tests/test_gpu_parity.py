@@ -63,7 +63,7 @@ def test_neighbors_fp64_match_oracle(ctx, name):
     m, face, bary, r_c = WORKLOADS[name]()
     mesh, parts = _setup(ctx, m, face, bary)
     g = css.geodesic_neighbors(parts, r_c, css.FP64)
-    r = O.OracleMesh(m).neighbors(face, bary, r_c)
+    r = O.OracleMesh(m).neighbors_gap(face, bary, r_c)
     n, md, mt = compare_pairs(g, r, r_c, FP64_RTOL, 1e-7)
     assert n > 0
     parts.free()
@@ -76,8 +76,10 @@ def test_neighbors_fp32_within_tolerance(ctx, name):
     mesh, parts = _setup(ctx, m, face, bary)
     diam = synth.bbox_diagonal(m)
     g = css.geodesic_neighbors(parts, r_c, css.FP32)
-    r = O.OracleMesh(m).neighbors(face, bary, r_c)
-    compare_pairs(g, r, r_c, FP32_REL_DIAM * diam, 1e-3, rel=False, band=FP32_REL_DIAM * diam)
+    r = O.OracleMesh(m).neighbors_gap(face, bary, r_c)
+    # tangents are compared except within the FP32 length tolerance of a cut-locus tie
+    tol = FP32_REL_DIAM * diam
+    compare_pairs(g, r, r_c, tol, 1e-4, rel=False, band=tol, tie=tol)
     parts.free()
     mesh.free()
 
@@ -100,11 +102,12 @@ def test_tiny_meshes_all_pairs(ctx, name, make):
     mesh, parts = _setup(ctx, m, face, bary)
     for prec, tol in ((css.FP64, FP64_RTOL), (css.FP32, None)):
         g = css.geodesic_neighbors(parts, math.inf, prec)
-        r = O.OracleMesh(m).neighbors(face, bary, math.inf)
+        r = O.OracleMesh(m).neighbors_gap(face, bary, math.inf)
         if prec == css.FP64:
             compare_pairs(g, r, math.inf, tol, 1e-7)
         else:
-            compare_pairs(g, r, math.inf, FP32_REL_DIAM * synth.bbox_diagonal(m), 1e-3, rel=False)
+            t32 = FP32_REL_DIAM * synth.bbox_diagonal(m)
+            compare_pairs(g, r, math.inf, t32, 1e-4, rel=False, tie=t32)
     parts.free()
     mesh.free()
 
@@ -119,7 +122,11 @@ def test_sources_on_vertices_and_edges(ctx):
     mesh, parts = _setup(ctx, m, face, bary)
     g = css.geodesic_neighbors(parts, 0.6, css.FP64)
     r = O.OracleMesh(m).neighbors(face, bary, 0.6)
-    compare_pairs(g, r, 0.6, FP64_RTOL, 1e-6)
+    # distances everywhere; tangents only for sources off the vertices (at a vertex the
+    # tangent plane is a cone and the direction in the source face's plane is set-valued)
+    compare_pairs(g, r, 0.6, FP64_RTOL, 2.0)
+    off = lambda c: (c[0][10:] - c[0][10], c[1][c[0][10]:], c[2][c[0][10]:], c[3][c[0][10]:])
+    compare_pairs(off(g), off(r), 0.6, FP64_RTOL, 1e-6)
     parts.free()
     mesh.free()
 
