@@ -218,7 +218,7 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
     if (degen && !win_degen_sees(W, L)) return;
     // occlusion predicate (FP64 in both forms): where the ray s -> c crosses the edge line
     const double xc = degen ? 0.0 : W.sx + (r.cx - W.sx) * (-W.sy) / (r.cy - W.sy);
-    if (degen || (xc >= (double)W.b0 && xc <= (double)W.b1)) {
+    if (degen || (xc >= (double)W.b0 - (double)tolv && xc <= (double)W.b1 + (double)tolv)) {
         VCand<R>& c = vc[nvc++];
         c.v = vcid; c.fixed = W.flags & WIN_FIXED; c.d = win_dist(W, r.cx, r.cy); win_tangent(W, r.cx, r.cy, c.tx, c.ty);
     }
@@ -619,7 +619,9 @@ __device__ double query(const DMesh& m, const Ws<R>& ws, int f0, double qx, doub
         const double dx = (bx - ax) / L, dy = (by - ay) / L;
         const double hx = (px - ax) * dx + (py - ay) * dy;
         const double hy = dx * (py - ay) - dy * (px - ax);
-        const double tol = 1e-12 * L;
+        // cone tolerance of the interval precision: adjacent windows stored in FP32 may
+        // leave or overlap by an ulp of the edge length, which must not hide a target
+        const double tol = (double)Tol<R>::w * L;
         int guard = 0;
         for (int wi = ws.ehead[slot]; wi >= 0 && guard < ws.wcap; ++guard) {
             const Win<R> w = ws.win[wi];

@@ -15,12 +15,26 @@ def csr_to_dict(rs, j, d, t):
     return out
 
 
-def compare_pairs(gpu, ref, r_c, dist_tol, tan_tol, rel=True, band=None, tie=None):
+def geodesic_walker(om, face, bary):
+    """Landing error of a straightest walk from particle i along tangent t for length d, to
+    particle j: a tangent is a valid answer iff it starts a geodesic of that length to j."""
+    x = om.world(face, bary)
+
+    def walk(i, j, d, t):
+        f2, b2, _, _ = om.shift(int(face[i]), bary[i], d * np.asarray(t), None)
+        return float(np.linalg.norm(om.world([f2], [b2])[0] - x[j]))
+    return walk
+
+
+def compare_pairs(gpu, ref, r_c, dist_tol, tan_tol, rel=True, band=None, tie=None, walker=None,
+                  land_tol=None):
     """Compare two CSR neighbour sets.  Pairs within `band` of the cutoff may be missing on
     either side.  When ref carries a fifth array (the oracle's tie gap), tangents of pairs
     whose rival geodesic is within `tie` (absolute length) are not compared: at such
     cut-locus points the tangent is set-valued.  Returns (n_compared, max_dist_err,
-    max_tan_err)."""
+    max_tan_err).  With `walker`, a tangent that differs from the reference by more than
+    tan_tol is still accepted when the walk along it lands within land_tol of the target:
+    the pair then lies on the cut locus, where several geodesics of equal length exist."""
     G = csr_to_dict(*gpu)
     R = csr_to_dict(*ref[:4])
     gap = {}
@@ -43,8 +57,13 @@ def compare_pairs(gpu, ref, r_c, dist_tol, tan_tol, rel=True, band=None, tie=Non
         md = max(md, err)
         tie_k = tie if tie is not None else (1e-12 * dr)
         if gap.get(k, math.inf) > tie_k:
-            mt = max(mt, float(np.linalg.norm(tg - tr)))
+            e = float(np.linalg.norm(tg - tr))
+            if e > tan_tol and walker is not None and walker(k[0], k[1], dg, tg) <= land_tol:
+                e = 0.0     # a different, equally valid geodesic
+            if e > mt:
+                mt, worst = e, (k, dg, dr, gap.get(k, math.inf))
         n += 1
     assert md <= dist_tol, f"distance error {md} > {dist_tol}"
-    assert mt <= tan_tol, f"tangent error {mt} > {tan_tol}"
+    assert mt <= tan_tol, f"tangent error {mt} > {tan_tol} at pair {worst[0]}: d_gpu={worst[1]!r} " \
+                          f"d_ref={worst[2]!r} rival gap={worst[3]!r}"
     return n, md, mt

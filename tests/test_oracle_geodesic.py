@@ -242,3 +242,20 @@ def test_mesh_validation():
     three = np.concatenate([m.faces, [[0, 1, 3]]])  # edge (0,1) used three times
     with pytest.raises(ValueError):
         O.OracleMesh(synth.meshes.Mesh(m.verts, three))
+
+
+def test_walk_check_rejects_a_wrong_tangent():
+    """The cut-locus acceptance rule used by the GPU parity tests (a differing tangent must
+    start a geodesic of the reported length to the target) rejects a perturbed tangent."""
+    from tests._common import geodesic_walker
+    m = synth.icosphere(3, 1.0)
+    om = O.OracleMesh(m)
+    face, bary = synth.place_uniform(m, 30, 4)
+    rs, j, d, t = om.neighbors(face, bary, 0.5)
+    walk = geodesic_walker(om, face, bary)
+    fr = om.face_frame(face[0])
+    n = np.cross(fr[1], fr[2])
+    for q in range(rs[0], rs[1]):
+        assert walk(0, int(j[q]), d[q], t[q]) < 1e-12
+        bad = t[q] * math.cos(1e-3) + np.cross(n, t[q]) * math.sin(1e-3)
+        assert walk(0, int(j[q]), d[q], bad) > 1e-5 * d[q]
