@@ -26,6 +26,21 @@ def geodesic_walker(om, face, bary):
     return walk
 
 
+def descent_checker(om, face, bary, r_c):
+    """Deficit 1 - (l(i,j) - l(i',j)) / eps where i' is particle i moved by eps along tangent t
+    (a straightest walk): 0 for any initial tangent of a shortest path from i to j, also on
+    the cut locus and for paths that bend at vertices (first variation of length), and
+    1 - cos(angle) for a direction off every such tangent."""
+    def check(i, j, d, t):
+        eps = 1e-4 * d
+        f2, b2, _, _ = om.shift(int(face[i]), bary[i], eps * np.asarray(t), None)
+        rc = 2 * d + 1e-12 if not math.isfinite(r_c) else r_c + eps
+        d0, _ = om.query(int(face[i]), bary[i], rc, [int(face[j])], [bary[j]])
+        d1, _ = om.query(f2, b2, rc, [int(face[j])], [bary[j]])
+        return 1.0 - (d0[0] - d1[0]) / eps
+    return check
+
+
 def compare_pairs(gpu, ref, r_c, dist_tol, tan_tol, rel=True, band=None, tie=None, walker=None,
                   land_tol=None):
     """Compare two CSR neighbour sets.  Pairs within `band` of the cutoff may be missing on

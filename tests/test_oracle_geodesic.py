@@ -259,3 +259,21 @@ def test_walk_check_rejects_a_wrong_tangent():
         assert walk(0, int(j[q]), d[q], t[q]) < 1e-12
         bad = t[q] * math.cos(1e-3) + np.cross(n, t[q]) * math.sin(1e-3)
         assert walk(0, int(j[q]), d[q], bad) > 1e-5 * d[q]
+
+
+def test_descent_check_accepts_shortest_directions_only():
+    """First-variation check used for cut-locus tangents: 0 deficit along a true initial
+    tangent (also for paths bending at saddle vertices), 1 - cos(angle) off it."""
+    from tests._common import descent_checker
+    m = synth.icosphere(2, 1.0, noise=0.05, seed=9)
+    om = O.OracleMesh(m)
+    face, bary = synth.place_uniform(m, 30, 4)
+    rs, j, d, t = om.neighbors(face, bary, 1.0)
+    chk = descent_checker(om, face, bary, 1.0)
+    for i in (0, 1, 2):
+        fr = om.face_frame(face[i])
+        n = np.cross(fr[1], fr[2])
+        for q in range(rs[i], rs[i + 1]):
+            assert abs(chk(i, int(j[q]), d[q], t[q])) < 1e-8
+            bad = t[q] * math.cos(2e-3) + np.cross(n, t[q]) * math.sin(2e-3)
+            assert chk(i, int(j[q]), d[q], bad) > 1e-6
