@@ -154,6 +154,14 @@ __device__ __forceinline__ double win_dist(const Win<R>& w, double px, double py
     return w.sig + (double)sqrt(dx * dx + dy * dy);
 }
 
+// the same in FP64 whatever the form: vertex distances become the sigma of later
+// pseudo-sources and decide near-ties between path families
+template <class R>
+__device__ __forceinline__ double win_dist_exact(const Win<R>& w, double px, double py) {
+    const double dx = px - w.sx, dy = py - w.sy;
+    return w.sig + sqrt(dx * dx + dy * dy);
+}
+
 template <class R>
 __device__ __forceinline__ void win_tangent(const Win<R>& w, double px, double py, R& tx, R& ty) {
     if (w.flags & WIN_FIXED) { tx = w.ta; ty = w.tb; return; }
@@ -184,6 +192,20 @@ __device__ __forceinline__ R ray_hit(double sx, double sy, R X, double ax, doubl
     return mu < (R)0 ? (R)0 : (mu > (R)1 ? (R)1 : mu);
 }
 
+// relative widening of child intervals computed with FP32 ray intersections, so that
+// rounding never opens a gap between neighbouring windows (an overlap is resolved exactly by
+// the FP64 trimming, a gap would hand its wedge to a longer path family)
+template <class R>
+struct Widen;
+template <>
+struct Widen<double> {
+    static constexpr double mu = 0.0;
+};
+template <>
+struct Widen<float> {
+    static constexpr float mu = 8.0f * 1.1920929e-7f;
+};
+
 template <class R>
 struct VCand {
     int32_t v;
@@ -208,11 +230,11 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
     const R tolv = (R)(Tol<R>::w * L);
     if (W.b0 <= tolv) {
         VCand<R>& c = vc[nvc++];
-        c.v = vu; c.fixed = W.flags & WIN_FIXED; c.d = win_dist(W, 0.0, 0.0); win_tangent(W, 0.0, 0.0, c.tx, c.ty);
+        c.v = vu; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact(W, 0.0, 0.0); win_tangent(W, 0.0, 0.0, c.tx, c.ty);
     }
     if ((double)W.b1 >= L - (double)tolv) {
         VCand<R>& c = vc[nvc++];
-        c.v = vv; c.fixed = W.flags & WIN_FIXED; c.d = win_dist(W, L, 0.0); win_tangent(W, L, 0.0, c.tx, c.ty);
+        c.v = vv; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact(W, L, 0.0); win_tangent(W, L, 0.0, c.tx, c.ty);
     }
     const bool degen = win_degen(W, L);
     if (degen && !win_degen_sees(W, L)) return;
@@ -220,7 +242,7 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
     const double xc = degen ? 0.0 : W.sx + (r.cx - W.sx) * (-W.sy) / (r.cy - W.sy);
     if (degen || (xc >= (double)W.b0 - (double)tolv && xc <= (double)W.b1 + (double)tolv)) {
         VCand<R>& c = vc[nvc++];
-        c.v = vcid; c.fixed = W.flags & WIN_FIXED; c.d = win_dist(W, r.cx, r.cy); win_tangent(W, r.cx, r.cy, c.tx, c.ty);
+        c.v = vcid; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact(W, r.cx, r.cy); win_tangent(W, r.cx, r.cy, c.tx, c.ty);
     }
     if (r.tl >= 0 && (degen || xc > (double)W.b0)) {
         R mu0 = (R)0, mu1 = (R)1;
@@ -238,6 +260,7 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
             c.tb = -W.ta * (R)r.sl + W.tb * (R)r.cl;
         }
         const R Lc = (R)(r.cx * r.cl + r.cy * r.sl);
+        if (!degen) { mu0 -= Widen<R>::mu; mu1 += Widen<R>::mu; }
         c.b0 = mu0 * Lc; c.b1 = mu1 * Lc;
         if (c.sy > 0.0) c.sy = 0.0;
         c.flags = (W.flags & WIN_FIXED) | WIN_ALIVE;
@@ -260,6 +283,7 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
             c.tb = -W.ta * (R)r.sr + W.tb * (R)r.cr;
         }
         const R Ld = (R)((L - r.cx) * r.cr - r.cy * r.sr);
+        if (!degen) { mu0 -= Widen<R>::mu; mu1 += Widen<R>::mu; }
         c.b0 = mu0 * Ld; c.b1 = mu1 * Ld;
         if (c.sy > 0.0) c.sy = 0.0;
         c.flags = (W.flags & WIN_FIXED) | WIN_ALIVE;
@@ -337,7 +361,7 @@ __device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win
     const double L = m.he[c.he].L;
     const R Lr = (R)L;
     const R tolw = (R)(Tol<R>::w * L);
-    const double tie = Tie<R>::rel;
+    const double tie = 1e-13;   // trimming compares exact FP64 lengths in both forms
     const bool c_direct = !(c.flags & WIN_FIXED);
     if (c.b0 < (R)0) c.b0 = (R)0;
     if (c.b1 > Lr) c.b1 = Lr;
@@ -414,9 +438,12 @@ __device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win
                 o_alive = false;
             } else {
                 int tail = oi;
+                const R wpad = (R)Widen<R>::mu * Lr;   // outward rounding of the kept parts
                 for (int q = 0; q < nk; ++q) {
-                    const R k0 = same ? keep[q][0] : Lr - keep[q][1];
-                    const R k1 = same ? keep[q][1] : Lr - keep[q][0];
+                    R k0 = (same ? keep[q][0] : Lr - keep[q][1]) - wpad;
+                    R k1 = (same ? keep[q][1] : Lr - keep[q][0]) + wpad;
+                    k0 = k0 < (R)0 ? (R)0 : k0;
+                    k1 = k1 > Lr ? Lr : k1;
                     if (q == 0) { ws.win[oi].b0 = k0; ws.win[oi].b1 = k1; }
                     else {
                         const int pid = win_alloc<R>(sm, ws.wcap);
@@ -480,7 +507,7 @@ __device__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, co
             const double d = c.d;
             const double vd = ws.vdist[slot];
             const int vf = ws.vflag[slot];
-            const double tie = Tie<R>::rel * d;
+            const double tie = 1e-13 * d;    // lengths are exact FP64 here in both forms
             // shorter beyond rounding, or a tie won by a direct path over a pseudo-source one
             if (d < vd - tie || (d <= vd + tie && !c.fixed && (vf & 2))) {
                 ws.vdist[slot] = d < vd ? d : vd;
@@ -601,10 +628,14 @@ __device__ double query(const DMesh& m, const Ws<R>& ws, int f0, double qx, doub
     double best = __longlong_as_double(0x7ff0000000000000ll);
     bool best_fixed = true;
     const double tie = Tie<R>::rel;
+    // FP32 form: candidates within the FP32 band of the current best are re-compared with
+    // exact FP64 lengths (near-degenerate predicate); best_exact holds the best's FP64 length
+    double best_exact = best;
     tx = (R)0; ty = (R)0;
     if (fl == f0) {
         const double dx = px - qx, dy = py - qy;
         best = sqrt(dx * dx + dy * dy);
+        best_exact = best;
         best_fixed = false;
         if (best > 0.0) { tx = (R)(dx / best); ty = (R)(dy / best); }
     }
@@ -634,10 +665,21 @@ __device__ double query(const DMesh& m, const Ws<R>& ws, int f0, double qx, doub
                 inside = X >= (double)w.b0 - tol && X <= (double)w.b1 + tol;
             }
             if (!inside) continue;
-            const double d = win_dist(w, hx, hy);
+            double d = win_dist(w, hx, hy);
             const bool direct = !(w.flags & WIN_FIXED);
-            if (d < best - tie * d || (d <= best + tie * d && direct && best_fixed)) {
-                best = d < best ? d : best;
+            double t_tie = tie;
+            double cmp_best = best;
+            if (sizeof(R) == sizeof(float) && fabs(d - best) <= 1e-5 * d) {
+                const double ex = w.sig + sqrt((hx - w.sx) * (hx - w.sx) + (hy - w.sy) * (hy - w.sy));
+                d = ex;
+                cmp_best = best_exact;
+                t_tie = 1e-13;
+            }
+            if (d < cmp_best - t_tie * d || (d <= cmp_best + t_tie * d && direct && best_fixed)) {
+                best = d < cmp_best ? d : cmp_best;
+                best_exact = sizeof(R) == sizeof(float)
+                                 ? w.sig + sqrt((hx - w.sx) * (hx - w.sx) + (hy - w.sy) * (hy - w.sy))
+                                 : d;
                 best_fixed = !direct;
                 win_tangent(w, hx, hy, tx, ty);
             }
@@ -649,7 +691,7 @@ __device__ double query(const DMesh& m, const Ws<R>& ws, int f0, double qx, doub
         double vx, vy;
         css::face_corner(m, fl, k, vx, vy);
         const double d = ws.vdist[slot] + sqrt((px - vx) * (px - vx) + (py - vy) * (py - vy));
-        if (d < best - tie * d) { best = d; best_fixed = true; tx = ws.vtan[2 * slot]; ty = ws.vtan[2 * slot + 1]; }
+        if (d < best - tie * d) { best = d; best_exact = d; best_fixed = true; tx = ws.vtan[2 * slot]; ty = ws.vtan[2 * slot + 1]; }
     }
     return best;
 }

@@ -82,7 +82,7 @@ def test_neighbors_fp32_within_tolerance(ctx, name):
     # is accepted only if it is the initial direction of a shortest path (moving the source
     # along it shortens the distance at the full rate): cut-locus points have several
     tol = FP32_REL_DIAM * diam
-    compare_pairs(g, r, r_c, tol, 1e-4, rel=False, band=tol, tie=tol,
+    compare_pairs(g, r, r_c, tol, 1e-5, rel=False, band=tol, tie=tol,
                   walker=descent_checker(om, face, bary, r_c), land_tol=1e-7)
     parts.free()
     mesh.free()
@@ -112,7 +112,7 @@ def test_tiny_meshes_all_pairs(ctx, name, make):
         else:
             t32 = FP32_REL_DIAM * synth.bbox_diagonal(m)
             om = O.OracleMesh(m)
-            compare_pairs(g, r, math.inf, t32, 1e-4, rel=False, tie=t32,
+            compare_pairs(g, r, math.inf, t32, 1e-5, rel=False, tie=t32,
                           walker=descent_checker(om, face, bary, math.inf), land_tol=1e-7)
     parts.free()
     mesh.free()
