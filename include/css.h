@@ -178,6 +178,30 @@ int css_batch_step(css_batch* batch, const css_potential* pot, const css_integra
                    double r_c, int precision, int64_t n_steps);
 int css_batch_free(css_batch* batch);
 
+/* ---------------------------------------------------------------- allocation-free forces
+ * css_compute_forces_noalloc has no counterpart in the paper.  It is for callers that
+ * cannot allocate device memory where they evaluate forces (inside a host callback, in
+ * a framework that forbids allocation on its hot path, or where the device footprint
+ * must stay fixed after start-up).  It computes the same forces and energy as
+ * css_compute_forces, for particles given directly as device arrays, and calls no
+ * cudaMalloc, cudaFree or allocating library routine: its scratch is one fixed device
+ * array of about 59 MB that every GPU loading this library holds until exit.
+ *   mesh     uploaded beforehand with css_mesh_upload (that call allocates);
+ *   face     device int32[n]; bary device double[n x 3]; forces device double[n x 3];
+ *   e_pot    device double[1] or NULL (zeroed, then summed into);
+ *   stream   cudaStream_t to run on (NULL: the legacy default stream); the call
+ *            synchronises it to read the status.
+ * Limits: n <= 262144 particles, at most 1048576 faces, 2048 windows per source and
+ * warp; beyond them it returns CSS_ERR_CAPACITY (sizes) or CSS_ERR_QUEUE_OVERFLOW (a
+ * source needing more windows), and css_compute_forces should be used instead.
+ * The first call on a device looks up the array's device address (set-up): make it
+ * before any stream capture.  Every call shares the array, which keeps the previous
+ * call's contents, so calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller. */
+int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* face,
+                               const double* bary, const css_potential* pot, double r_c,
+                               int precision, double* forces, double* e_pot, void* stream);
+
 /* ---------------------------------------------------------------- measurement
  * css_last_kernel_ms: device time (ms) between CUDA events recorded on the context
  * stream immediately before and after the last neighbour/force kernel launch

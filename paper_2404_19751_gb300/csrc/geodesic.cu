@@ -969,3 +969,114 @@ cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* 
 }
 
 }  // namespace cssi
+
+// =====================================================================================
+// Allocation-free force evaluation.
+//
+// Some callers cannot call cudaMalloc at the point where they need forces: code running
+// inside a host callback or a framework that forbids device allocation on its hot path,
+// or an embedding that must not change the device memory footprint after start-up. For
+// them css_compute_forces_noalloc runs the same neighbour/force kernel as
+// css_compute_forces, but all of its scratch (the per-warp window workspace, the face
+// buckets and the launch counters) lives in the one file-scope device array below, of a
+// fixed size that every GPU loading this library holds until the process exits.
+namespace {
+
+constexpr size_t NA_WS_BYTES = 48ull << 20;        // per-warp window workspaces
+constexpr int NA_MAX_WARPS = 1024;
+constexpr int NA_WIN_CAP = 2048;                    // windows per warp
+constexpr int64_t NA_MAX_FACES = 1 << 20;
+constexpr int64_t NA_MAX_PARTICLES = 1 << 18;
+constexpr int NA_WARPS_PER_CTA = 4;
+constexpr size_t NA_OFF_GEN = NA_WS_BYTES;
+constexpr size_t NA_OFF_FCNT = NA_OFF_GEN + NA_MAX_WARPS * 4;
+constexpr size_t NA_OFF_FSTART = NA_OFF_FCNT + (NA_MAX_FACES + 1) * 4;
+constexpr size_t NA_OFF_FITEMS = NA_OFF_FSTART + (NA_MAX_FACES + 1) * 4;
+constexpr size_t NA_OFF_SCAN = NA_OFF_FITEMS + NA_MAX_PARTICLES * 4;
+constexpr size_t NA_SCAN_INTS = (NA_MAX_FACES + 1) / 2048 + 2;
+constexpr size_t NA_OFF_PCNT = NA_OFF_SCAN + NA_SCAN_INTS * 4;
+constexpr size_t NA_OFF_SCAL = (NA_OFF_PCNT + NA_MAX_PARTICLES * 4 + 255) & ~(size_t)255;  // work, status
+constexpr size_t NA_OFF_COUNT = NA_OFF_SCAL + 256;                                         // 8 counters
+constexpr size_t NA_BYTES = NA_OFF_COUNT + 8 * 8;   // ~59 MB in all
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+struct NaDevice {
+    char* base = nullptr;   // device address of g_noalloc_scratch on this device
+    int layout = -1;        // precision whose workspace layout the bytes currently hold
+};
+NaDevice g_na[64];
+
+}  // namespace
+
+int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* face, const double* bary,
+                               const css_potential* pot, double r_c, int precision, double* forces,
+                               double* e_pot, void* stream) {
+    if (!mesh || !face || !bary || !pot || !forces || n < 1 || !(r_c > 0.0) ||
+        (precision != CSS_FP64 && precision != CSS_FP32) || pot->kind < 0 || pot->kind > 2)
+        return CSS_ERR_INVALID_ARG;
+    css_ctx* c = mesh->ctx;
+    if (n > NA_MAX_PARTICLES || mesh->nf > NA_MAX_FACES) {
+        c->err = "compute_forces_noalloc: at most " + std::to_string(NA_MAX_PARTICLES) + " particles and " +
+                 std::to_string(NA_MAX_FACES) + " faces fit its fixed scratch";
+        return CSS_ERR_CAPACITY;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CSS_ERR_CUDA;
+    NaDevice& D = g_na[dev];
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!D.base) {   // first call on this device: host code needs the array's device address
+        cudaError_t e = cudaGetSymbolAddress((void**)&D.base, g_noalloc_scratch);
+        if (e != cudaSuccess) { D.base = nullptr; c->err = std::string("noalloc set-up: ") + cudaGetErrorString(e); return CSS_ERR_CUDA; }
+    }
+    cssi::GeoWs g{};
+    g.stride = cssi::geo_ws_bytes_per_warp(precision, NA_WIN_CAP, &g.log_eh, &g.log_vh, &g.log_fh, &g.fcap, &g.emcap);
+    g.wcap = NA_WIN_CAP;
+    g.nwarps = (int)std::min<size_t>(NA_MAX_WARPS, NA_WS_BYTES / g.stride);
+    g.nwarps -= g.nwarps % NA_WARPS_PER_CTA;
+    g.base = D.base;
+    g.gen = (uint32_t*)(D.base + NA_OFF_GEN);
+    int32_t* fcnt = (int32_t*)(D.base + NA_OFF_FCNT);
+    int32_t* fstart = (int32_t*)(D.base + NA_OFF_FSTART);
+    int32_t* fitems = (int32_t*)(D.base + NA_OFF_FITEMS);
+    int32_t* scan = (int32_t*)(D.base + NA_OFF_SCAN);
+    int32_t* pcnt = (int32_t*)(D.base + NA_OFF_PCNT);
+    int* scal = (int*)(D.base + NA_OFF_SCAL);
+    unsigned long long* cnt = (unsigned long long*)(D.base + NA_OFF_COUNT);
+    cudaError_t e = cudaSuccess;
+    if (D.layout != precision) {
+        // the array keeps the previous call's bytes; a new workspace layout starts from zero so
+        // no stale bytes look like hash entries, and the face counts start from zero
+        e = cudaMemsetAsync(D.base, 0, NA_OFF_FSTART, st);
+        if (e == cudaSuccess) D.layout = precision;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, 256 + 8 * 8, st);
+    if (e == cudaSuccess && e_pot) e = cudaMemsetAsync(e_pot, 0, sizeof(double), st);
+    if (e == cudaSuccess) e = cssi::launch_bucket((int32_t)n, (int32_t)mesh->nf, face, fcnt, fstart, fitems, scan, st);
+    cssi::GeoJob j{};
+    j.m = mesh->view();
+    j.n = (int32_t)n;
+    j.face = face;
+    j.bary = bary;
+    j.fstart = fstart;
+    j.fitems = fitems;
+    j.rc = r_c;
+    j.pcnt = pcnt;
+    j.want_forces = 1;
+    j.pot = *pot;
+    j.force = forces;
+    j.epot = e_pot;
+    if (e == cudaSuccess)
+        e = cssi::launch_geodesic(j, nullptr, nullptr, nullptr, (int32_t)n, precision, g, NA_WARPS_PER_CTA,
+                                  g.nwarps / NA_WARPS_PER_CTA, scal, scal + 1, cnt, st);
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, scal + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { c->err = std::string("compute_forces_noalloc: ") + cudaGetErrorString(e); return CSS_ERR_CUDA; }
+    if (status) {
+        c->err = "compute_forces_noalloc: a source needs more than the fixed window workspace (" +
+                 std::to_string(NA_WIN_CAP) + " windows per warp); use css_compute_forces";
+        return CSS_ERR_QUEUE_OVERFLOW;
+    }
+    return CSS_OK;
+}
