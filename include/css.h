@@ -213,7 +213,7 @@ int css_last_kernel_ms(css_ctx* ctx, double* ms);
 int css_fma_peak(css_ctx* ctx, int precision, double* flops_per_s);
 
 /* ---------------------------------------------------------------- tuning
- * Launch shape of the neighbour/force kernel: warps per CTA (1..16) and the
+ * Launch shape of the neighbour/force kernel: warps per CTA (1..8) and the
  * per-warp window-workspace capacity (windows; rounded up to a power of two).
  * 0 keeps the current value.  The batched form's autotuner calls this. */
 int css_set_launch(css_ctx* ctx, int32_t warps_per_cta, int32_t window_capacity);

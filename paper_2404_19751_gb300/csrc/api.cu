@@ -319,7 +319,7 @@ int css_fma_peak(css_ctx* c, int precision, double* flops_per_s) {
 }
 
 int css_set_launch(css_ctx* c, int32_t warps_per_cta, int32_t window_capacity) {
-    if (!c || warps_per_cta < 0 || warps_per_cta > 16 || window_capacity < 0) return CSS_ERR_INVALID_ARG;
+    if (!c || warps_per_cta < 0 || warps_per_cta > 8 || window_capacity < 0) return CSS_ERR_INVALID_ARG;
     if (warps_per_cta) c->warps_per_cta = warps_per_cta;
     if (window_capacity) c->win_cap = next_pow2(window_capacity);
     return CSS_OK;
@@ -350,7 +350,7 @@ int css_mesh_free(css_mesh* m) {
     if (!m) return CSS_ERR_INVALID_ARG;
     cudaFree(m->he); cudaFree(m->twin); cudaFree(m->edge); cudaFree(m->fv); cudaFree(m->lay);
     cudaFree(m->frame); cudaFree(m->theta); cudaFree(m->pseudo); cudaFree(m->bnd);
-    cudaFree(m->ring_start); cudaFree(m->ring); cudaFree(m->X);
+    cudaFree(m->ring_start); cudaFree(m->ring); cudaFree(m->X); cudaFree(m->he32); cudaFree(m->lay32);
     delete m;
     return CSS_OK;
 }

@@ -22,6 +22,12 @@ struct __align__(16) HeRec {
     int32_t tl, tr;  // twin of half-edge (f,k+2) [edge c-u] and (f,k+1) [edge v-c], -1: boundary
 };
 
+// FP32 copy of HeRec for the FP32 form's arithmetic (32 B)
+struct __align__(16) HeRec32 {
+    float L, cx, cy, cl, sl, cr, sr;
+    int32_t pad;
+};
+
 struct DMesh {
     int32_t nv, nf;
     int32_t periodic;
@@ -37,6 +43,8 @@ struct DMesh {
     const uint8_t* bnd;           // nv: boundary vertex
     const int32_t* ring_start;    // nv + 1
     const int32_t* ring;          // 3 nf corners h with fv[h] == v, grouped by vertex
+    const HeRec32* he32;          // 3 nf, FP32 copies of he
+    const float* lay32;           // 3 nf, FP32 copies of lay
 };
 
 __device__ __forceinline__ double cross2(double ax, double ay, double bx, double by) { return ax * by - ay * bx; }

@@ -53,6 +53,8 @@ struct css_mesh {
     int32_t* ring_start = nullptr;
     int32_t* ring = nullptr;
     double* X = nullptr;
+    css::HeRec32* he32 = nullptr;
+    float* lay32 = nullptr;
     css::DMesh view() const;
 };
 

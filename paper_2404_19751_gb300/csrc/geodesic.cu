@@ -42,14 +42,43 @@ constexpr int WIN_FIXED = 4;   // tangent fixed (descends from a pseudo-source v
 constexpr int MAXP = 6;        // interval pieces one insertion may hold
 constexpr int MAX_WARPS_CTA = 16;
 
-template <class R>
-struct Win {
-    double sx, sy;     // pseudo-source in the frame of half-edge `he`  } accumulated unfolded
-    double sig;        // geodesic length source -> pseudo-source        } source state: FP64
-    R b0, b1;          // interval along the half-edge
-    R ta, tb;          // image of the source-face x axis (direct) or fixed tangent
+// Window record.  The pseudo-source s and its geodesic length sigma are the accumulated
+// unfolded source state and stay FP64 in both forms; the FP32 form also keeps FP32 copies
+// of them for its arithmetic, so that a window is 64 bytes and FP64 instructions are only
+// issued for the unfolding transform of s and for near-degenerate decisions.
+struct Win32 {
+    double sx, sy, sig;
+    float fsx, fsy, fsig;
+    float b0, b1;      // interval along the half-edge
+    float ta, tb;      // image of the source-face x axis (direct) or fixed tangent
     int32_t he, next, flags;
 };
+struct Win64 {
+    double sx, sy, sig;
+    double b0, b1, ta, tb;
+    int32_t he, next, flags;
+};
+template <class R>
+struct WinT;
+template <>
+struct WinT<float> {
+    using type = Win32;
+};
+template <>
+struct WinT<double> {
+    using type = Win64;
+};
+template <class R>
+using Win = typename WinT<R>::type;
+
+__device__ __forceinline__ float fsx(const Win32& w) { return w.fsx; }
+__device__ __forceinline__ float fsy(const Win32& w) { return w.fsy; }
+__device__ __forceinline__ float fsig(const Win32& w) { return w.fsig; }
+__device__ __forceinline__ double fsx(const Win64& w) { return w.sx; }
+__device__ __forceinline__ double fsy(const Win64& w) { return w.sy; }
+__device__ __forceinline__ double fsig(const Win64& w) { return w.sig; }
+__device__ __forceinline__ void set_fast(Win32& w) { w.fsx = (float)w.sx; w.fsy = (float)w.sy; w.fsig = (float)w.sig; }
+__device__ __forceinline__ void set_fast(Win64&) {}
 
 template <class R>
 struct Tol;
@@ -140,18 +169,53 @@ __device__ inline Ws<R> ws_bind(const cssi::GeoWs& g, int warp) {
 }
 
 // ------------------------------------------------------------------ window geometry
+// The "fast" type F is the form's arithmetic type: float in the FP32 form, double in FP64.
+
+// half-edge geometry in the form's precision
 template <class R>
-__device__ __forceinline__ double win_key(const Win<R>& w) {
-    double x = w.sx < (double)w.b0 ? (double)w.b0 : (w.sx > (double)w.b1 ? (double)w.b1 : w.sx);
-    double dx = x - w.sx;
-    return w.sig + (double)sqrt((R)(dx * dx + w.sy * w.sy));
+struct HeF {
+    R L, cx, cy, cl, sl, cr, sr;
+};
+template <class R>
+__device__ __forceinline__ HeF<R> he_fast(const DMesh& m, int h, const HeRec& r);
+template <>
+__device__ __forceinline__ HeF<double> he_fast<double>(const DMesh&, int, const HeRec& r) {
+    return HeF<double>{r.L, r.cx, r.cy, r.cl, r.sl, r.cr, r.sr};
+}
+template <>
+__device__ __forceinline__ HeF<float> he_fast<float>(const DMesh& m, int h, const HeRec&) {
+    const css::HeRec32 q = m.he32[h];
+    return HeF<float>{q.L, q.cx, q.cy, q.cl, q.sl, q.cr, q.sr};
 }
 
-// distance carried to the point (px, py) of the window frame
 template <class R>
-__device__ __forceinline__ double win_dist(const Win<R>& w, double px, double py) {
-    R dx = (R)(px - w.sx), dy = (R)(py - w.sy);
-    return w.sig + (double)sqrt(dx * dx + dy * dy);
+__device__ __forceinline__ void face_corner_f(const DMesh& m, int f, int k, R& x, R& y);
+template <>
+__device__ __forceinline__ void face_corner_f<double>(const DMesh& m, int f, int k, double& x, double& y) {
+    css::face_corner(m, f, k, x, y);
+}
+template <>
+__device__ __forceinline__ void face_corner_f<float>(const DMesh& m, int f, int k, float& x, float& y) {
+    k = (k >= 3) ? k - 3 : k;
+    if (k == 0) { x = 0.f; y = 0.f; }
+    else if (k == 1) { x = m.lay32[3 * f]; y = 0.f; }
+    else { x = m.lay32[3 * f + 1]; y = m.lay32[3 * f + 2]; }
+}
+
+// smallest distance the window carries over its interval
+template <class R>
+__device__ __forceinline__ R win_key(const Win<R>& w) {
+    const R sx = fsx(w), sy = fsy(w);
+    const R x = sx < w.b0 ? w.b0 : (sx > w.b1 ? w.b1 : sx);
+    const R dx = x - sx;
+    return fsig(w) + sqrt(dx * dx + sy * sy);
+}
+
+// distance carried to the point (px, py) of the window frame, form precision
+template <class R>
+__device__ __forceinline__ R win_dist(const Win<R>& w, R px, R py) {
+    const R dx = px - fsx(w), dy = py - fsy(w);
+    return fsig(w) + sqrt(dx * dx + dy * dy);
 }
 
 // the same in FP64 whatever the form: vertex distances become the sigma of later
@@ -163,10 +227,10 @@ __device__ __forceinline__ double win_dist_exact(const Win<R>& w, double px, dou
 }
 
 template <class R>
-__device__ __forceinline__ void win_tangent(const Win<R>& w, double px, double py, R& tx, R& ty) {
+__device__ __forceinline__ void win_tangent(const Win<R>& w, R px, R py, R& tx, R& ty) {
     if (w.flags & WIN_FIXED) { tx = w.ta; ty = w.tb; return; }
-    R dx = (R)(px - w.sx), dy = (R)(py - w.sy);
-    R n = sqrt(dx * dx + dy * dy);
+    R dx = px - fsx(w), dy = py - fsy(w);
+    const R n = sqrt(dx * dx + dy * dy);
     dx /= n; dy /= n;
     tx = dx * w.ta + dy * w.tb;
     ty = -dx * w.tb + dy * w.ta;
@@ -174,27 +238,27 @@ __device__ __forceinline__ void win_tangent(const Win<R>& w, double px, double p
 
 // a pseudo-source on the edge line sees the face beyond only through its own position
 template <class R>
-__device__ __forceinline__ bool win_degen(const Win<R>& w, double L) { return w.sy > -1e-13 * L; }
+__device__ __forceinline__ bool win_degen(const Win<R>& w, R L) { return fsy(w) > (R)-1e-13 * L; }
 template <class R>
-__device__ __forceinline__ bool win_degen_sees(const Win<R>& w, double L) {
-    double tol = 1e-12 * L;
-    return w.sx >= (double)w.b0 - tol && w.sx <= (double)w.b1 + tol;
+__device__ __forceinline__ bool win_degen_sees(const Win<R>& w, R L) {
+    const R tol = (R)1e-12 * L;
+    return fsx(w) >= w.b0 - tol && fsx(w) <= w.b1 + tol;
 }
 
 // parameter in [0,1] along A->B hit by the ray from s through (X, 0)
 template <class R>
-__device__ __forceinline__ R ray_hit(double sx, double sy, R X, double ax, double ay, double bx, double by) {
-    R dx = (R)((double)X - sx), dy = (R)(-sy);
-    R ex = (R)(bx - ax), ey = (R)(by - ay);
-    R den = ex * dy - ey * dx;
-    R qx = (R)(sx - ax), qy = (R)(sy - ay);
-    R mu = den != (R)0 ? (qx * dy - qy * dx) / den : (R)0;
+__device__ __forceinline__ R ray_hit(R sx, R sy, R X, R ax, R ay, R bx, R by) {
+    const R dx = X - sx, dy = -sy;
+    const R ex = bx - ax, ey = by - ay;
+    const R den = ex * dy - ey * dx;
+    const R qx = sx - ax, qy = sy - ay;
+    const R mu = den != (R)0 ? (qx * dy - qy * dx) / den : (R)0;
     return mu < (R)0 ? (R)0 : (mu > (R)1 ? (R)1 : mu);
 }
 
 // relative widening of child intervals computed with FP32 ray intersections, so that
 // rounding never opens a gap between neighbouring windows (an overlap is resolved exactly by
-// the FP64 trimming, a gap would hand its wedge to a longer path family)
+// the trimming, a gap would hand its wedge to a longer path family)
 template <class R>
 struct Widen;
 template <>
@@ -210,11 +274,12 @@ template <class R>
 struct VCand {
     int32_t v;
     int32_t fixed;   // tangent comes from a pseudo-source path
-    double d;
+    double d;        // exact FP64 length
     R tx, ty;
 };
 
-// Unfold window W into the next face: vertex candidates and at most two children.
+// Unfold window W into the next face: distance candidates for the pseudo-source vertices it
+// reaches (paths through any other vertex can be shortened, Sec. 2.2) and at most two children.
 template <class R>
 __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* vc, int& nvc, Win<R>* ch,
                           int& nch) {
@@ -224,53 +289,64 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
     const int f = h / 3;
     const int k = h - 3 * f;
     const HeRec r = m.he[h];
+    const HeF<R> q = he_fast<R>(m, h, r);
     const int k1 = (k == 2) ? 0 : k + 1, k2 = (k == 0) ? 2 : k - 1;
     const int32_t vu = m.fv[h], vv = m.fv[3 * f + k1], vcid = m.fv[3 * f + k2];
-    const double L = r.L;
-    const R tolv = (R)(Tol<R>::w * L);
-    if (W.b0 <= tolv) {
+    const R tolv = (R)Tol<R>::w * q.L;
+    const R sx = fsx(W), sy = fsy(W);
+    if (W.b0 <= tolv && m.pseudo[vu]) {
         VCand<R>& c = vc[nvc++];
-        c.v = vu; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact(W, 0.0, 0.0); win_tangent(W, 0.0, 0.0, c.tx, c.ty);
+        c.v = vu; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact<R>(W, 0.0, 0.0);
+        win_tangent<R>(W, (R)0, (R)0, c.tx, c.ty);
     }
-    if ((double)W.b1 >= L - (double)tolv) {
+    if (W.b1 >= q.L - tolv && m.pseudo[vv]) {
         VCand<R>& c = vc[nvc++];
-        c.v = vv; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact(W, L, 0.0); win_tangent(W, L, 0.0, c.tx, c.ty);
+        c.v = vv; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact<R>(W, r.L, 0.0);
+        win_tangent<R>(W, q.L, (R)0, c.tx, c.ty);
     }
-    const bool degen = win_degen(W, L);
-    if (degen && !win_degen_sees(W, L)) return;
-    // occlusion predicate (FP64 in both forms): where the ray s -> c crosses the edge line
-    const double xc = degen ? 0.0 : W.sx + (r.cx - W.sx) * (-W.sy) / (r.cy - W.sy);
-    if (degen || (xc >= (double)W.b0 - (double)tolv && xc <= (double)W.b1 + (double)tolv)) {
+    const bool degen = win_degen<R>(W, q.L);
+    if (degen && !win_degen_sees<R>(W, q.L)) return;
+    // occlusion predicate: where the ray s -> c crosses the edge line; in the FP32 form it is
+    // re-evaluated in FP64 when it falls within 1e-5 L of an interval end
+    R xc = degen ? (R)0 : sx + (q.cx - sx) * (-sy) / (q.cy - sy);
+    if (sizeof(R) == sizeof(float) && !degen &&
+        (fabs(xc - W.b0) < (R)1e-5 * q.L || fabs(xc - W.b1) < (R)1e-5 * q.L)) {
+        xc = (R)(W.sx + (r.cx - W.sx) * (-W.sy) / (r.cy - W.sy));
+    }
+    if ((degen || (xc >= W.b0 - tolv && xc <= W.b1 + tolv)) && m.pseudo[vcid]) {
         VCand<R>& c = vc[nvc++];
-        c.v = vcid; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact(W, r.cx, r.cy); win_tangent(W, r.cx, r.cy, c.tx, c.ty);
+        c.v = vcid; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact<R>(W, r.cx, r.cy);
+        win_tangent<R>(W, q.cx, q.cy, c.tx, c.ty);
     }
-    if (r.tl >= 0 && (degen || xc > (double)W.b0)) {
+    if (r.tl >= 0 && (degen || xc > W.b0)) {
         R mu0 = (R)0, mu1 = (R)1;
         if (!degen) {
-            mu0 = ray_hit<R>(W.sx, W.sy, W.b0, 0.0, 0.0, r.cx, r.cy);
-            mu1 = ((double)W.b1 >= xc) ? (R)1 : ray_hit<R>(W.sx, W.sy, W.b1, 0.0, 0.0, r.cx, r.cy);
+            mu0 = ray_hit<R>(sx, sy, W.b0, (R)0, (R)0, q.cx, q.cy);
+            mu1 = (W.b1 >= xc) ? (R)1 : ray_hit<R>(sx, sy, W.b1, (R)0, (R)0, q.cx, q.cy);
+            mu0 -= Widen<R>::mu; mu1 += Widen<R>::mu;
         }
         Win<R>& c = ch[nch];
         c = W;
         c.he = r.tl;
-        c.sx = W.sx * r.cl + W.sy * r.sl;           // rotate by -angle(c), origin at u
+        c.sx = W.sx * r.cl + W.sy * r.sl;           // rotate by -angle(c), origin at u (FP64)
         c.sy = -W.sx * r.sl + W.sy * r.cl;
-        if (!(W.flags & WIN_FIXED)) {
-            c.ta = W.ta * (R)r.cl + W.tb * (R)r.sl;
-            c.tb = -W.ta * (R)r.sl + W.tb * (R)r.cl;
-        }
-        const R Lc = (R)(r.cx * r.cl + r.cy * r.sl);
-        if (!degen) { mu0 -= Widen<R>::mu; mu1 += Widen<R>::mu; }
-        c.b0 = mu0 * Lc; c.b1 = mu1 * Lc;
         if (c.sy > 0.0) c.sy = 0.0;
+        set_fast(c);
+        if (!(W.flags & WIN_FIXED)) {
+            c.ta = W.ta * q.cl + W.tb * q.sl;
+            c.tb = -W.ta * q.sl + W.tb * q.cl;
+        }
+        const R Lc = q.cx * q.cl + q.cy * q.sl;
+        c.b0 = mu0 * Lc; c.b1 = mu1 * Lc;
         c.flags = (W.flags & WIN_FIXED) | WIN_ALIVE;
-        if (win_key(c) < rc) ++nch;
+        if ((double)win_key<R>(c) < rc) ++nch;
     }
-    if (r.tr >= 0 && (degen || xc < (double)W.b1)) {
+    if (r.tr >= 0 && (degen || xc < W.b1)) {
         R mu0 = (R)0, mu1 = (R)1;
         if (!degen) {
-            mu0 = ((double)W.b0 <= xc) ? (R)0 : ray_hit<R>(W.sx, W.sy, W.b0, r.cx, r.cy, L, 0.0);
-            mu1 = ray_hit<R>(W.sx, W.sy, W.b1, r.cx, r.cy, L, 0.0);
+            mu0 = (W.b0 <= xc) ? (R)0 : ray_hit<R>(sx, sy, W.b0, q.cx, q.cy, q.L, (R)0);
+            mu1 = ray_hit<R>(sx, sy, W.b1, q.cx, q.cy, q.L, (R)0);
+            mu0 -= Widen<R>::mu; mu1 += Widen<R>::mu;
         }
         Win<R>& c = ch[nch];
         c = W;
@@ -278,16 +354,16 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
         const double px = W.sx - r.cx, py = W.sy - r.cy;   // rotate by -angle(v - c), origin at c
         c.sx = px * r.cr + py * r.sr;
         c.sy = -px * r.sr + py * r.cr;
-        if (!(W.flags & WIN_FIXED)) {
-            c.ta = W.ta * (R)r.cr + W.tb * (R)r.sr;
-            c.tb = -W.ta * (R)r.sr + W.tb * (R)r.cr;
-        }
-        const R Ld = (R)((L - r.cx) * r.cr - r.cy * r.sr);
-        if (!degen) { mu0 -= Widen<R>::mu; mu1 += Widen<R>::mu; }
-        c.b0 = mu0 * Ld; c.b1 = mu1 * Ld;
         if (c.sy > 0.0) c.sy = 0.0;
+        set_fast(c);
+        if (!(W.flags & WIN_FIXED)) {
+            c.ta = W.ta * q.cr + W.tb * q.sr;
+            c.tb = -W.ta * q.sr + W.tb * q.cr;
+        }
+        const R Ld = (q.L - q.cx) * q.cr - q.cy * q.sr;
+        c.b0 = mu0 * Ld; c.b1 = mu1 * Ld;
         c.flags = (W.flags & WIN_FIXED) | WIN_ALIVE;
-        if (win_key(c) < rc) ++nch;
+        if ((double)win_key<R>(c) < rc) ++nch;
     }
 }
 
@@ -295,7 +371,7 @@ __device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* 
 // twice (FP64 in both forms: this is the near-degenerate intersection predicate).  Spurious
 // roots only add breakpoints; the winner of each piece is decided by evaluation.
 __device__ int equal_points(double ax, double ay, double sa, double bx, double by, double sb, double lo, double hi,
-                            double* r) {
+                            double& r0, double& r1) {
     const double del = sb - sa;
     const double al = bx - ax;
     const double be = (ax * ax + ay * ay) - (bx * bx + by * by) - del * del;
@@ -311,27 +387,54 @@ __device__ int equal_points(double ax, double ay, double sa, double bx, double b
         double disc = c1 * c1 - 4.0 * c2 * c0;
         if (disc < 0.0) disc = 0.0;
         const double sq = sqrt(disc);
-        const double q = -0.5 * (c1 + (c1 >= 0.0 ? sq : -sq));
-        if (q != 0.0) { cand0 = q / c2; cand1 = c0 / q; nc = 2; }
+        const double qq = -0.5 * (c1 + (c1 >= 0.0 ? sq : -sq));
+        if (qq != 0.0) { cand0 = qq / c2; cand1 = c0 / qq; nc = 2; }
         else { cand0 = -c1 / (2.0 * c2); nc = 1; }
     }
     int n = 0;
-    if (nc > 0 && cand0 > lo && cand0 < hi) r[n++] = cand0;
-    if (nc > 1 && cand1 > lo && cand1 < hi) r[n++] = cand1;
-    if (n == 2 && r[0] > r[1]) { double t = r[0]; r[0] = r[1]; r[1] = t; }
+    const bool ok0 = nc > 0 && cand0 > lo && cand0 < hi;
+    const bool ok1 = nc > 1 && cand1 > lo && cand1 < hi;
+    if (ok0 && ok1) { r0 = fmin(cand0, cand1); r1 = fmax(cand0, cand1); n = 2; }
+    else if (ok0) { r0 = cand0; n = 1; }
+    else if (ok1) { r0 = cand1; n = 1; }
     return n;
 }
 
-// Append [x0, x1] to a sorted interval list, merging with a touching last interval.  When
-// the list is full, `cover` decides: true extends the last interval over the gap (a window
-// that keeps more than it must only costs work: every window carries real path lengths),
-// false drops the interval (used for the parts a window loses, so it never loses too much).
+// ---- register-resident interval lists (sorted, disjoint, at most MAXP)
+// Every index is resolved by unrolled compare-and-select so the lists never spill to
+// local memory.  When a list is full, `cover` decides: true extends the last interval over
+// the gap (a window that keeps more than it must only costs work: every window carries real
+// path lengths), false drops the new interval (used for the parts a window loses, so it
+// never loses too much).
 template <class R>
-__device__ __forceinline__ void ivl_add(R (*iv)[2], int& n, R x0, R x1, bool cover = true) {
+struct Ivl {
+    R a[MAXP], b[MAXP];
+    int n;
+};
+
+template <class R>
+__device__ __forceinline__ R ivl_get(const R (&v)[MAXP], int i) {
+    R r = v[0];
+#pragma unroll
+    for (int k = 1; k < MAXP; ++k)
+        if (i == k) r = v[k];
+    return r;
+}
+template <class R>
+__device__ __forceinline__ void ivl_set(R (&v)[MAXP], int i, R x) {
+#pragma unroll
+    for (int k = 0; k < MAXP; ++k)
+        if (i == k) v[k] = x;
+}
+template <class R>
+__device__ __forceinline__ void ivl_add(Ivl<R>& L, R x0, R x1, bool cover = true) {
     if (!(x1 > x0)) return;
-    if (n > 0 && x0 <= iv[n - 1][1]) { if (x1 > iv[n - 1][1]) iv[n - 1][1] = x1; return; }
-    if (n < MAXP) { iv[n][0] = x0; iv[n][1] = x1; ++n; }
-    else if (cover) iv[n - 1][1] = x1;
+    if (L.n > 0) {
+        const R lb = ivl_get<R>(L.b, L.n - 1);
+        if (x0 <= lb) { if (x1 > lb) ivl_set<R>(L.b, L.n - 1, x1); return; }
+    }
+    if (L.n < MAXP) { ivl_set<R>(L.a, L.n, x0); ivl_set<R>(L.b, L.n, x1); ++L.n; }
+    else if (cover) L.b[MAXP - 1] = x1;
 }
 
 template <class R>
@@ -353,27 +456,64 @@ __device__ __forceinline__ int win_alloc(WarpSm& sm, int wcap) {
     return p;
 }
 
+// Outcome of comparing two windows on an overlap [lo, hi]: one of them carries the
+// smaller distance everywhere, or the exact FP64 split is needed.
+enum { CMP_EXISTING = 0, CMP_CANDIDATE = 1, CMP_SPLIT = 2 };
+
+// FP32 dominance test with rigorous margins: the distance difference D(x) is bounded from
+// its endpoint values and from bounds on its derivative (each distance's derivative along the
+// edge is monotone in x), with a rounding margin E on every evaluated difference.
+__device__ __forceinline__ int dominance_f32(float csx, float csy, float csig, float osx, float osy, float osig,
+                                             float lo, float hi) {
+    const float dcl = sqrtf((lo - csx) * (lo - csx) + csy * csy), dch = sqrtf((hi - csx) * (hi - csx) + csy * csy);
+    const float dol = sqrtf((lo - osx) * (lo - osx) + osy * osy), doh = sqrtf((hi - osx) * (hi - osx) + osy * osy);
+    const float Dlo = (csig + dcl) - (osig + dol), Dhi = (csig + dch) - (osig + doh);
+    const float E = 2.4e-6f * (csig + osig + fmaxf(dcl, dch) + fmaxf(dol, doh)) + 1e-30f;
+    const bool pos = Dlo > E && Dhi > E, neg = Dlo < -E && Dhi < -E;
+    if (!pos && !neg) return CMP_SPLIT;
+    if (!(dcl > 0.f && dch > 0.f && dol > 0.f && doh > 0.f)) return CMP_SPLIT;
+    // derivative of each distance along the edge: (x - s_x) / |x - s|, increasing in x
+    const float gcl = (lo - csx) / dcl, gch = (hi - csx) / dch, gol = (lo - osx) / dol, goh = (hi - osx) / doh;
+    const float m0 = gcl - goh - 1e-5f, m1 = gch - gol + 1e-5f;   // D' in [m0, m1]
+    const float W = hi - lo;
+    if (pos) {
+        if (m0 >= 0.f || m1 <= 0.f) return CMP_EXISTING;   // monotone between two positive values
+        // min over x of max(Dlo + m0 u, Dhi - m1 (W - u)), u = x - lo in [0, W]
+        float u = (Dlo - Dhi + m1 * W) / (m1 - m0);
+        u = fminf(fmaxf(u, 0.f), W);
+        const float lb = fmaxf(Dlo + m0 * u, Dhi - m1 * (W - u));
+        return lb > E ? CMP_EXISTING : CMP_SPLIT;
+    }
+    if (m0 >= 0.f || m1 <= 0.f) return CMP_CANDIDATE;
+    float u = (Dhi - Dlo + m1 * W) / (m1 - m0);   // max over x of min(Dlo + m1 u, Dhi - m0 (W - u))
+    u = fminf(fmaxf(u, 0.f), W);
+    const float ub = fminf(Dlo + m1 * u, Dhi - m0 * (W - u));
+    return ub < -E ? CMP_CANDIDATE : CMP_SPLIT;
+}
+
 // Insert candidate window c on its edge (list slot es), intersecting it with every window
 // already on the edge from either side: on each overlap both keep only where they carry
-// the smaller distance (ties to the existing window).  Executed by one lane per edge.
+// the smaller distance.  Executed by one lane per edge.
 template <class R>
 __device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win<R> c, double rc) {
-    const double L = m.he[c.he].L;
-    const R Lr = (R)L;
-    const R tolw = (R)(Tol<R>::w * L);
-    const double tie = 1e-13;   // trimming compares exact FP64 lengths in both forms
+    const double Ld = m.he[c.he].L;
+    const R Lr = (R)Ld;
+    const R tolw = (R)Tol<R>::w * Lr;
+    const double tie = 1e-13;   // exact FP64 comparisons below
     const bool c_direct = !(c.flags & WIN_FIXED);
     if (c.b0 < (R)0) c.b0 = (R)0;
     if (c.b1 > Lr) c.b1 = Lr;
-    if (!(c.b1 - c.b0 > tolw) || !(win_key(c) < rc)) return;
-    int err = 0;
-    R pc[MAXP][2];
-    int np = 1;
-    pc[0][0] = c.b0; pc[0][1] = c.b1;
+    if (!(c.b1 - c.b0 > tolw) || !((double)win_key<R>(c) < rc)) return;
+    Ivl<R> pc;
+    pc.n = 1;
+    pc.a[0] = c.b0; pc.b[0] = c.b1;
+#pragma unroll
+    for (int k = 1; k < MAXP; ++k) { pc.a[k] = (R)0; pc.b[k] = (R)0; }
     int prev = -1;
     int oi = ws.ehead[es];
     int guard = 0;
-    while (oi >= 0 && np > 0) {
+    int err = 0;
+    while (oi >= 0 && pc.n > 0) {
         if (++guard > ws.wcap) { err |= css::ST_ITER_LIMIT; break; }
         Win<R> o = ws.win[oi];
         const int onext = o.next;
@@ -384,25 +524,35 @@ __device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win
         }
         const bool same = (o.he == c.he);
         const R o0 = same ? o.b0 : Lr - o.b1, o1 = same ? o.b1 : Lr - o.b0;
-        const double osx = same ? o.sx : L - o.sx, osy = same ? o.sy : -o.sy;
-        R npc[MAXP][2];
-        int nn = 0;
-        R lost[MAXP][2];
-        int nl = 0;
-        for (int p = 0; p < np; ++p) {
-            const R a0 = pc[p][0], a1 = pc[p][1];
+        Ivl<R> npc, lost;
+        npc.n = 0; lost.n = 0;
+#pragma unroll
+        for (int k = 0; k < MAXP; ++k) { npc.a[k] = npc.b[k] = lost.a[k] = lost.b[k] = (R)0; }
+#pragma unroll
+        for (int p = 0; p < MAXP; ++p) {
+            if (p >= pc.n) break;
+            const R a0 = pc.a[p], a1 = pc.b[p];
             const R lo = a0 > o0 ? a0 : o0, hi = a1 < o1 ? a1 : o1;
-            if (!(hi - lo > tolw)) { ivl_add(npc, nn, a0, a1); continue; }
-            double bp[4];
-            int nb = 0;
-            bp[nb++] = (double)lo;
-            double rr[2];
-            const int nr = equal_points(c.sx, c.sy, c.sig, osx, osy, o.sig, (double)lo, (double)hi, rr);
-            for (int q = 0; q < nr; ++q) bp[nb++] = rr[q];
-            bp[nb++] = (double)hi;
-            ivl_add(npc, nn, a0, lo);
-            for (int q = 0; q + 1 < nb; ++q) {
-                const double xm = 0.5 * (bp[q] + bp[q + 1]);
+            if (!(hi - lo > tolw)) { ivl_add<R>(npc, a0, a1); continue; }
+            int cmp = CMP_SPLIT;
+            if (sizeof(R) == sizeof(float)) {
+                const R osx = same ? fsx(o) : Lr - fsx(o), osy = same ? fsy(o) : -fsy(o);
+                cmp = dominance_f32((float)fsx(c), (float)fsy(c), (float)fsig(c), (float)osx, (float)osy,
+                                    (float)fsig(o), (float)lo, (float)hi);
+            }
+            if (cmp == CMP_EXISTING) { ivl_add<R>(npc, a0, lo); ivl_add<R>(npc, hi, a1); continue; }
+            if (cmp == CMP_CANDIDATE) { ivl_add<R>(npc, a0, a1); ivl_add<R>(lost, lo, hi, false); continue; }
+            // exact FP64 split of the overlap at the equal-distance points
+            const double osx = same ? o.sx : Ld - o.sx, osy = same ? o.sy : -o.sy;
+            double r0 = 0.0, r1 = 0.0;
+            const int nr = equal_points(c.sx, c.sy, c.sig, osx, osy, o.sig, (double)lo, (double)hi, r0, r1);
+            ivl_add<R>(npc, a0, lo);
+            double x0 = (double)lo;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (q > nr) break;
+                const double x1 = q < nr ? (q == 0 ? r0 : r1) : (double)hi;
+                const double xm = 0.5 * (x0 + x1);
                 const double dc = c.sig + sqrt((xm - c.sx) * (xm - c.sx) + c.sy * c.sy);
                 const double dox = xm - osx;
                 const double dd = dc - (o.sig + sqrt(dox * dox + osy * osy));
@@ -410,67 +560,78 @@ __device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win
                 // window beats one descending from a pseudo-source (whose tangent is only
                 // exact on the tie line), otherwise the existing window keeps it, so exact
                 // ties never fragment intervals
-                const bool win = (dd < -tie * dc) ||
-                                 (dd <= tie * dc && c_direct && (o.flags & WIN_FIXED));
+                const bool win = (dd < -tie * dc) || (dd <= tie * dc && c_direct && (o.flags & WIN_FIXED));
                 if (win) {
-                    ivl_add(npc, nn, (R)bp[q], (R)bp[q + 1]);
-                    ivl_add(lost, nl, (R)bp[q], (R)bp[q + 1], false);
+                    ivl_add<R>(npc, (R)x0, (R)x1);
+                    ivl_add<R>(lost, (R)x0, (R)x1, false);
                 }
+                x0 = x1;
             }
-            ivl_add(npc, nn, hi, a1);
+            ivl_add<R>(npc, hi, a1);
         }
-        np = 0;
-        for (int p = 0; p < nn; ++p)
-            if (npc[p][1] - npc[p][0] > tolw) { pc[np][0] = npc[p][0]; pc[np][1] = npc[p][1]; ++np; }
-        bool o_alive = true;
-        if (nl > 0) {
-            R keep[MAXP][2];
-            int nk = 0;
-            R cur = o0;
-            for (int q = 0; q < nl; ++q) {
-                if (lost[q][0] - cur > tolw) ivl_add(keep, nk, cur, lost[q][0]);
-                if (lost[q][1] > cur) cur = lost[q][1];
+        pc.n = 0;
+#pragma unroll
+        for (int p = 0; p < MAXP; ++p)
+            if (p < npc.n && npc.b[p] - npc.a[p] > tolw) {
+                ivl_set<R>(pc.a, pc.n, npc.a[p]);
+                ivl_set<R>(pc.b, pc.n, npc.b[p]);
+                ++pc.n;
             }
-            if (o1 - cur > tolw) ivl_add(keep, nk, cur, o1);
-            if (nk == 0) {
+        if (lost.n > 0) {
+            Ivl<R> keep;
+            keep.n = 0;
+#pragma unroll
+            for (int k = 0; k < MAXP; ++k) { keep.a[k] = keep.b[k] = (R)0; }
+            R cur = o0;
+#pragma unroll
+            for (int q = 0; q < MAXP; ++q) {
+                if (q >= lost.n) break;
+                if (lost.a[q] - cur > tolw) ivl_add<R>(keep, cur, lost.a[q]);
+                if (lost.b[q] > cur) cur = lost.b[q];
+            }
+            if (o1 - cur > tolw) ivl_add<R>(keep, cur, o1);
+            if (keep.n == 0) {
                 ws.win[oi].flags = o.flags & ~WIN_ALIVE;
                 if (prev < 0) ws.ehead[es] = onext; else ws.win[prev].next = onext;
-                o_alive = false;
-            } else {
-                int tail = oi;
-                const R wpad = (R)Widen<R>::mu * Lr;   // outward rounding of the kept parts
-                for (int q = 0; q < nk; ++q) {
-                    R k0 = (same ? keep[q][0] : Lr - keep[q][1]) - wpad;
-                    R k1 = (same ? keep[q][1] : Lr - keep[q][0]) + wpad;
-                    k0 = k0 < (R)0 ? (R)0 : k0;
-                    k1 = k1 > Lr ? Lr : k1;
-                    if (q == 0) { ws.win[oi].b0 = k0; ws.win[oi].b1 = k1; }
-                    else {
-                        const int pid = win_alloc<R>(sm, ws.wcap);
-                        if (pid < 0) break;
-                        Win<R> piece = o;
-                        piece.b0 = k0; piece.b1 = k1;
-                        piece.next = onext;
-                        ws.win[pid] = piece;
-                        ws.win[tail].next = pid;          // keep the list order, skip the pieces
-                        tail = pid;
-                    }
-                }
-                prev = tail;
+                oi = onext;
+                continue;
             }
+            int tail = oi;
+            const R wpad = (R)Widen<R>::mu * Lr;   // outward rounding of the kept parts
+#pragma unroll
+            for (int q = 0; q < MAXP; ++q) {
+                if (q >= keep.n) break;
+                R k0 = (same ? keep.a[q] : Lr - keep.b[q]) - wpad;
+                R k1 = (same ? keep.b[q] : Lr - keep.a[q]) + wpad;
+                k0 = k0 < (R)0 ? (R)0 : k0;
+                k1 = k1 > Lr ? Lr : k1;
+                if (q == 0) { ws.win[oi].b0 = k0; ws.win[oi].b1 = k1; }
+                else {
+                    const int pid = win_alloc<R>(sm, ws.wcap);
+                    if (pid < 0) break;
+                    Win<R> piece = o;
+                    piece.b0 = k0; piece.b1 = k1;
+                    piece.next = onext;
+                    ws.win[pid] = piece;
+                    ws.win[tail].next = pid;          // keep the list order, skip the pieces
+                    tail = pid;
+                }
+            }
+            prev = tail;
         } else {
             prev = oi;
         }
-        if (!o_alive) { oi = onext; continue; }
         oi = onext;
     }
     if (err) atomicOr(&sm.err, err);
     bool added = false;
-    for (int p = 0; p < np; ++p) {
+#pragma unroll
+    for (int p = 0; p < MAXP; ++p) {
+        if (p >= pc.n) break;
         Win<R> w = c;
-        w.b0 = pc[p][0]; w.b1 = pc[p][1];
+        w.b0 = pc.a[p]; w.b1 = pc.b[p];
         w.flags = (c.flags & WIN_FIXED) | WIN_ALIVE;
-        if (!(win_key(w) < rc)) continue;
+        if (!((double)win_key<R>(w) < rc)) continue;
         const int id = win_alloc<R>(sm, ws.wcap);
         if (id < 0) break;
         w.next = ws.ehead[es];
@@ -492,6 +653,7 @@ __device__ __forceinline__ int group_rounds(bool has, int key, int lane, int& ra
 template <class R>
 __device__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, const VCand<R>& c, double rc,
                              int lane) {
+    if (!__any_sync(CSS_FULL, has)) return;
     bool claimed = false;
     int slot = -1;
     if (has) {
@@ -514,7 +676,7 @@ __device__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, co
                 ws.vtan[2 * slot] = c.tx;
                 ws.vtan[2 * slot + 1] = c.ty;
                 ws.vflag[slot] = c.fixed ? (vf | 2) : (vf & ~2);
-                if (d < vd && m.pseudo[c.v] && d < rc && !(ws.vflag[slot] & 1)) {
+                if (d < vd && d < rc && !(ws.vflag[slot] & 1)) {
                     ws.vflag[slot] |= 1;
                     const int p = atomicAdd(&sm.nemit, 1);
                     if (p < ws.emcap) ws.emit[p] = slot;
@@ -528,6 +690,7 @@ __device__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, co
 
 template <class R>
 __device__ void child_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, const Win<R>& c, double rc, int lane) {
+    if (!__any_sync(CSS_FULL, has)) return;
     bool claimed = false;
     int slot = -1;
     if (has) {
@@ -539,7 +702,7 @@ __device__ void child_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, con
     int rank;
     const int rounds = group_rounds(has, slot, lane, rank);
     for (int q = 0; q < rounds; ++q) {
-        if (has && rank == q) insert_window(m, ws, sm, slot, c, rc);
+        if (has && rank == q) insert_window<R>(m, ws, sm, slot, c, rc);
         __syncwarp();
     }
 }
@@ -550,6 +713,7 @@ template <class R>
 __device__ void emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, int lane) {
     __syncwarp();
     const int ne = min(sm.nemit, ws.emcap);
+    if (ne == 0) return;
     for (int base = 0; base < ne; base += 32) {
         const int it = base + lane;
         const bool has = it < ne;
@@ -585,13 +749,14 @@ __device__ void emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, int
                     c.sx = r.L - r.cx;
                     c.sy = -r.cy;
                     c.sig = dv;
+                    set_fast(c);
                     c.ta = tx;
                     c.tb = ty;
                     c.flags = WIN_FIXED | WIN_ALIVE;
                     c.next = -1;
                 }
             }
-            child_round(m, ws, sm, hh, c, rc, lane);
+            child_round<R>(m, ws, sm, hh, c, rc, lane);
         }
     }
     __syncwarp();
@@ -621,10 +786,13 @@ __device__ __forceinline__ double pot_u(const css_potential& p, double l) {
 
 // distance + source tangent (source-face layout) of particle j of face fl
 template <class R>
-__device__ double query(const DMesh& m, const Ws<R>& ws, int f0, double qx, double qy, int fl, const double* bj,
-                        R& tx, R& ty) {
-    const double L01 = m.lay[3 * fl], x2 = m.lay[3 * fl + 1], y2 = m.lay[3 * fl + 2];
-    const double px = bj[1] * L01 + bj[2] * x2, py = bj[2] * y2;
+__device__ double query(const DMesh& m, const Ws<R>& ws, int f0, R qx, R qy, int fl, const double* bj, R& tx,
+                        R& ty) {
+    R L01, x2, y2, dummy;
+    face_corner_f<R>(m, fl, 1, L01, dummy);
+    face_corner_f<R>(m, fl, 2, x2, y2);
+    const R b1 = (R)bj[1], b2 = (R)bj[2];
+    const R px = b1 * L01 + b2 * x2, py = b2 * y2;
     double best = __longlong_as_double(0x7ff0000000000000ll);
     bool best_fixed = true;
     const double tie = Tie<R>::rel;
@@ -633,64 +801,85 @@ __device__ double query(const DMesh& m, const Ws<R>& ws, int f0, double qx, doub
     double best_exact = best;
     tx = (R)0; ty = (R)0;
     if (fl == f0) {
-        const double dx = px - qx, dy = py - qy;
-        best = sqrt(dx * dx + dy * dy);
+        const R dx = px - qx, dy = py - qy;
+        const R d = sqrt(dx * dx + dy * dy);
+        best = (double)d;
         best_exact = best;
         best_fixed = false;
-        if (best > 0.0) { tx = (R)(dx / best); ty = (R)(dy / best); }
+        if (d > (R)0) { tx = dx / d; ty = dy / d; }
     }
     for (int k = 0; k < 3; ++k) {
         const int h = 3 * fl + k;
         const int slot = css::ht_find(ws.ekey, ws.log_eh, ws.gen, m.edge[h]);
         if (slot < 0) continue;
-        double ax, ay, bx, by;
-        css::face_corner(m, fl, k, ax, ay);
-        css::face_corner(m, fl, k + 1, bx, by);
-        const double L = m.he[h].L;
-        const double dx = (bx - ax) / L, dy = (by - ay) / L;
-        const double hx = (px - ax) * dx + (py - ay) * dy;
-        const double hy = dx * (py - ay) - dy * (px - ax);
+        R ax, ay, bx, by;
+        face_corner_f<R>(m, fl, k, ax, ay);
+        face_corner_f<R>(m, fl, k + 1, bx, by);
+        R L;
+        if (sizeof(R) == sizeof(float)) L = (R)m.he32[h].L; else L = (R)m.he[h].L;
+        const R dx = (bx - ax) / L, dy = (by - ay) / L;
+        const R hx = (px - ax) * dx + (py - ay) * dy;
+        const R hy = dx * (py - ay) - dy * (px - ax);
         // cone tolerance of the interval precision: adjacent windows stored in FP32 may
         // leave or overlap by an ulp of the edge length, which must not hide a target
-        const double tol = (double)Tol<R>::w * L;
+        const R tol = (R)Tol<R>::w * L;
         int guard = 0;
         for (int wi = ws.ehead[slot]; wi >= 0 && guard < ws.wcap; ++guard) {
             const Win<R> w = ws.win[wi];
             wi = w.next;
             if (!(w.flags & WIN_ALIVE) || w.he != h) continue;
             bool inside;
-            if (win_degen(w, L)) inside = win_degen_sees(w, L);
+            if (win_degen<R>(w, L)) inside = win_degen_sees<R>(w, L);
             else {
-                const double X = w.sx + (hx - w.sx) * (-w.sy) / (hy - w.sy);
-                inside = X >= (double)w.b0 - tol && X <= (double)w.b1 + tol;
+                const R X = fsx(w) + (hx - fsx(w)) * (-fsy(w)) / (hy - fsy(w));
+                inside = X >= w.b0 - tol && X <= w.b1 + tol;
             }
             if (!inside) continue;
-            double d = win_dist(w, hx, hy);
+            double d = (double)win_dist<R>(w, hx, hy);
             const bool direct = !(w.flags & WIN_FIXED);
             double t_tie = tie;
             double cmp_best = best;
             if (sizeof(R) == sizeof(float) && fabs(d - best) <= 1e-5 * d) {
-                const double ex = w.sig + sqrt((hx - w.sx) * (hx - w.sx) + (hy - w.sy) * (hy - w.sy));
-                d = ex;
+                // exact lengths: the target in this frame from the FP64 layout
+                double axd, ayd, bxd, byd;
+                css::face_corner(m, fl, k, axd, ayd);
+                css::face_corner(m, fl, k + 1, bxd, byd);
+                const double Ldd = m.he[h].L;
+                const double pxd = bj[1] * m.lay[3 * fl] + bj[2] * m.lay[3 * fl + 1], pyd = bj[2] * m.lay[3 * fl + 2];
+                const double ddx = (bxd - axd) / Ldd, ddy = (byd - ayd) / Ldd;
+                const double hxd = (pxd - axd) * ddx + (pyd - ayd) * ddy;
+                const double hyd = ddx * (pyd - ayd) - ddy * (pxd - axd);
+                d = win_dist_exact<R>(w, hxd, hyd);
                 cmp_best = best_exact;
                 t_tie = 1e-13;
             }
             if (d < cmp_best - t_tie * d || (d <= cmp_best + t_tie * d && direct && best_fixed)) {
                 best = d < cmp_best ? d : cmp_best;
-                best_exact = sizeof(R) == sizeof(float)
-                                 ? w.sig + sqrt((hx - w.sx) * (hx - w.sx) + (hy - w.sy) * (hy - w.sy))
-                                 : d;
+                if (sizeof(R) == sizeof(float)) {
+                    double axd, ayd, bxd, byd;
+                    css::face_corner(m, fl, k, axd, ayd);
+                    css::face_corner(m, fl, k + 1, bxd, byd);
+                    const double Ldd = m.he[h].L;
+                    const double pxd = bj[1] * m.lay[3 * fl] + bj[2] * m.lay[3 * fl + 1], pyd = bj[2] * m.lay[3 * fl + 2];
+                    const double ddx = (bxd - axd) / Ldd, ddy = (byd - ayd) / Ldd;
+                    best_exact = win_dist_exact<R>(w, (pxd - axd) * ddx + (pyd - ayd) * ddy,
+                                                   ddx * (pyd - ayd) - ddy * (pxd - axd));
+                } else {
+                    best_exact = d;
+                }
                 best_fixed = !direct;
-                win_tangent(w, hx, hy, tx, ty);
+                win_tangent<R>(w, hx, hy, tx, ty);
             }
         }
     }
     for (int k = 0; k < 3; ++k) {
-        const int slot = css::ht_find(ws.vkey, ws.log_vh, ws.gen, m.fv[3 * fl + k]);
+        const int32_t v = m.fv[3 * fl + k];
+        if (!m.pseudo[v]) continue;   // only pseudo-source vertices can bend a shortest path
+        const int slot = css::ht_find(ws.vkey, ws.log_vh, ws.gen, v);
         if (slot < 0) continue;
-        double vx, vy;
-        css::face_corner(m, fl, k, vx, vy);
-        const double d = ws.vdist[slot] + sqrt((px - vx) * (px - vx) + (py - vy) * (py - vy));
+        R vx, vy;
+        face_corner_f<R>(m, fl, k, vx, vy);
+        const double d = ws.vdist[slot] + (double)sqrt((px - vx) * (px - vx) + (py - vy) * (py - vy));
         if (d < best - tie * d) { best = d; best_exact = d; best_fixed = true; tx = ws.vtan[2 * slot]; ty = ws.vtan[2 * slot + 1]; }
     }
     return best;
@@ -703,25 +892,26 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
     const double rc = J.rc;
     const int f0 = J.face[i];
     const double* b = J.bary + 3 * (size_t)i;
-    const double qx = b[1] * m.lay[3 * f0] + b[2] * m.lay[3 * f0 + 1];
-    const double qy = b[2] * m.lay[3 * f0 + 2];
+    const double qxd = b[1] * m.lay[3 * f0] + b[2] * m.lay[3 * f0 + 1];
+    const double qyd = b[2] * m.lay[3 * f0 + 2];
     if (lane == 0) { sm.nwin = 0; sm.head = 0; sm.nface = 0; sm.nemit = 0; sm.err = 0; }
     __syncwarp();
     if (lane == 0) face_add(ws, sm, f0);
-    {   // the source's own corners
+    {   // the source's own pseudo-source corners
         VCand<R> c;
-        const bool has = lane < 3;
-        if (has) {
+        bool has = false;
+        if (lane < 3) {
+            c.v = m.fv[3 * f0 + lane];
+            has = m.pseudo[c.v] != 0;
             double vx, vy;
             css::face_corner(m, f0, lane, vx, vy);
-            const double dx = vx - qx, dy = vy - qy, d = sqrt(dx * dx + dy * dy);
-            c.v = m.fv[3 * f0 + lane];
+            const double dx = vx - qxd, dy = vy - qyd, d = sqrt(dx * dx + dy * dy);
             c.fixed = 0;
             c.d = d;
             c.tx = (R)(d > 0.0 ? dx / d : 1.0);
             c.ty = (R)(d > 0.0 ? dy / d : 0.0);
         }
-        vertex_round(m, ws, sm, has, c, rc, lane);
+        vertex_round<R>(m, ws, sm, has, c, rc, lane);
     }
     {   // one window per edge of the source face, covering the whole edge
         Win<R> c;
@@ -736,23 +926,24 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
                 css::face_corner(m, f0, lane + 1, bx, by);
                 const double L = m.he[h].L;
                 const double dx = (bx - ax) / L, dy = (by - ay) / L;
-                const double hx = (qx - ax) * dx + (qy - ay) * dy;
-                const double hy = dx * (qy - ay) - dy * (qx - ax);
+                const double hx = (qxd - ax) * dx + (qyd - ay) * dy;
+                const double hy = dx * (qyd - ay) - dy * (qxd - ax);
                 c.he = tw;
                 c.b0 = (R)0;
                 c.b1 = (R)m.he[tw].L;
                 c.sx = L - hx;
                 c.sy = hy > 0.0 ? -hy : 0.0;
                 c.sig = 0.0;
+                set_fast(c);
                 c.ta = (R)(-dx);
                 c.tb = (R)dy;
                 c.flags = WIN_ALIVE;
                 c.next = -1;
             }
         }
-        child_round(m, ws, sm, has, c, rc, lane);
+        child_round<R>(m, ws, sm, has, c, rc, lane);
     }
-    emit_round(m, ws, sm, rc, lane);
+    emit_round<R>(m, ws, sm, rc, lane);
     unsigned long long n_prop = 0;
     for (int wave = 0;; ++wave) {
         __syncwarp();
@@ -765,25 +956,26 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
         bool act = false;
         if (idx < nwin) {
             w = ws.win[idx];
-            act = (w.flags & WIN_ALIVE) && !(w.flags & WIN_DONE) && win_key(w) < rc;
+            act = (w.flags & WIN_ALIVE) && !(w.flags & WIN_DONE) && (double)win_key<R>(w) < rc;
             if (act) ws.win[idx].flags = w.flags | WIN_DONE;
         }
         VCand<R> vc[3];
         Win<R> ch[2];
         int nvc = 0, nch = 0;
-        if (act) propagate(m, w, rc, vc, nvc, ch, nch);
+        if (act) propagate<R>(m, w, rc, vc, nvc, ch, nch);
         n_prop += __popc(__ballot_sync(CSS_FULL, act));
         __syncwarp();
 #pragma unroll
-        for (int q = 0; q < 3; ++q) vertex_round(m, ws, sm, q < nvc, vc[q], rc, lane);
+        for (int q = 0; q < 3; ++q) vertex_round<R>(m, ws, sm, q < nvc, vc[q], rc, lane);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) child_round(m, ws, sm, q < nch, ch[q], rc, lane);
-        emit_round(m, ws, sm, rc, lane);
+        for (int q = 0; q < 2; ++q) child_round<R>(m, ws, sm, q < nch, ch[q], rc, lane);
+        emit_round<R>(m, ws, sm, rc, lane);
     }
     __syncwarp();
     const int err = sm.err;
     const int nface = min(sm.nface, ws.fcap);
     // ---- target evaluation (+ forces)
+    const R qx = (R)qxd, qy = (R)qyd;
     double fx = 0.0, fy = 0.0, en = 0.0;
     int npair = 0;
     const bool wp = J.want_pairs != 0;
@@ -815,7 +1007,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
             if (t < total) {
                 j = J.fitems[o_st + (t - o_ex)];
                 if (j != i) {
-                    d = query(m, ws, f0, qx, qy, o_fl, J.bary + 3 * (size_t)j, tx, ty);
+                    d = query<R>(m, ws, f0, qx, qy, o_fl, J.bary + 3 * (size_t)j, tx, ty);
                     ispair = d < rc;
                 }
             }
@@ -865,7 +1057,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
 }
 
 template <class R>
-__global__ void __launch_bounds__(512) k_geodesic(cssi::GeoJob job0, const cssi::GeoJob* jobs,
+__global__ void __launch_bounds__(256) k_geodesic(cssi::GeoJob job0, const cssi::GeoJob* jobs,
                                                   const int32_t* job_of_item, const int32_t* src_of_item,
                                                   int32_t nitems, cssi::GeoWs g, int* work, int* status,
                                                   unsigned long long* counters) {

@@ -117,7 +117,7 @@ __global__ void k_faces(const double* X, const int32_t* F, int64_t nf, int perio
 }
 
 __global__ void k_halfedges(const double* lay, const int32_t* F, const int32_t* twin, int64_t nf, HeRec* he,
-                            uint8_t* bnd, int32_t* ring_cnt) {
+                            css::HeRec32* he32, float* lay32, uint8_t* bnd, int32_t* ring_cnt) {
     int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (h >= 3 * nf) return;
     int64_t f = h / 3;
@@ -144,6 +144,12 @@ __global__ void k_halfedges(const double* lay, const int32_t* F, const int32_t* 
     r.tl = twin[3 * f + (k + 2) % 3];
     r.tr = twin[3 * f + (k + 1) % 3];
     he[h] = r;
+    css::HeRec32 q;
+    q.L = (float)r.L; q.cx = (float)r.cx; q.cy = (float)r.cy;
+    q.cl = (float)r.cl; q.sl = (float)r.sl; q.cr = (float)r.cr; q.sr = (float)r.sr;
+    q.pad = 0;
+    he32[h] = q;
+    lay32[h] = (float)lay[h];   // 3 per face: the same indexing as the half-edges
     if (twin[h] < 0) { bnd[F[h]] = 1; bnd[F[3 * f + (k + 1) % 3]] = 1; }
     atomicAdd(ring_cnt + F[h], 1);
 }
@@ -201,6 +207,8 @@ css::DMesh css_mesh::view() const {
     d.bnd = bnd;
     d.ring_start = ring_start;
     d.ring = ring;
+    d.he32 = he32;
+    d.lay32 = lay32;
     return d;
 }
 
@@ -253,6 +261,8 @@ int build_mesh(css_ctx* ctx, const double* dX, int64_t nv, const int32_t* dF, in
     CK(cudaMalloc(&m->ring_start, (nv + 1) * sizeof(int32_t)));
     CK(cudaMalloc(&m->ring, nh * sizeof(int32_t)));
     CK(cudaMalloc(&m->X, 3 * nv * sizeof(double)));
+    CK(cudaMalloc(&m->he32, nh * sizeof(css::HeRec32)));
+    CK(cudaMalloc(&m->lay32, 3 * nf * sizeof(float)));
     CK(cudaMalloc(&ring_cnt, (nv + 1) * sizeof(int32_t)));
     CK(cudaMalloc(&tmp, scan_tmp_ints(nv + 1) * sizeof(int32_t)));
     CK(cudaMemcpyAsync(m->X, dX, 3 * nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -278,7 +288,7 @@ int build_mesh(css_ctx* ctx, const double* dX, int64_t nv, const int32_t* dF, in
     if (hflag & (4 | 8)) { ctx->err = "mesh_upload: an edge is shared by more than two faces"; rc = CSS_ERR_NONMANIFOLD; goto done; }
     if (hflag & 16) { ctx->err = "mesh_upload: inconsistent face orientation"; rc = CSS_ERR_NONMANIFOLD; goto done; }
     if (hflag & 32) { ctx->err = "mesh_upload: degenerate (zero-area) face"; rc = CSS_ERR_NONMANIFOLD; goto done; }
-    k_halfedges<<<nblk(nh), 256, 0, st>>>(m->lay, dF, m->twin, nf, m->he, m->bnd, ring_cnt);
+    k_halfedges<<<nblk(nh), 256, 0, st>>>(m->lay, dF, m->twin, nf, m->he, m->he32, m->lay32, m->bnd, ring_cnt);
     CK(launch_scan_i32(ring_cnt, m->ring_start, nv + 1, tmp, st));
     CK(cudaMemsetAsync(ring_cnt, 0, (nv + 1) * sizeof(int32_t), st));
     k_ring_scatter<<<nblk(nh), 256, 0, st>>>(dF, nf, m->ring_start, ring_cnt, m->ring);
