@@ -68,18 +68,19 @@ int next_pow2(int x) {
 }
 
 // ---- workspace for the persistent neighbour/force kernel
-int ensure_ws(css_ctx* c, int precision, GeoWs* out, int* nctas) {
-    int bps = cssi::geodesic_blocks_per_sm(precision, c->warps_per_cta);
+int ensure_ws(css_ctx* c, int precision, int shared, GeoWs* out, int* nctas) {
+    int bps = cssi::geodesic_blocks_per_sm(precision, c->warps_per_cta, shared);
     if (bps < 1) bps = 1;
     const int ncta = c->sm_count * bps;
     const int nwarps = ncta * c->warps_per_cta;
     GeoWs g{};
+    g.shared = shared;
     g.stride = cssi::geo_ws_bytes_per_warp(precision, c->win_cap, &g.log_eh, &g.log_vh, &g.log_fh, &g.fcap, &g.emcap);
     g.wcap = c->win_cap;
     g.nwarps = nwarps;
     const size_t need = g.stride * (size_t)nwarps;
     // a layout change re-zeroes the workspace so old bytes never look like valid hash tags
-    const int64_t key = (int64_t)precision * 1000003 + (int64_t)c->win_cap * 31 + c->warps_per_cta;
+    const int64_t key = (int64_t)precision * 1000003 + (int64_t)c->win_cap * 31 + c->warps_per_cta + 17 * shared;
     const bool relayout = (need > c->ws_bytes) || (c->ws_warps < nwarps) || (c->ws_key != key);
     if (need > c->ws_bytes) {
         cudaFree(c->ws);
@@ -176,11 +177,15 @@ int read_status(css_ctx* c, int* status) {
     return CSS_OK;
 }
 
-// grow the capacity that overflowed; false when nothing can grow any more
-bool grow_for(css_ctx* c, int status, int* retries) {
+// grow the capacity that overflowed; false when nothing can grow any more.  A table
+// overflow of a launch with shared-memory tables sets *to_global instead: the patch is
+// too large for them and the launch is repeated with the global tables.
+bool grow_for(css_ctx* c, int status, int* retries, int shared, bool* to_global) {
     ++*retries;
+    *to_global = false;
     if (*retries > MAX_RETRY) return false;
     bool grown = false;
+    if ((status & css::ST_HASH_OVERFLOW) && shared) { *to_global = true; grown = true; status &= ~css::ST_HASH_OVERFLOW; }
     if (status & (css::ST_WIN_OVERFLOW | css::ST_HASH_OVERFLOW | css::ST_ITER_LIMIT)) {
         if (c->win_cap >= WIN_CAP_MAX) return false;
         c->win_cap *= 2;
@@ -189,6 +194,8 @@ bool grow_for(css_ctx* c, int status, int* retries) {
     if (status & css::ST_PAIR_OVERFLOW) { c->pair_cap *= 2; grown = true; }
     return grown;
 }
+
+int use_shared(const css_parts* p) { return p->ctx->shared_tables && !p->global_tables; }
 
 int status_error(css_ctx* c, int status) {
     if (status & (css::ST_WIN_OVERFLOW | css::ST_HASH_OVERFLOW)) {
@@ -211,7 +218,8 @@ int run_geo(css_parts* p, double rc, int prec, int want_pairs, int want_forces, 
         if (want_pairs) { int rc2 = ensure_pairs(p, c->pair_cap); if (rc2) return rc2; }
         GeoWs g;
         int nctas = 0;
-        int rc1 = ensure_ws(c, prec, &g, &nctas);
+        const int shared = use_shared(p);
+        int rc1 = ensure_ws(c, prec, shared, &g, &nctas);
         if (rc1) return rc1;
         TRY(c, "reset", cudaMemsetAsync(c->dscal + 1, 0, sizeof(int), c->stream));
         TRY(c, "reset", cudaMemsetAsync(c->depot, 0, sizeof(double), c->stream));
@@ -222,7 +230,9 @@ int run_geo(css_parts* p, double rc, int prec, int want_pairs, int want_forces, 
         if (rc1) return rc1;
         if (status == 0) return CSS_OK;
         c->last_counters[4] += 1;
-        if (!grow_for(c, status, &retries)) return status_error(c, status);
+        bool to_global = false;
+        if (!grow_for(c, status, &retries, shared, &to_global)) return status_error(c, status);
+        if (to_global) p->global_tables = 1;
     }
 }
 
@@ -619,7 +629,8 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
         TRY(c, "snapshot", snap_take(p));
         GeoWs g;
         int nctas = 0;
-        rc = ensure_ws(c, precision, &g, &nctas);
+        const int shared = use_shared(p);
+        rc = ensure_ws(c, precision, shared, &g, &nctas);
         if (rc) break;
         TRY(c, "reset", cudaMemsetAsync(c->dscal + 1, 0, sizeof(int), st));
         TRY(c, "reset", cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), st));
@@ -628,7 +639,7 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
             std::string key((const char*)pot, sizeof(*pot));
             key.append((const char*)it, sizeof(*it));
             key.append((const char*)&r_c, sizeof(r_c));
-            const int64_t shape[4] = {precision, c->ws_key, nctas, (int64_t)(uintptr_t)c->ws};
+            const int64_t shape[5] = {precision, c->ws_key, nctas, (int64_t)(uintptr_t)c->ws, shared};
             key.append((const char*)shape, sizeof(shape));
             if (!p->graph || p->graph_key != key) {
                 if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
@@ -648,7 +659,9 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
         rc = read_status(c, &status);
         if (rc) break;
         if (status == 0) break;
-        if (!grow_for(c, status, &retries)) { rc = status_error(c, status); break; }
+        bool to_global = false;
+        if (!grow_for(c, status, &retries, shared, &to_global)) { rc = status_error(c, status); break; }
+        if (to_global) p->global_tables = 1;
         TRY(c, "restore", snap_restore(p));
     }
     if (noise && !is_device_ptr(noise)) cudaFree(dnoise);
@@ -756,7 +769,9 @@ int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator*
         for (css_parts* p : b->sets) TRY(c, "snapshot", snap_take(p));
         GeoWs g;
         int nctas = 0;
-        int rc = ensure_ws(c, precision, &g, &nctas);
+        int shared = c->shared_tables;
+        for (css_parts* p : b->sets) shared = shared && !p->global_tables;
+        int rc = ensure_ws(c, precision, shared, &g, &nctas);
         if (rc) return rc;
         TRY(c, "reset", cudaMemsetAsync(c->dscal + 1, 0, sizeof(int), st));
         TRY(c, "reset", cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), st));
@@ -783,7 +798,9 @@ int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator*
         rc = read_status(c, &status);
         if (rc) return rc;
         if (status == 0) break;
-        if (!grow_for(c, status, &retries)) return status_error(c, status);
+        bool to_global = false;
+        if (!grow_for(c, status, &retries, shared, &to_global)) return status_error(c, status);
+        if (to_global) for (css_parts* p : b->sets) p->global_tables = 1;
         for (css_parts* p : b->sets) TRY(c, "restore", snap_restore(p));
     }
     for (css_parts* p : b->sets) {

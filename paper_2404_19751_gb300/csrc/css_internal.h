@@ -24,6 +24,7 @@ struct css_ctx {
     int warps_per_cta = 4;
     int win_cap = 2048;              // windows per warp workspace
     int pair_cap = 64;               // pairs per source slab
+    int shared_tables = 1;           // try shared-memory tables first
     // small device scalars: [0] work counter, [1] status, [2..] counters
     int* dscal = nullptr;
     unsigned long long* dcount = nullptr;   // 8 counters
@@ -89,6 +90,7 @@ struct css_parts {
     double* pd = nullptr;
     double* pt = nullptr;
     int pair_cap_alloc = 0;
+    int global_tables = 0;      // this set's patches overflowed the shared-memory tables
     // captured single-step graph and the launch parameters it was captured for
     cudaGraphExec_t graph = nullptr;
     std::string graph_key;
@@ -120,6 +122,7 @@ struct GeoJob {
 };
 
 struct GeoWs {
+    int shared;              // keyed tables in shared memory (else in the global slice)
     char* base;
     size_t stride;           // bytes per warp
     int log_eh, log_vh, log_fh;
@@ -135,7 +138,7 @@ cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const int32
                             const int32_t* src_of_item, int32_t nitems, int precision,
                             const GeoWs& ws, int warps_per_cta, int nctas, int* work_counter,
                             int* status, unsigned long long* counters, cudaStream_t st);
-int geodesic_blocks_per_sm(int precision, int warps_per_cta);
+int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared);
 cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd,
                                  const double* pt, int pair_cap, const int64_t* row_start,
                                  int32_t* out_j, double* out_d, double* out_t, cudaStream_t st);

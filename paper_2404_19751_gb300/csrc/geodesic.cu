@@ -39,7 +39,7 @@ using css::HeRec;
 constexpr int WIN_ALIVE = 1;
 constexpr int WIN_DONE = 2;    // already unfolded
 constexpr int WIN_FIXED = 4;   // tangent fixed (descends from a pseudo-source vertex)
-constexpr int MAXP = 6;        // interval pieces one insertion may hold
+constexpr int MAXP = 4;        // interval pieces one insertion may hold
 constexpr int MAX_WARPS_CTA = 16;
 
 // Window record.  The pseudo-source s and its geodesic length sigma are the accumulated
@@ -107,8 +107,16 @@ struct WarpSm {
     int nwin, head, nface, nemit, err;
 };
 
+// Per-warp working state.  The keyed tables (edge heads, pseudo-source vertices, face set)
+// live either in shared memory -- plain 32-bit keys, cleared for every source, for patches
+// that fit -- or in the warp's global workspace slice with generation-tagged 64-bit keys;
+// the window pool is always in the global slice.
 template <class R>
 struct Ws {
+    bool shared;
+    int32_t* sekey;
+    int32_t* svkey;
+    int32_t* sfkey;
     unsigned long long* ekey;
     int32_t* ehead;
     unsigned long long* vkey;
@@ -165,7 +173,98 @@ __device__ inline Ws<R> ws_bind(const cssi::GeoWs& g, int warp) {
     w.log_eh = g.log_eh; w.log_vh = g.log_vh; w.log_fh = g.log_fh;
     w.wcap = g.wcap; w.fcap = g.fcap; w.emcap = g.emcap;
     w.gen = 0;
+    w.shared = false;
+    w.sekey = w.svkey = w.sfkey = nullptr;
     return w;
+}
+
+// shared-memory tables of one warp (sizes are powers of two; overflow makes the host rerun
+// the launch with the global tables)
+constexpr int SH_LOG_EH = 9, SH_LOG_VH = 8, SH_LOG_FH = 9;
+constexpr int SH_FCAP = 512, SH_EMCAP = 256;
+
+template <class R>
+__host__ __device__ constexpr size_t sh_bytes_per_warp() {
+    return (size_t)(1 << SH_LOG_EH) * 8 + (size_t)(1 << SH_LOG_VH) * (4 + 8 + 2 * sizeof(R) + 4) +
+           (size_t)(1 << SH_LOG_FH) * 4 + (size_t)SH_FCAP * 4 + (size_t)SH_EMCAP * 4;
+}
+
+template <class R>
+__device__ inline void ws_bind_shared(Ws<R>& w, unsigned char* base) {
+    unsigned char* p = base;
+    w.sekey = (int32_t*)p; p += (1 << SH_LOG_EH) * 4;
+    w.ehead = (int32_t*)p; p += (1 << SH_LOG_EH) * 4;
+    w.vdist = (double*)p; p += (1 << SH_LOG_VH) * 8;
+    w.vtan = (R*)p; p += (1 << SH_LOG_VH) * 2 * sizeof(R);
+    w.svkey = (int32_t*)p; p += (1 << SH_LOG_VH) * 4;
+    w.vflag = (int32_t*)p; p += (1 << SH_LOG_VH) * 4;
+    w.sfkey = (int32_t*)p; p += (1 << SH_LOG_FH) * 4;
+    w.flist = (int32_t*)p; p += SH_FCAP * 4;
+    w.emit = (int32_t*)p;
+    w.vvid = w.svkey;   // the key is the vertex id
+    w.log_eh = SH_LOG_EH; w.log_vh = SH_LOG_VH; w.log_fh = SH_LOG_FH;
+    w.fcap = SH_FCAP; w.emcap = SH_EMCAP;
+    w.shared = true;
+}
+
+__device__ __forceinline__ int sh_insert(int32_t* keys, int logcap, int32_t key, bool& claimed) {
+    const uint32_t mask = (1u << logcap) - 1u;
+    uint32_t slot = ((uint32_t)key * 2654435761u) >> (32 - logcap);
+    claimed = false;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        int32_t cur = *(volatile int32_t*)(keys + slot);
+        if (cur == key) return (int)slot;
+        if (cur == -1) {
+            const int32_t prev = atomicCAS(keys + slot, -1, key);
+            if (prev == -1) { claimed = true; return (int)slot; }
+            if (prev == key) return (int)slot;
+        }
+        slot = (slot + 1u) & mask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int sh_find(const int32_t* keys, int logcap, int32_t key) {
+    const uint32_t mask = (1u << logcap) - 1u;
+    uint32_t slot = ((uint32_t)key * 2654435761u) >> (32 - logcap);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const int32_t cur = *(volatile const int32_t*)(keys + slot);
+        if (cur == key) return (int)slot;
+        if (cur == -1) return -1;
+        slot = (slot + 1u) & mask;
+    }
+    return -1;
+}
+
+template <class R>
+__device__ __forceinline__ int ws_eins(Ws<R>& ws, int32_t key, bool& claimed) {
+    return ws.shared ? sh_insert(ws.sekey, ws.log_eh, key, claimed) : css::ht_insert(ws.ekey, ws.log_eh, ws.gen, key, claimed);
+}
+template <class R>
+__device__ __forceinline__ int ws_efind(const Ws<R>& ws, int32_t key) {
+    return ws.shared ? sh_find(ws.sekey, ws.log_eh, key) : css::ht_find(ws.ekey, ws.log_eh, ws.gen, key);
+}
+template <class R>
+__device__ __forceinline__ int ws_vins(Ws<R>& ws, int32_t key, bool& claimed) {
+    return ws.shared ? sh_insert(ws.svkey, ws.log_vh, key, claimed) : css::ht_insert(ws.vkey, ws.log_vh, ws.gen, key, claimed);
+}
+template <class R>
+__device__ __forceinline__ int ws_vfind(const Ws<R>& ws, int32_t key) {
+    return ws.shared ? sh_find(ws.svkey, ws.log_vh, key) : css::ht_find(ws.vkey, ws.log_vh, ws.gen, key);
+}
+template <class R>
+__device__ __forceinline__ int ws_fins(Ws<R>& ws, int32_t key, bool& claimed) {
+    return ws.shared ? sh_insert(ws.sfkey, ws.log_fh, key, claimed) : css::ht_insert(ws.fkey, ws.log_fh, ws.gen, key, claimed);
+}
+
+// forget the previous source's shared tables
+template <class R>
+__device__ __forceinline__ void ws_clear_shared(Ws<R>& ws, int lane) {
+    if (!ws.shared) return;
+    for (int k = lane; k < (1 << SH_LOG_EH); k += 32) ws.sekey[k] = -1;
+    for (int k = lane; k < (1 << SH_LOG_VH); k += 32) ws.svkey[k] = -1;
+    for (int k = lane; k < (1 << SH_LOG_FH); k += 32) ws.sfkey[k] = -1;
+    __syncwarp();
 }
 
 // ------------------------------------------------------------------ window geometry
@@ -281,8 +380,8 @@ struct VCand {
 // Unfold window W into the next face: distance candidates for the pseudo-source vertices it
 // reaches (paths through any other vertex can be shortened, Sec. 2.2) and at most two children.
 template <class R>
-__device__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* vc, int& nvc, Win<R>* ch,
-                          int& nch) {
+__device__ __noinline__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* vc, int& nvc,
+                                       Win<R>* ch, int& nch) {
     nvc = 0;
     nch = 0;
     const int h = W.he;
@@ -440,7 +539,7 @@ __device__ __forceinline__ void ivl_add(Ivl<R>& L, R x0, R x1, bool cover = true
 template <class R>
 __device__ __forceinline__ void face_add(Ws<R>& ws, WarpSm& sm, int32_t f) {
     bool claimed;
-    int s = css::ht_insert(ws.fkey, ws.log_fh, ws.gen, f, claimed);
+    int s = ws_fins<R>(ws, f, claimed);
     if (s < 0) { atomicOr(&sm.err, css::ST_HASH_OVERFLOW); return; }
     if (claimed) {
         int p = atomicAdd(&sm.nface, 1);
@@ -468,7 +567,11 @@ __device__ __forceinline__ int dominance_f32(float csx, float csy, float csig, f
     const float dcl = sqrtf((lo - csx) * (lo - csx) + csy * csy), dch = sqrtf((hi - csx) * (hi - csx) + csy * csy);
     const float dol = sqrtf((lo - osx) * (lo - osx) + osy * osy), doh = sqrtf((hi - osx) * (hi - osx) + osy * osy);
     const float Dlo = (csig + dcl) - (osig + dol), Dhi = (csig + dch) - (osig + doh);
-    const float E = 2.4e-6f * (csig + osig + fmaxf(dcl, dch) + fmaxf(dol, doh)) + 1e-30f;
+    // rounding margin: the FP32 copies of s, sigma and the interval ends carry 2^-24
+    // relative errors, every evaluated distance a few more; 1e-6 of the sum of magnitudes
+    // bounds the error of each difference with ample slack
+    const float E = 4.8e-7f * (fabsf(csx) + fabsf(csy) + fabsf(osx) + fabsf(osy) + 2.f * (fabsf(lo) + fabsf(hi)) +
+                               csig + osig + dcl + dch + dol + doh) + 1e-30f;
     const bool pos = Dlo > E && Dhi > E, neg = Dlo < -E && Dhi < -E;
     if (!pos && !neg) return CMP_SPLIT;
     if (!(dcl > 0.f && dch > 0.f && dol > 0.f && doh > 0.f)) return CMP_SPLIT;
@@ -491,15 +594,148 @@ __device__ __forceinline__ int dominance_f32(float csx, float csy, float csig, f
     return ub < -E ? CMP_CANDIDATE : CMP_SPLIT;
 }
 
+// FP32 location of the equal-distance points of two windows on the overlap (coordinates
+// centred on the overlap to keep the squared terms small) and the winner of each piece,
+// each confirmed by an evaluated distance difference beyond the rounding margin.  Returns
+// false when some piece cannot be decided in FP32 (then the FP64 split is used).
+__device__ __forceinline__ bool split_f32(float csx, float csy, float csig, float osx, float osy, float osig, float lo,
+                                          float hi, float* bp, bool* cwin, int& npieces) {
+    const float xm = 0.5f * (lo + hi);
+    const float ax = csx - xm, bx = osx - xm, l0 = lo - xm, h0 = hi - xm;
+    const float del = osig - csig;
+    const float al = bx - ax;
+    const float be = (ax * ax + csy * csy) - (bx * bx + osy * osy) - del * del;
+    const float c2 = del * del - al * al;
+    const float c1 = -(2.f * del * del * bx + al * be);
+    const float c0 = del * del * (bx * bx + osy * osy) - 0.25f * be * be;
+    float r[2];
+    int nc = 0;
+    const float scale = fabsf(c2) + fabsf(c1) / (fabsf(h0) + fabsf(l0) + 1e-30f) + 1e-30f;
+    if (fabsf(c2) <= 1e-6f * scale) {
+        if (c1 != 0.f) r[nc++] = -c0 / c1;
+    } else {
+        float disc = c1 * c1 - 4.f * c2 * c0;
+        if (disc < 0.f) disc = 0.f;
+        const float sq = sqrtf(disc);
+        const float qq = -0.5f * (c1 + (c1 >= 0.f ? sq : -sq));
+        if (qq != 0.f) { r[nc++] = qq / c2; r[nc++] = c0 / qq; }
+        else r[nc++] = -c1 / (2.f * c2);
+    }
+    bp[0] = lo;
+    int nb = 1;
+    float ra = 2.f * hi, rb = 2.f * hi;   // sorted roots inside (lo, hi)
+    if (nc > 0 && r[0] + xm > lo && r[0] + xm < hi) ra = r[0] + xm;
+    if (nc > 1 && r[1] + xm > lo && r[1] + xm < hi) { const float t = r[1] + xm; if (t < ra) { rb = ra; ra = t; } else rb = t; }
+    if (ra < hi) bp[nb++] = ra;
+    if (rb < hi) bp[nb++] = rb;
+    bp[nb] = hi;
+    npieces = nb;
+    const float E = 4.8e-7f * (fabsf(csx) + fabsf(csy) + fabsf(osx) + fabsf(osy) + 2.f * (fabsf(lo) + fabsf(hi)) + csig + osig) +
+                    1e-30f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        if (q >= nb) break;
+        const float x = 0.5f * (bp[q] + bp[q + 1]);
+        const float dc = csig + sqrtf((x - csx) * (x - csx) + csy * csy);
+        const float dd = dc - (osig + sqrtf((x - osx) * (x - osx) + osy * osy));
+        if (!(fabsf(dd) > E + 4.8e-7f * 2.f * dc)) return false;
+        cwin[q] = dd < 0.f;
+    }
+    return true;
+}
+
+// Exact split of an overlap [lo, hi] between candidate (a, sa) and existing (b, sb): the
+// equal-distance points in FP64, the winner of each piece decided in FP32 when the evaluated
+// difference clears its rounding margin, else in FP64 with the exact tie rule (a direct
+// window beats one descending from a pseudo-source).  Returns the breakpoints and, per piece,
+// whether the candidate wins.
+__device__ __noinline__ int split_exact(double ax, double ay, double sa, double bx, double by, double sb, double lo,
+                                        double hi, bool c_direct_o_fixed, double* bp, bool* cwin) {
+    if (__double_as_longlong(sa) == __double_as_longlong(sb)) {
+        // equal path lengths to both pseudo-sources: the candidate is shorter on one side of the
+        // perpendicular bisector of a and b, so the overlap splits at most once, at the point
+        // where the bisector meets the edge line (x - a_x)^2 + a_y^2 = (x - b_x)^2 + b_y^2
+        bp[0] = lo;
+        if (ax == bx) {   // D(x) = |x-a| - |x-b| has the sign of |a_y| - |b_y| everywhere
+            bp[1] = hi;
+            const double d = fabs(ay) - fabs(by);
+            cwin[0] = d < 0.0 || (d == 0.0 && c_direct_o_fixed);
+            return 1;
+        }
+        const double xs = 0.5 * (ax + bx) + 0.5 * (by - ay) * (by + ay) / (bx - ax);
+        const bool c_left = ax < bx;   // the candidate wins for x < xs iff a_x < b_x
+        if (xs > lo && xs < hi) {
+            bp[1] = xs; bp[2] = hi;
+            cwin[0] = c_left; cwin[1] = !c_left;
+            return 2;
+        }
+        bp[1] = hi;
+        cwin[0] = (xs >= hi) ? c_left : !c_left;
+        return 1;
+    }
+    double r0 = 0.0, r1 = 0.0;
+    const int nr = equal_points(ax, ay, sa, bx, by, sb, lo, hi, r0, r1);
+    bp[0] = lo;
+    bp[1] = nr > 0 ? r0 : hi;
+    bp[2] = nr > 1 ? r1 : hi;
+    bp[nr + 1] = hi;
+    const float fax = (float)ax, fay = (float)ay, fsa = (float)sa, fbx = (float)bx, fby = (float)by, fsb = (float)sb;
+    const float E = 4.8e-7f * (fabsf(fax) + fabsf(fay) + fabsf(fbx) + fabsf(fby) + 2.f * (fabsf((float)lo) + fabsf((float)hi)) +
+                               fsa + fsb) + 1e-30f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        if (q > nr) break;
+        const double xmd = 0.5 * (bp[q] + bp[q + 1]);
+        const float xm = (float)xmd;
+        const float dcf = fsa + sqrtf((xm - fax) * (xm - fax) + fay * fay);
+        const float ddf = dcf - (fsb + sqrtf((xm - fbx) * (xm - fbx) + fby * fby));
+        if (fabsf(ddf) > E + 9.6e-7f * dcf) { cwin[q] = ddf < 0.f; continue; }
+        const double dc = sa + sqrt((xmd - ax) * (xmd - ax) + ay * ay);
+        const double dd = dc - (sb + sqrt((xmd - bx) * (xmd - bx) + by * by));
+        const double tie = 1e-13;
+        cwin[q] = (dd < -tie * dc) || (dd <= tie * dc && c_direct_o_fixed);
+    }
+    return nr + 1;
+}
+
+// bit-identical pseudo-source and length: the same path family, equal everywhere
+template <class R>
+__device__ __forceinline__ bool same_family(const Win<R>& a, const Win<R>& b) {
+    return __double_as_longlong(a.sx) == __double_as_longlong(b.sx) &&
+           __double_as_longlong(a.sy) == __double_as_longlong(b.sy) &&
+           __double_as_longlong(a.sig) == __double_as_longlong(b.sig);
+}
+
 // Insert candidate window c on its edge (list slot es), intersecting it with every window
 // already on the edge from either side: on each overlap both keep only where they carry
 // the smaller distance.  Executed by one lane per edge.
 template <class R>
-__device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win<R> c, double rc) {
+__device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win<R> c, double rc);
+
+template <class R>
+__device__ __forceinline__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, const Win<R>& c0,
+                                              double rc) {
+    if (ws.ehead[es] >= 0) { insert_window_general<R>(m, ws, sm, es, c0, rc); return; }
+    // first window on this edge: nothing to intersect with
+    Win<R> c = c0;
+    const R Lr = sizeof(R) == sizeof(float) ? (R)m.he32[c.he].L : (R)m.he[c.he].L;
+    if (c.b0 < (R)0) c.b0 = (R)0;
+    if (c.b1 > Lr) c.b1 = Lr;
+    if (!(c.b1 - c.b0 > (R)Tol<R>::w * Lr) || !((double)win_key<R>(c) < rc)) return;
+    const int id = win_alloc<R>(sm, ws.wcap);
+    if (id < 0) return;
+    c.flags = (c.flags & WIN_FIXED) | WIN_ALIVE;
+    c.next = -1;
+    ws.win[id] = c;
+    ws.ehead[es] = id;
+    face_add(ws, sm, c.he / 3);
+}
+
+template <class R>
+__device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win<R> c, double rc) {
     const double Ld = m.he[c.he].L;
     const R Lr = (R)Ld;
     const R tolw = (R)Tol<R>::w * Lr;
-    const double tie = 1e-13;   // exact FP64 comparisons below
     const bool c_direct = !(c.flags & WIN_FIXED);
     if (c.b0 < (R)0) c.b0 = (R)0;
     if (c.b1 > Lr) c.b1 = Lr;
@@ -535,37 +771,52 @@ __device__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win
             const R lo = a0 > o0 ? a0 : o0, hi = a1 < o1 ? a1 : o1;
             if (!(hi - lo > tolw)) { ivl_add<R>(npc, a0, a1); continue; }
             int cmp = CMP_SPLIT;
-            if (sizeof(R) == sizeof(float)) {
-                const R osx = same ? fsx(o) : Lr - fsx(o), osy = same ? fsy(o) : -fsy(o);
-                cmp = dominance_f32((float)fsx(c), (float)fsy(c), (float)fsig(c), (float)osx, (float)osy,
-                                    (float)fsig(o), (float)lo, (float)hi);
-            }
+            // FP32 copies of both pseudo-sources in the candidate's frame (conversions in the
+            // FP64 form; the margins of the FP32 tests cover their rounding)
+            const float fcx = (float)fsx(c), fcy = (float)fsy(c), fcs = (float)fsig(c);
+            const float fox = same ? (float)fsx(o) : (float)Lr - (float)fsx(o);
+            const float foy = same ? (float)fsy(o) : -(float)fsy(o);
+            const float fos = (float)fsig(o);
+            const bool eq_sig = __double_as_longlong(c.sig) == __double_as_longlong(o.sig);
+            if (same && same_family<R>(c, o)) cmp = CMP_EXISTING;   // equal everywhere: ties stay
+            else if (!eq_sig) cmp = dominance_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi);
+            // equal sigma: the exact bisector split below is cheaper than any FP32 attempt
             if (cmp == CMP_EXISTING) { ivl_add<R>(npc, a0, lo); ivl_add<R>(npc, hi, a1); continue; }
             if (cmp == CMP_CANDIDATE) { ivl_add<R>(npc, a0, a1); ivl_add<R>(lost, lo, hi, false); continue; }
-            // exact FP64 split of the overlap at the equal-distance points
-            const double osx = same ? o.sx : Ld - o.sx, osy = same ? o.sy : -o.sy;
-            double r0 = 0.0, r1 = 0.0;
-            const int nr = equal_points(c.sx, c.sy, c.sig, osx, osy, o.sig, (double)lo, (double)hi, r0, r1);
-            ivl_add<R>(npc, a0, lo);
-            double x0 = (double)lo;
+            if (sizeof(R) == sizeof(float) && !eq_sig) {
+                float bpf[4];
+                bool cw[3];
+                int npz = 0;
+                if (split_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi, bpf, cw, npz)) {
+                    ivl_add<R>(npc, a0, lo);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                if (q > nr) break;
-                const double x1 = q < nr ? (q == 0 ? r0 : r1) : (double)hi;
-                const double xm = 0.5 * (x0 + x1);
-                const double dc = c.sig + sqrt((xm - c.sx) * (xm - c.sx) + c.sy * c.sy);
-                const double dox = xm - osx;
-                const double dd = dc - (o.sig + sqrt(dox * dox + osy * osy));
-                // the candidate wins where it is shorter beyond rounding; on a tie a direct
-                // window beats one descending from a pseudo-source (whose tangent is only
-                // exact on the tie line), otherwise the existing window keeps it, so exact
-                // ties never fragment intervals
-                const bool win = (dd < -tie * dc) || (dd <= tie * dc && c_direct && (o.flags & WIN_FIXED));
-                if (win) {
-                    ivl_add<R>(npc, (R)x0, (R)x1);
-                    ivl_add<R>(lost, (R)x0, (R)x1, false);
+                    for (int q = 0; q < 3; ++q) {
+                        if (q >= npz) break;
+                        if (cw[q]) {
+                            ivl_add<R>(npc, (R)bpf[q], (R)bpf[q + 1]);
+                            ivl_add<R>(lost, (R)bpf[q], (R)bpf[q + 1], false);
+                        }
+                    }
+                    ivl_add<R>(npc, hi, a1);
+                    continue;
                 }
-                x0 = x1;
+            }
+            // exact split of the overlap at the equal-distance points
+            {
+                const double osx = same ? o.sx : Ld - o.sx, osy = same ? o.sy : -o.sy;
+                double bp[4];
+                bool cw[3];
+                const int npz = split_exact(c.sx, c.sy, c.sig, osx, osy, o.sig, (double)lo, (double)hi,
+                                            c_direct && (o.flags & WIN_FIXED), bp, cw);
+                ivl_add<R>(npc, a0, lo);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (q >= npz) break;
+                    if (cw[q]) {
+                        ivl_add<R>(npc, (R)bp[q], (R)bp[q + 1]);
+                        ivl_add<R>(lost, (R)bp[q], (R)bp[q + 1], false);
+                    }
+                }
             }
             ivl_add<R>(npc, hi, a1);
         }
@@ -657,10 +908,14 @@ __device__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, co
     bool claimed = false;
     int slot = -1;
     if (has) {
-        slot = css::ht_insert(ws.vkey, ws.log_vh, ws.gen, c.v, claimed);
+        slot = ws_vins<R>(ws, c.v, claimed);
         if (slot < 0) { atomicOr(&sm.err, css::ST_HASH_OVERFLOW); has = false; }
     }
-    if (claimed) { ws.vdist[slot] = __longlong_as_double(0x7ff0000000000000ll); ws.vflag[slot] = 0; ws.vvid[slot] = c.v; }
+    if (claimed) {
+        ws.vdist[slot] = __longlong_as_double(0x7ff0000000000000ll);
+        ws.vflag[slot] = 0;
+        if (!ws.shared) ws.vvid[slot] = c.v;
+    }
     __syncwarp();
     int rank;
     const int rounds = group_rounds(has, slot, lane, rank);
@@ -694,7 +949,7 @@ __device__ void child_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, con
     bool claimed = false;
     int slot = -1;
     if (has) {
-        slot = css::ht_insert(ws.ekey, ws.log_eh, ws.gen, m.edge[c.he], claimed);
+        slot = ws_eins<R>(ws, m.edge[c.he], claimed);
         if (slot < 0) { atomicOr(&sm.err, css::ST_HASH_OVERFLOW); has = false; }
     }
     if (claimed) ws.ehead[slot] = -1;
@@ -786,8 +1041,8 @@ __device__ __forceinline__ double pot_u(const css_potential& p, double l) {
 
 // distance + source tangent (source-face layout) of particle j of face fl
 template <class R>
-__device__ double query(const DMesh& m, const Ws<R>& ws, int f0, R qx, R qy, int fl, const double* bj, R& tx,
-                        R& ty) {
+__device__ __noinline__ double query(const DMesh& m, const Ws<R>& ws, int f0, R qx, R qy, int fl, const double* bj,
+                                     R& tx, R& ty) {
     R L01, x2, y2, dummy;
     face_corner_f<R>(m, fl, 1, L01, dummy);
     face_corner_f<R>(m, fl, 2, x2, y2);
@@ -810,7 +1065,7 @@ __device__ double query(const DMesh& m, const Ws<R>& ws, int f0, R qx, R qy, int
     }
     for (int k = 0; k < 3; ++k) {
         const int h = 3 * fl + k;
-        const int slot = css::ht_find(ws.ekey, ws.log_eh, ws.gen, m.edge[h]);
+        const int slot = ws_efind<R>(ws, m.edge[h]);
         if (slot < 0) continue;
         R ax, ay, bx, by;
         face_corner_f<R>(m, fl, k, ax, ay);
@@ -875,7 +1130,7 @@ __device__ double query(const DMesh& m, const Ws<R>& ws, int f0, R qx, R qy, int
     for (int k = 0; k < 3; ++k) {
         const int32_t v = m.fv[3 * fl + k];
         if (!m.pseudo[v]) continue;   // only pseudo-source vertices can bend a shortest path
-        const int slot = css::ht_find(ws.vkey, ws.log_vh, ws.gen, v);
+        const int slot = ws_vfind<R>(ws, v);
         if (slot < 0) continue;
         R vx, vy;
         face_corner_f<R>(m, fl, k, vx, vy);
@@ -894,6 +1149,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
     const double* b = J.bary + 3 * (size_t)i;
     const double qxd = b[1] * m.lay[3 * f0] + b[2] * m.lay[3 * f0 + 1];
     const double qyd = b[2] * m.lay[3 * f0 + 2];
+    ws_clear_shared<R>(ws, lane);
     if (lane == 0) { sm.nwin = 0; sm.head = 0; sm.nface = 0; sm.nemit = 0; sm.err = 0; }
     __syncwarp();
     if (lane == 0) face_add(ws, sm, f0);
@@ -1068,6 +1324,8 @@ __global__ void __launch_bounds__(256) k_geodesic(cssi::GeoJob job0, const cssi:
     if (gw >= g.nwarps) return;
     WarpSm& sm = smem[wib];
     Ws<R> ws = ws_bind<R>(g, gw);
+    extern __shared__ __align__(16) unsigned char dsm[];
+    if (g.shared) ws_bind_shared<R>(ws, dsm + (size_t)wib * sh_bytes_per_warp<R>());
     uint32_t gen = 0;
     if (lane == 0) gen = g.gen[gw];
     gen = __shfl_sync(CSS_FULL, gen, 0);
@@ -1135,21 +1393,29 @@ cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const int32
                             int warps_per_cta, int nctas, int* work_counter, int* status,
                             unsigned long long* counters, cudaStream_t st) {
     const dim3 block(32 * warps_per_cta);
-    if (precision == CSS_FP32)
-        k_geodesic<float><<<nctas, block, 0, st>>>(job0, djobs, job_of_item, src_of_item, nitems, ws, work_counter,
-                                                   status, counters);
-    else
-        k_geodesic<double><<<nctas, block, 0, st>>>(job0, djobs, job_of_item, src_of_item, nitems, ws, work_counter,
+    if (precision == CSS_FP32) {
+        const size_t sm = ws.shared ? warps_per_cta * sh_bytes_per_warp<float>() : 0;
+        k_geodesic<float><<<nctas, block, sm, st>>>(job0, djobs, job_of_item, src_of_item, nitems, ws, work_counter,
                                                     status, counters);
+    } else {
+        const size_t sm = ws.shared ? warps_per_cta * sh_bytes_per_warp<double>() : 0;
+        k_geodesic<double><<<nctas, block, sm, st>>>(job0, djobs, job_of_item, src_of_item, nitems, ws, work_counter,
+                                                     status, counters);
+    }
     return cudaGetLastError();
 }
 
-int geodesic_blocks_per_sm(int precision, int warps_per_cta) {
+int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared) {
     int nb = 0;
-    if (precision == CSS_FP32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<float>, 32 * warps_per_cta, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<double>, 32 * warps_per_cta, 0);
+    if (precision == CSS_FP32) {
+        const size_t sm = shared ? warps_per_cta * sh_bytes_per_warp<float>() : 0;
+        cudaFuncSetAttribute(k_geodesic<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * sh_bytes_per_warp<float>()));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<float>, 32 * warps_per_cta, sm);
+    } else {
+        const size_t sm = shared ? warps_per_cta * sh_bytes_per_warp<double>() : 0;
+        cudaFuncSetAttribute(k_geodesic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * sh_bytes_per_warp<double>()));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<double>, 32 * warps_per_cta, sm);
+    }
     return nb;
 }
 
