@@ -835,15 +835,16 @@ double om_pair_dudl(const om_potential* p, double l) {
 
 /* F_i = sum_j -U'(l_ij) grad_{x_i} l_ij with grad_{x_i} l_ij = -(unit initial tangent of the
  * geodesic from i to j), i.e. F_i = sum_j U'(l_ij) t_ij: repulsive for U' < 0. */
-int om_forces(const om_mesh* m, int64_t n, const int32_t* face, const double* bary,
-              double r_c, const om_potential* pot, double* F, double* epot, int nthreads) {
+int om_forces_subset(const om_mesh* m, int64_t n, const int32_t* face, const double* bary, double r_c,
+                     const om_potential* pot, int64_t ns, const int64_t* src, double* F, double* e_src,
+                     int nthreads) {
     for (int64_t i = 0; i < n; ++i) if (face[i] < 0 || face[i] >= m->nf) return -1;
+    for (int64_t k = 0; src && k < ns; ++k) if (src[k] < 0 || src[k] >= n) return -1;
     double* x = (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
     for (int64_t i = 0; i < n; ++i) om_world_position(m, face[i], bary + 3 * i, x + 3 * i);
-    double e = 0.0;
 #ifdef _OPENMP
     if (nthreads <= 0) nthreads = omp_get_max_threads();
-#pragma omp parallel num_threads(nthreads) reduction(+ : e)
+#pragma omp parallel num_threads(nthreads)
 #endif
     {
         ows* s = ws_create(m);
@@ -851,11 +852,12 @@ int om_forces(const om_mesh* m, int64_t n, const int32_t* face, const double* ba
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 4)
 #endif
-        for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = 0; k < ns; ++k) {
+            const int64_t i = src ? src[k] : k;
             run_source(s, face[i], bary + 3 * i);
             double qx, qy;
             bary_to_face(m, face[i], bary + 3 * i, &qx, &qy);
-            double fx = 0.0, fy = 0.0;
+            double fx = 0.0, fy = 0.0, e = 0.0;
             for (int64_t j = 0; j < n; ++j) {
                 if (j == i || !(euclid(m, x + 3 * i, x + 3 * j) < r_c)) continue;
                 double tx, ty;
@@ -865,13 +867,26 @@ int om_forces(const om_mesh* m, int64_t n, const int32_t* face, const double* ba
                 fx += du * tx; fy += du * ty;
                 e += 0.5 * om_pair_energy(pot, d);
             }
-            face_to_world_vec(m, face[i], fx, fy, F + 3 * i);
+            face_to_world_vec(m, face[i], fx, fy, F + 3 * k);
+            if (e_src) e_src[k] = e;
         }
         ws_destroy(s);
     }
-    if (epot) *epot = e;
     free(x);
     return 0;
+}
+
+int om_forces(const om_mesh* m, int64_t n, const int32_t* face, const double* bary,
+              double r_c, const om_potential* pot, double* F, double* epot, int nthreads) {
+    double* e = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+    const int rc = om_forces_subset(m, n, face, bary, r_c, pot, n, NULL, F, e, nthreads);
+    if (rc == 0 && epot) {
+        double sum = 0.0;
+        for (int64_t i = 0; i < n; ++i) sum += e[i];
+        *epot = sum;
+    }
+    free(e);
+    return rc;
 }
 
 /* ------------------------------------------------------------------ face walk (Sec. 3.2) */

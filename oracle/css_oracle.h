@@ -83,6 +83,11 @@ double om_pair_dudl(const om_potential* p, double l);         /* dU/dl */
 /* F (n x 3, world, in each particle's face plane) and E_pot = 1/2 sum_ij U(l_ij). */
 int om_forces(const om_mesh* m, int64_t n, const int32_t* face, const double* bary,
               double r_c, const om_potential* pot, double* F, double* epot, int nthreads);
+/* Forces on the listed particles src[0..ns) only (src NULL: particles 0..ns-1): F is ns x 3,
+   e_src (ns, or NULL) receives each listed particle's half pair energies 1/2 sum_j U(l_ij). */
+int om_forces_subset(const om_mesh* m, int64_t n, const int32_t* face, const double* bary, double r_c,
+                     const om_potential* pot, int64_t ns, const int64_t* src, double* F, double* e_src,
+                     int nthreads);
 
 /* Shift one particle by the world tangent displacement disp3 along the surface,
  * carrying ncarry world tangent vectors (parallel transport).  Returns the number of

@@ -42,6 +42,8 @@ def lib():
         L.om_pair_dudl.restype = C.c_double
         L.om_forces.argtypes = [P, C.c_int64, P, P, C.c_double, P, P, P, C.c_int]
         L.om_forces.restype = C.c_int
+        L.om_forces_subset.argtypes = [P, C.c_int64, P, P, C.c_double, P, C.c_int64, P, P, P, C.c_int]
+        L.om_forces_subset.restype = C.c_int
         L.om_shift.argtypes = [P, P, P, P, C.c_int, P]
         L.om_shift.restype = C.c_int
         L.om_integrate.argtypes = [P, C.c_int64, P, P, P, P, P, P, P, C.c_double, C.c_int64,
@@ -186,22 +188,24 @@ class OracleMesh:
             out = (rs, j[:k].copy(), d[:k].copy(), t[:k].copy())
             return (out + (st.asdict(),)) if stats else out
 
-    def neighbors_gap(self, face, bary, r_c: float, nthreads: int = 0):
+    def neighbors_gap(self, face, bary, r_c: float, nthreads: int = 0, sources=None):
         """(row_start, j, dist, tangent, gap): gap = extra length of the best rival path whose
-        initial tangent differs (+inf when the geodesic is unique among the candidates)."""
+        initial tangent differs (+inf when the geodesic is unique among the candidates).
+        With `sources`, only those rows, in the order given."""
         face = _i32(face)
         bary = _f64(bary)
         n = face.shape[0]
-        src = np.arange(n, dtype=np.int64)
+        src = np.arange(n, dtype=np.int64) if sources is None else np.ascontiguousarray(sources, dtype=np.int64)
+        ns = src.shape[0]
         np_ = C.c_int64(0)
-        cap = max(16, n * 8)
+        cap = max(16, ns * 8)
         while True:
-            rs = np.zeros(n + 1, np.int64)
+            rs = np.zeros(ns + 1, np.int64)
             j = np.zeros(cap, np.int32)
             d = np.zeros(cap)
             t = np.zeros((cap, 3))
             g = np.zeros(cap)
-            rc = lib().om_neighbors_gap(self.h, n, _p(face), _p(bary), float(r_c), n, _p(src), cap,
+            rc = lib().om_neighbors_gap(self.h, n, _p(face), _p(bary), float(r_c), ns, _p(src), cap,
                                         C.byref(np_), _p(rs), _p(j), _p(d), _p(t), _p(g), int(nthreads), None)
             if rc == -5:
                 cap = int(np_.value)
@@ -222,6 +226,20 @@ class OracleMesh:
         if rc != 0:
             raise ValueError(f"oracle forces failed ({rc})")
         return F, e.value
+
+    def forces_subset(self, face, bary, r_c: float, pot: dict, sources, nthreads: int = 0):
+        """Forces (len(sources) x 3) and half pair energies on the listed particles only."""
+        face = _i32(face)
+        bary = _f64(bary)
+        src = np.ascontiguousarray(sources, dtype=np.int64)
+        F = np.zeros((src.shape[0], 3))
+        e = np.zeros(src.shape[0])
+        P = potential(pot)
+        rc = lib().om_forces_subset(self.h, face.shape[0], _p(face), _p(bary), float(r_c), C.byref(P),
+                                    src.shape[0], _p(src), _p(F), _p(e), int(nthreads))
+        if rc != 0:
+            raise ValueError(f"oracle forces failed ({rc})")
+        return F, e
 
     def shift(self, face: int, bary, disp3, carry=None):
         f = np.array([face], np.int32)

@@ -82,3 +82,41 @@ def compare_pairs(gpu, ref, r_c, dist_tol, tan_tol, rel=True, band=None, tie=Non
     assert mt <= tan_tol, f"tangent error {mt} > {tan_tol} at pair {worst[0]}: d_gpu={worst[1]!r} " \
                           f"d_ref={worst[2]!r} rival gap={worst[3]!r}"
     return n, md, mt
+
+
+def select_rows(csr, rows):
+    """The CSR rows `rows` (in that order) of a (row_start, j, dist, tangent) result."""
+    rs, j, d, t = csr[:4]
+    idx = [np.arange(rs[i], rs[i + 1]) for i in rows]
+    cnt = np.array([len(a) for a in idx], np.int64)
+    out_rs = np.concatenate([[0], np.cumsum(cnt)])
+    sel = np.concatenate(idx) if idx else np.zeros(0, np.int64)
+    return out_rs, j[sel], d[sel], t[sel]
+
+
+def sample_sources(n, k, seed):
+    """k distinct particle indices (seeded), sorted."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n, size=min(k, n), replace=False))
+
+
+def force_row_bounds(ref_rows, pot, dudl, delta, tan_err, tie=None):
+    """Per-row bound on |F_gpu - F_ref| for forces built from distances within `delta` and
+    tangents within `tan_err` of the reference rows (row_start, j, dist, tangent[, gap]):
+    each pair moves its U' by at most its variation over [d - delta, d + delta], and turns
+    it by tan_err (fully, where the reference reports a rival geodesic within `tie`); pairs
+    within delta of the cutoff may be present on one side only."""
+    rs, d = ref_rows[0], ref_rows[2]
+    gap = ref_rows[4] if len(ref_rows) > 4 else np.full(len(d), np.inf)
+    rc = pot["r_cut"]
+    edge = abs(dudl(max(rc - delta, 1e-300)))
+    out = np.zeros(len(rs) - 1)
+    for k in range(len(rs) - 1):
+        b = 4.0 * edge
+        for q in range(rs[k], rs[k + 1]):
+            u = dudl(d[q])
+            lo = dudl(d[q] - delta) if d[q] > delta else math.inf
+            hi = dudl(d[q] + delta)
+            b += max(abs(lo - u), abs(hi - u)) + abs(u) * (2.0 if tie is not None and gap[q] <= tie else tan_err)
+        out[k] = b
+    return out

@@ -159,6 +159,31 @@ def test_flat_forces_equal_euclidean():
     assert E == pytest.approx(Ew, rel=1e-12)
 
 
+def test_subset_forces_equal_euclidean_rows():
+    """Forces on a listed subset follow the same flat closed form; the per-particle half
+    energies add up to the total."""
+    cfg = synth.make_config("flat64")
+    m, face, bary, pot = cfg["mesh"], cfg["face"], cfg["bary"], cfg["pot"]
+    om = O.OracleMesh(m)
+    x = synth.particles.world_positions(m, face, bary)
+    src = [5, 0, 63, 17]
+    F, e = om.forces_subset(face, bary, math.inf, pot, src)
+    s = pot["sigma"]
+    for k, i in enumerate(src):
+        Fw = np.zeros(3)
+        ew = 0.0
+        for j in range(len(x)):
+            r = np.linalg.norm(x[j] - x[i])
+            if j != i and r < s:
+                Fw += -2 * (1 - r / s) / s * (x[j] - x[i]) / r
+                ew += 0.5 * (1 - r / s) ** 2
+        np.testing.assert_allclose(F[k], Fw, atol=1e-12)
+        assert e[k] == pytest.approx(ew, rel=1e-12, abs=1e-15)
+    _, e_all = om.forces_subset(face, bary, math.inf, pot, np.arange(len(face)))
+    _, E = om.forces(face, bary, math.inf, pot)
+    assert e_all.sum() == pytest.approx(E, rel=1e-12)
+
+
 def test_forces_are_minus_energy_gradient():
     """F_i = -dE/dx_i along the tangent plane, by central differences on a curved mesh."""
     m = synth.icosphere(3, 1.0, noise=0.01, seed=1)
