@@ -139,35 +139,46 @@ def cpu_baseline(cfg, budget_s: float = 12.0):
 
 
 def run_reference(args, rank: int, world: int):
+    """The oracle as it stands, on the host cores: full MD steps of the same workload
+    (forces by window propagation from every particle, the face walk), one mesh after
+    another for the many-mesh workload."""
     if rank != 0:
         return
-    import numpy as np
     from oracle import oracle as O
     cfg = workload(args.workload)
-    om = O.OracleMesh(cfg["mesh"])
     cores = os.cpu_count() or 1
-    face, bary, vel = cfg["face"], cfg["bary"], cfg["vel"]
     pot, integ, rc = cfg["pot"], cfg["integ"], cfg["r_c"]
-    F, _ = om.forces(face, bary, rc, pot, nthreads=cores)
-    state = dict(face=face, bary=bary, vel=vel, force=F)
-    for _ in range(args.warmup):
-        state = om.integrate(state["face"], state["bary"], state["vel"], None, state["force"], pot, integ, rc, 1,
-                             nthreads=cores)
+    items = cfg["items"] if "items" in cfg else [cfg]
+    states = []
+    for it in items:
+        om = O.OracleMesh(it["mesh"])
+        F, _ = om.forces(it["face"], it["bary"], rc, pot, nthreads=cores)
+        states.append((om, dict(face=it["face"], bary=it["bary"], vel=it.get("vel"), orient=it.get("orient"),
+                                force=F)))
+
+    def step(k):
+        out = []
+        for om, st in states:
+            st = om.integrate(st["face"], st["bary"], st["vel"], st["orient"], st["force"], pot, integ, rc, 1,
+                              nthreads=cores, seed=1, step0=k)
+            out.append((om, st))
+        return out
+    for k in range(args.warmup):
+        states = step(k)
     times, pairs = [], 0
-    for _ in range(args.steps):
+    for k in range(args.steps):
         t0 = time.perf_counter()
-        state = om.integrate(state["face"], state["bary"], state["vel"], None, state["force"], pot, integ, rc, 1,
-                             nthreads=cores)
+        states = step(args.warmup + k)
         times.append(time.perf_counter() - t0)
-        rs, *_ = om.neighbors(state["face"], state["bary"], rc, nthreads=cores)
-        pairs += int(rs[-1])
+        for om, st in states:
+            rs, *_ = om.neighbors(st["face"], st["bary"], rc, nthreads=cores)
+            pairs += int(rs[-1])
     total = sum(times)
     v = pairs / total
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n_particles": len(face), "faces": int(cfg["mesh"].nf),
-                       "r_c": rc, "integrator": "NVE velocity Verlet", "l2": "host run"},
+            "config": dict(describe(cfg, 1), l2="host run", precision="FP64 oracle"),
             "md_steps_per_s": args.steps / total,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} oracle MD steps of the full workload after {args.warmup} "
@@ -176,8 +187,113 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+POT_NAMES = {0: "harmonic (1-d/sigma)^2", 1: "WCA", 2: "Gaussian"}
+INT_NAMES = {0: "NVE velocity Verlet", 1: "overdamped Brownian", 2: "active Brownian"}
+
+
+def describe(cfg, world):
+    """The config object of the JSON line, from the workload itself."""
+    pot, integ, rc = cfg["pot"], cfg["integ"], cfg["r_c"]
+    if "items" in cfg:
+        nfs = [it["mesh"].nf for it in cfg["items"]]
+        mesh = f"{len(nfs)} tori, {min(nfs)}-{max(nfs)} faces each ({sum(nfs)} total)"
+        n = sum(len(it["face"]) for it in cfg["items"])
+    else:
+        m = cfg["mesh"]
+        mesh = f"{m.name}, {m.nf} faces" + (", periodic" if m.period is not None else "")
+        n = len(cfg["face"])
+    return {"workload": cfg["name"], "mesh": mesh, "n_particles": n,
+            "r_c": rc if math.isfinite(rc) else "all pairs",
+            "potential": f"{POT_NAMES[pot['kind']]}, sigma={pot['sigma']:.4g}",
+            "integrator": f"{INT_NAMES[integ['kind']]} dt={integ['dt']:g}",
+            "l2": "256 MiB flush between timed steps", "parallelism": f"replicas x{world}"}
+
+
+class Timer:
+    """Per-step CUDA events on the library's stream, an L2-flushing write before each
+    timed step (outside the events), clocks sampled during the timed region."""
+
+    def __init__(self, torch, stream, flush, local, dist):
+        self.torch, self.stream, self.flush, self.local, self.dist = torch, stream, flush, local, dist
+
+    def run(self, step, steps, warmup, counters):
+        torch = self.torch
+        for _ in range(warmup):
+            step()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        kms, pairs, props = [], 0, 0
+        torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(self.local) as clk:
+            for k in range(steps):
+                with torch.cuda.stream(self.stream):
+                    self.flush.zero_()
+                    ev[k][0].record(self.stream)
+                km, pc, pp = step()
+                with torch.cuda.stream(self.stream):
+                    ev[k][1].record(self.stream)
+                kms.append(km)
+                pairs += pc
+                props += pp
+            torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+        t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        if self.dist:
+            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+            self.dist.all_reduce(tt, op=self.dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return dict(t=t, steps=steps, kernel_ms=kms, pairs=pairs, props=props, clocks=clk.summary())
+
+
+def accuracy(css, ctx, cases):
+    """Max distance error of both forms against the oracle on (mesh handle, synth mesh,
+    face, bary, r_c) cases, relative to each mesh's bounding-box diagonal."""
+    import synth
+    from oracle import oracle as O
+    from tests._common import csr_to_dict
+    acc = {}
+    for prec, nm in ((css.FP32, "fp32"), (css.FP64, "fp64")):
+        worst, only = 0.0, 0
+        worst_abs = 0.0
+        for mesh, m, face, bary, rc, om in cases:
+            om = om or O.OracleMesh(m)
+            R = csr_to_dict(*om.neighbors(face, bary, rc))
+            p2 = css.particles_set(ctx, mesh, face, bary)
+            G = csr_to_dict(*css.geodesic_neighbors(p2, rc, prec))
+            p2.free()
+            common = set(G) & set(R)
+            err = max((abs(G[k][0] - R[k][0]) for k in common), default=0.0)
+            worst_abs = max(worst_abs, err)
+            worst = max(worst, err / synth.bbox_diagonal(m))
+            only += len(set(G) ^ set(R))
+        acc[nm] = {"max_abs_dist_err": worst_abs, "max_err_over_diameter": worst, "pairs_only_one_side": only}
+    return acc
+
+
+def roofline(css, ctx, pk, props_per_src, n, pairs_per_launch, kern_s, kernel_name):
+    fp32_peak_nominal = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    alg_flops = n * props_per_src * FLOPS_PER_PROPAGATION + pairs_per_launch * FLOPS_PER_PAIR
+    achieved = alg_flops / kern_s
+    faces_per_src = props_per_src / 2.0     # about two windows enter each face reached
+    alg_bytes = n * faces_per_src * BYTES_PER_FACE + pairs_per_launch * 24.0
+    hbm = float(pk.get("hbm_gbs", 6800.0)) * 1e9
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak_nominal / 1e12,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak_nominal, "traffic": None,
+            "kernel": kernel_name, "kernel_ms": kern_s * 1e3,
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+            "fma_probe_tflops": {"fp32": ctx.fma_peak(css.FP32) / 1e12, "fp64": ctx.fma_peak(css.FP64) / 1e12},
+            "algorithmic": {"propagations_per_source": props_per_src,
+                            "flops_per_propagation": FLOPS_PER_PROPAGATION,
+                            "flops_per_pair": FLOPS_PER_PAIR, "flops_per_launch": alg_flops}}
+    mem = {"achieved_gbs": alg_bytes / kern_s / 1e9, "peak_gbs": hbm / 1e9,
+           "frac": alg_bytes / kern_s / hbm, "bytes_per_launch": alg_bytes}
+    return roof, mem
+
+
 def run_ours(args, rank: int, world: int):
-    import numpy as np
     import torch
     import paper_2404_19751_gb300 as css
     from paper_2404_19751_gb300 import build as cbuild
@@ -195,60 +311,40 @@ def run_ours(args, rank: int, world: int):
             dist.barrier()
     css.load()
     cfg = workload(args.workload)
-    m = cfg["mesh"]
-    pot, integ, rc = cfg["pot"], cfg["integ"], cfg["r_c"]
     stream = torch.cuda.Stream()
     ctx = css.create(local, stream=stream.cuda_stream)
-    mesh = css.mesh_upload(ctx, m.verts, m.faces, m.period)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    timer = Timer(torch, stream, flush, local, dist)
+    if "items" in cfg:
+        line = run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world)
+    else:
+        line = run_single(args, cfg, css, ctx, torch, stream, timer, rank, world)
+    if rank == 0 and line:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_single(args, cfg, css, ctx, torch, stream, timer, rank, world):
+    import numpy as np
+    m = cfg["mesh"]
+    pot, integ, rc = cfg["pot"], cfg["integ"], cfg["r_c"]
+    mesh = css.mesh_upload(ctx, m.verts, m.faces, m.period)
     n = len(cfg["face"])
 
     def timed_run(prec, steps, warmup):
         parts = css.particles_set(ctx, mesh, cfg["face"], cfg["bary"], cfg["vel"], cfg["orient"], seed=1)
-        for _ in range(warmup):
+
+        def step():
             css.integrate_step(parts, pot, integ, rc, prec, 1)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        kms, pairs, props = [], 0, 0
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
-            for k in range(steps):
-                with torch.cuda.stream(stream):
-                    flush.zero_()
-                    ev[k][0].record(stream)
-                css.integrate_step(parts, pot, integ, rc, prec, 1)
-                with torch.cuda.stream(stream):
-                    ev[k][1].record(stream)
-                kms.append(ctx.last_kernel_ms())
-                c = ctx.last_counters()
-                pairs += c["pairs"]
-                props += c["propagated"]
-            torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        step_ms = [a.elapsed_time(b) for a, b in ev]
-        state = css.particles_get(parts)
+            c = ctx.last_counters()
+            return ctx.last_kernel_ms(), c["pairs"], c["propagated"]
+        r = timer.run(step, steps, warmup, True)
         parts.free()
-        return dict(step_ms=step_ms, kernel_ms=kms, pairs=pairs, props=props, clocks=clk.summary(), state=state)
+        return r
 
     r32 = timed_run(css.FP32, args.steps, args.warmup)
     r64 = timed_run(css.FP64, max(3, args.steps // 2), max(3, args.warmup))
-
-    def agg(r):
-        t = sum(r["step_ms"]) / 1e3
-        if dist:
-            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return t
-
-    t32 = agg(r32)
-    t64 = agg(r64)
-    k32 = len(r32["step_ms"])
-    k64 = len(r64["step_ms"])
-    value = world * r32["pairs"] / t32
+    t32, t64, k32, k64 = r32["t"], r64["t"], r32["steps"], r64["steps"]
     # ---- end to end through the C ABI with host buffers: upload the state from pinned
     # host memory, one step, read the state back, every step
     parts = css.particles_set(ctx, mesh, cfg["face"], cfg["bary"], cfg["vel"], cfg["orient"], seed=1)
@@ -259,60 +355,26 @@ def run_ours(args, rank: int, world: int):
     ob = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     ov = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     oF = torch.empty((n, 3), dtype=torch.float64).pin_memory()
-    for _ in range(max(3, args.warmup)):
+
+    def e2e_step():
         css.particles_update(parts, hf, hb, hv)
         css.integrate_step(parts, pot, integ, rc, css.FP32, 1)
+        pc = ctx.last_counters()["pairs"]
         css.particles_get_into(parts, of, ob, ov, None, oF)
-    torch.cuda.synchronize()
-    e2e_steps = args.steps
-    ee = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    e2e_pairs = 0
-    with torch.cuda.stream(stream):
-        ee[0].record(stream)
-    for _ in range(e2e_steps):
-        css.particles_update(parts, hf, hb, hv)
-        css.integrate_step(parts, pot, integ, rc, css.FP32, 1)
-        e2e_pairs += ctx.last_counters()["pairs"]
-        css.particles_get_into(parts, of, ob, ov, None, oF)
-    with torch.cuda.stream(stream):
-        ee[1].record(stream)
-    torch.cuda.synchronize()
-    e2e_t = ee[0].elapsed_time(ee[1]) / 1e3
+        return pc
+    e2e_t, e2e_pairs = e2e_time(torch, stream, e2e_step, args, timer.dist)
     parts.free()
-    if dist:
-        tt = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
     h2d = n * (4 + 24 + 24)
     d2h = n * (4 + 24 + 24 + 24)
     if rank != 0:
-        return
-    # ---- accuracy of this run's first state against the oracle, roofline, CPU baseline
+        mesh.free()
+        return None
     pk = peaks()
-    fp32_peak_nominal = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
-    fp32_probe = ctx.fma_peak(css.FP32)
-    fp64_probe = ctx.fma_peak(css.FP64)
     cb, ostats, om = (None, None, None)
     if not args.no_cpu_baseline and world == 1:
         cb, ostats, om = cpu_baseline(cfg)
-    acc = {}
     try:
-        import synth
-        from tests._common import csr_to_dict
-        if om is None:
-            from oracle import oracle as O
-            om = O.OracleMesh(m)
-        ref = om.neighbors(cfg["face"], cfg["bary"], rc)
-        p2 = css.particles_set(ctx, mesh, cfg["face"], cfg["bary"])
-        R = csr_to_dict(*ref)
-        diam = synth.bbox_diagonal(m)
-        for prec, nm in ((css.FP32, "fp32"), (css.FP64, "fp64")):
-            G = csr_to_dict(*css.geodesic_neighbors(p2, rc, prec))
-            common = set(G) & set(R)
-            err = max((abs(G[k][0] - R[k][0]) for k in common), default=0.0)
-            acc[nm] = {"max_abs_dist_err": err, "max_err_over_diameter": err / diam,
-                       "pairs_only_one_side": len(set(G) ^ set(R))}
-        p2.free()
+        acc = accuracy(css, ctx, [(mesh, m, cfg["face"], cfg["bary"], rc, om)])
     except Exception as e:  # accuracy is informative; the parity tests are the gate
         acc = {"error": str(e)}
     # algorithmic work per launch: the oracle's (priority-ordered) propagation count per
@@ -321,21 +383,13 @@ def run_ours(args, rank: int, world: int):
         props_per_src = ostats["windows_propagated"] / max(1, ostats["sources"])
     else:
         props_per_src = r32["props"] / max(1, k32 * n)
-    pairs_per_launch = r32["pairs"] / k32
-    alg_flops = n * props_per_src * FLOPS_PER_PROPAGATION + pairs_per_launch * FLOPS_PER_PAIR
-    kern_s = statistics.mean(r32["kernel_ms"]) / 1e3
-    achieved = alg_flops / kern_s
-    faces_per_src = props_per_src / 2.0     # about two windows enter each face reached
-    alg_bytes = n * faces_per_src * BYTES_PER_FACE + pairs_per_launch * 24.0
-    hbm = float(pk.get("hbm_gbs", 6800.0)) * 1e9
+    roof, mem = roofline(css, ctx, pk, props_per_src, n, r32["pairs"] / k32,
+                         statistics.mean(r32["kernel_ms"]) / 1e3, "k_geodesic<float>")
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": k32, "warmup": args.warmup,
-        "ms_per_step": 1e3 * t32 / k32, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "mesh": f"icosphere level 5, radius 1, {m.nf} faces",
-                   "n_particles": n, "r_c": rc, "potential": "harmonic (1-d/sigma)^2, sigma=0.15",
-                   "integrator": "NVE velocity Verlet dt=0.002", "precision": "FP32 form",
-                   "l2": "256 MiB flush between timed steps", "parallelism": f"replicas x{world}"},
+        "metric": METRIC, "value": world * r32["pairs"] / t32, "unit": UNIT, "n_gpus": world, "steps": k32,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t32 / k32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(describe(cfg, world), precision="FP32 form"),
         "md_steps_per_s": world * k32 / t32,
         "pairs_per_step": r32["pairs"] / k32,
         "fp64": {"value": world * r64["pairs"] / t64, "unit": UNIT, "md_steps_per_s": world * k64 / t64,
@@ -343,16 +397,8 @@ def run_ours(args, rank: int, world: int):
                  "clocks": r64["clocks"]},
         "fp32_over_fp64": (r32["pairs"] / t32) / (r64["pairs"] / t64),
         "accuracy_vs_oracle": acc,
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak_nominal / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak_nominal, "traffic": None,
-                     "kernel": "k_geodesic<float>", "kernel_ms": kern_s * 1e3,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
-                     "fma_probe_tflops": {"fp32": fp32_probe / 1e12, "fp64": fp64_probe / 1e12},
-                     "algorithmic": {"propagations_per_source": props_per_src,
-                                     "flops_per_propagation": FLOPS_PER_PROPAGATION,
-                                     "flops_per_pair": FLOPS_PER_PAIR, "flops_per_launch": alg_flops}},
-        "memory_roofline": {"achieved_gbs": alg_bytes / kern_s / 1e9, "peak_gbs": hbm / 1e9,
-                            "frac": alg_bytes / kern_s / hbm, "bytes_per_launch": alg_bytes},
+        "roofline": roof,
+        "memory_roofline": mem,
         "e2e": {"value": world * e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 8 * k32,
@@ -360,9 +406,184 @@ def run_ours(args, rank: int, world: int):
     }
     if cb:
         line["cpu_baseline"] = cb
-    print(json.dumps(line), flush=True)
     mesh.free()
-    ctx.close()
+    return line
+
+
+def e2e_time(torch, stream, step, args, dist):
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ee = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    pairs = 0
+    with torch.cuda.stream(stream):
+        ee[0].record(stream)
+    for _ in range(args.steps):
+        pairs += step()
+    with torch.cuda.stream(stream):
+        ee[1].record(stream)
+    torch.cuda.synchronize()
+    t = ee[0].elapsed_time(ee[1]) / 1e3
+    if dist:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, pairs
+
+
+def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
+    """Many independent meshes: the FP32 batched form (one persistent launch per step over
+    every source of every mesh, inside a captured graph) against the plain FP64 path (one
+    integrate call per mesh), both forms of both shown."""
+    import numpy as np
+    items = cfg["items"]
+    pot, integ, rc = cfg["pot"], cfg["integ"], cfg["r_c"]
+    meshes = [css.mesh_upload(ctx, it["mesh"].verts, it["mesh"].faces) for it in items]
+    n = sum(len(it["face"]) for it in items)
+
+    def make_sets():
+        return [css.particles_set(ctx, meshes[k], it["face"], it["bary"], it["vel"], None, seed=1)
+                for k, it in enumerate(items)]
+
+    def batched(prec, steps, warmup):
+        sets = make_sets()
+        b = css.batch_create(ctx, sets)
+
+        def step():
+            css.batch_step(b, pot, integ, rc, prec, 1)
+            c = ctx.last_counters()
+            return ctx.last_kernel_ms(), c["pairs"], c["propagated"]
+        r = timer.run(step, steps, warmup, True)
+        b.free()
+        for p in sets:
+            p.free()
+        return r
+
+    def plain(prec, steps, warmup):
+        sets = make_sets()
+
+        def step():
+            km = pc = pp = 0
+            for p in sets:
+                css.integrate_step(p, pot, integ, rc, prec, 1)
+                c = ctx.last_counters()
+                km += ctx.last_kernel_ms()
+                pc += c["pairs"]
+                pp += c["propagated"]
+            return km, pc, pp
+        r = timer.run(step, steps, warmup, True)
+        for p in sets:
+            p.free()
+        return r
+
+    r32b = batched(css.FP32, args.steps, args.warmup)
+    ks = max(3, args.steps // 2)
+    r64p = plain(css.FP64, ks, max(3, args.warmup))
+    r64b = batched(css.FP64, ks, max(3, args.warmup))
+    r32p = plain(css.FP32, ks, max(3, args.warmup))
+
+    def rate(r):
+        return world * r["pairs"] / r["t"]
+
+    def sub(r, what):
+        return {"value": rate(r), "unit": UNIT, "what": what, "md_steps_per_s": world * r["steps"] / r["t"],
+                "mesh_steps_per_s": world * len(items) * r["steps"] / r["t"],
+                "ms_per_step": 1e3 * r["t"] / r["steps"], "kernel_ms": statistics.mean(r["kernel_ms"]),
+                "clocks": r["clocks"]}
+    # ---- end to end: every mesh's state up from pinned host memory, one batched step, all
+    # states back, every step
+    sets = make_sets()
+    b = css.batch_create(ctx, sets)
+    host = []
+    for it in items:
+        k = len(it["face"])
+        host.append((torch.from_numpy(np.ascontiguousarray(it["face"], np.int32)).pin_memory(),
+                     torch.from_numpy(np.ascontiguousarray(it["bary"])).pin_memory(),
+                     torch.from_numpy(np.ascontiguousarray(it["vel"])).pin_memory(),
+                     torch.empty(k, dtype=torch.int32).pin_memory(), torch.empty((k, 3), dtype=torch.float64).pin_memory(),
+                     torch.empty((k, 3), dtype=torch.float64).pin_memory(),
+                     torch.empty((k, 3), dtype=torch.float64).pin_memory()))
+
+    def e2e_step():
+        for p, h in zip(sets, host):
+            css.particles_update(p, h[0], h[1], h[2])
+        css.batch_step(b, pot, integ, rc, css.FP32, 1)
+        pc = ctx.last_counters()["pairs"]
+        for p, h in zip(sets, host):
+            css.particles_get_into(p, h[3], h[4], h[5], None, h[6])
+        return pc
+    e2e_t, e2e_pairs = e2e_time(torch, stream, e2e_step, args, timer.dist)
+    b.free()
+    for p in sets:
+        p.free()
+    if rank != 0:
+        for mh in meshes:
+            mh.free()
+        return None
+    pk = peaks()
+    # the oracle on the host cores: full neighbour passes over every mesh, bounded
+    cb, props_per_src = None, None
+    oms = {}
+    if not args.no_cpu_baseline and world == 1:
+        from oracle import oracle as O
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        pairs = srcs = props = 0
+        passes = 0
+        while passes < 1 or time.perf_counter() - t0 < 12.0:
+            for k, it in enumerate(items):
+                om = oms.get(k) or O.OracleMesh(it["mesh"])
+                oms[k] = om
+                rs, j, d, t, st = om.neighbors(it["face"], it["bary"], rc, nthreads=cores, stats=True)
+                pairs += int(rs[-1])
+                srcs += st["sources"]
+                props += st["windows_propagated"]
+            passes += 1
+        el = time.perf_counter() - t0
+        props_per_src = props / max(1, srcs)
+        cb = dict(value=pairs / el, unit=UNIT, cores=cores, kind="oracle",
+                  sample=f"{passes} full neighbour pass(es) over all {len(items)} meshes ({n} sources, "
+                         f"r_c={rc}), FP64, OpenMP over sources, {el:.1f} s, mesh setup included")
+    if props_per_src is None:
+        props_per_src = r32b["props"] / max(1, r32b["steps"] * n)
+    order = np.argsort([len(it["face"]) for it in items], kind="stable")
+    pick = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    try:
+        acc = accuracy(css, ctx, [(meshes[k], items[k]["mesh"], items[k]["face"], items[k]["bary"], rc, oms.get(k))
+                                  for k in pick])
+        acc["sampled_meshes"] = pick
+    except Exception as e:
+        acc = {"error": str(e)}
+    k32 = r32b["steps"]
+    roof, mem = roofline(css, ctx, pk, props_per_src, n, r32b["pairs"] / k32,
+                         statistics.mean(r32b["kernel_ms"]) / 1e3, "k_geodesic<float> (batched launch)")
+    launches_per_step = 7 * len(items) + 1
+    line = {
+        "metric": METRIC, "value": rate(r32b), "unit": UNIT, "n_gpus": world, "steps": k32,
+        "warmup": args.warmup, "ms_per_step": 1e3 * r32b["t"] / k32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(describe(cfg, world), precision="FP32 form, batched (one launch over all meshes)"),
+        "md_steps_per_s": world * k32 / r32b["t"],
+        "mesh_steps_per_s": world * len(items) * k32 / r32b["t"],
+        "particle_steps_per_s": world * n * k32 / r32b["t"],
+        "pairs_per_step": r32b["pairs"] / k32,
+        "fp64": sub(r64p, "plain FP64: one integrate call per mesh"),
+        "fp64_batched": sub(r64b, "FP64 form, batched"),
+        "fp32_plain": sub(r32p, "FP32 form, one integrate call per mesh"),
+        "fp32_over_fp64": rate(r32b) / rate(r64p),
+        "accuracy_vs_oracle": acc,
+        "roofline": roof,
+        "memory_roofline": mem,
+        "e2e": {"value": world * e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": n * (4 + 24 + 24),
+                "d2h_bytes_per_step": n * (4 + 24 + 24 + 24)},
+        "gpu_launches": launches_per_step * k32,
+        "clocks": r32b["clocks"],
+    }
+    if cb:
+        line["cpu_baseline"] = cb
+    for mh in meshes:
+        mh.free()
+    return line
 
 
 def main():

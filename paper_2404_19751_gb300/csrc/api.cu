@@ -763,7 +763,15 @@ int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator*
         TRY(c, "batch jobs", cudaMemcpyAsync(b->djobs, hj.data(), hj.size() * sizeof(GeoJob), cudaMemcpyHostToDevice, st));
         TRY(c, "batch jobs", cudaStreamSynchronize(st));
     }
-    const bool nve = it->kind == CSS_INT_NVE;
+    // NVE needs the forces at the starting positions unless every set still holds them
+    bool nve = it->kind == CSS_INT_NVE;
+    if (nve) {
+        bool valid = true;
+        for (css_parts* p : b->sets)
+            valid = valid && p->force_valid && p->force_rc == r_c && p->force_prec == precision &&
+                    memcmp(&p->force_pot, pot, sizeof(css_potential)) == 0;
+        nve = !valid;
+    }
     int retries = 0;
     for (;;) {
         for (css_parts* p : b->sets) TRY(c, "snapshot", snap_take(p));

@@ -104,7 +104,8 @@ struct Tie<float> {
 };
 
 struct WarpSm {
-    int nwin, head, nface, nemit, err;
+    int nwin, npend, nface, nemit, err;
+    int sel[32];      // window ids picked for the current wave
 };
 
 // Per-warp working state.  The keyed tables (edge heads, pseudo-source vertices, face set)
@@ -128,6 +129,8 @@ struct Ws {
     int32_t* flist;
     Win<R>* win;
     int32_t* emit;
+    int32_t* pq;      // pending (not yet unfolded) window ids
+    float* pk;        // their keys when queued (lower bounds: trimming only raises a key)
     int log_eh, log_vh, log_fh, wcap, fcap, emcap;
     uint32_t gen;
 };
@@ -150,12 +153,14 @@ __host__ __device__ inline size_t ws_layout(int log_eh, int log_vh, int log_fh, 
     off[8] = o; o = al16(o + (size_t)fcap * 4);   // flist
     off[9] = o; o = al16(o + (size_t)wcap * sizeof(Win<R>));
     off[10] = o; o = al16(o + (size_t)emcap * 4);
+    off[11] = o; o = al16(o + (size_t)wcap * 4);   // pq
+    off[12] = o; o = al16(o + (size_t)wcap * 4);   // pk
     return o;
 }
 
 template <class R>
 __device__ inline Ws<R> ws_bind(const cssi::GeoWs& g, int warp) {
-    size_t off[11];
+    size_t off[13];
     ws_layout<R>(g.log_eh, g.log_vh, g.log_fh, g.wcap, g.fcap, g.emcap, off);
     char* b = g.base + (size_t)warp * g.stride;
     Ws<R> w;
@@ -170,6 +175,8 @@ __device__ inline Ws<R> ws_bind(const cssi::GeoWs& g, int warp) {
     w.flist = (int32_t*)(b + off[8]);
     w.win = (Win<R>*)(b + off[9]);
     w.emit = (int32_t*)(b + off[10]);
+    w.pq = (int32_t*)(b + off[11]);
+    w.pk = (float*)(b + off[12]);
     w.log_eh = g.log_eh; w.log_vh = g.log_vh; w.log_fh = g.log_fh;
     w.wcap = g.wcap; w.fcap = g.fcap; w.emcap = g.emcap;
     w.gen = 0;
@@ -555,6 +562,15 @@ __device__ __forceinline__ int win_alloc(WarpSm& sm, int wcap) {
     return p;
 }
 
+// queue a window that still has to be unfolded (each window is queued at most once, so
+// the queue never holds more entries than the pool)
+template <class R>
+__device__ __forceinline__ void push_pending(Ws<R>& ws, WarpSm& sm, int id, float key) {
+    const int p = atomicAdd(&sm.npend, 1);
+    ws.pq[p] = id;
+    ws.pk[p] = key;
+}
+
 // Outcome of comparing two windows on an overlap [lo, hi]: one of them carries the
 // smaller distance everywhere, or the exact FP64 split is needed.
 enum { CMP_EXISTING = 0, CMP_CANDIDATE = 1, CMP_SPLIT = 2 };
@@ -728,6 +744,7 @@ __device__ __forceinline__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm&
     c.next = -1;
     ws.win[id] = c;
     ws.ehead[es] = id;
+    push_pending<R>(ws, sm, id, (float)win_key<R>(c));
     face_add(ws, sm, c.he / 3);
 }
 
@@ -864,6 +881,7 @@ __device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R>& ws, Wa
                     piece.b0 = k0; piece.b1 = k1;
                     piece.next = onext;
                     ws.win[pid] = piece;
+                    if (!(o.flags & WIN_DONE)) push_pending<R>(ws, sm, pid, (float)win_key<R>(piece));
                     ws.win[tail].next = pid;          // keep the list order, skip the pieces
                     tail = pid;
                 }
@@ -888,6 +906,7 @@ __device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R>& ws, Wa
         w.next = ws.ehead[es];
         ws.win[id] = w;
         ws.ehead[es] = id;
+        push_pending<R>(ws, sm, id, (float)win_key<R>(w));
         added = true;
     }
     if (added) face_add(ws, sm, c.he / 3);
@@ -962,21 +981,40 @@ __device__ void child_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, con
     }
 }
 
-// Pseudo-source vertices reached this wave start windows on every edge opposite them;
-// their one-ring faces join the target faces (paths may bend there, Sec. 2.2).
+// Pseudo-source vertices whose distance is final start windows on every edge opposite
+// them; their one-ring faces join the target faces (paths may bend there, Sec. 2.2).  A
+// vertex's distance is final once no queued window can still shorten it: every
+// candidate a window yields is at least that window's key, so vertices with
+// d(v) <= kmin (the smallest queued key) go now and the others wait.  Returns the number
+// of vertices emitted.
 template <class R>
-__device__ void emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, int lane) {
+__device__ int emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, double kmin, int lane) {
     __syncwarp();
     const int ne = min(sm.nemit, ws.emcap);
-    if (ne == 0) return;
+    if (ne == 0) return 0;
+    // the vertices that wait are compacted to the front of the list in place (a write
+    // never lands behind the entries still to be read)
+    int n_wait = 0;
+    int emitted = 0;
     for (int base = 0; base < ne; base += 32) {
         const int it = base + lane;
-        const bool has = it < ne;
+        int vs = -1;
+        bool go = false;
+        if (it < ne) {
+            vs = ws.emit[it];
+            go = ws.vdist[vs] <= kmin;
+        }
+        __syncwarp();
+        const unsigned gm = __ballot_sync(CSS_FULL, go);
+        const unsigned wm = __ballot_sync(CSS_FULL, it < ne && !go);
+        if (it < ne && !go) ws.emit[n_wait + __popc(wm & css::lanemask_lt())] = vs;
+        n_wait += __popc(wm);
+        // emit this chunk's vertices now (at most 32)
+        const bool has = go;
         int vid = 0, rs = 0, len = 0;
         double dv = 0.0;
         R tx = (R)0, ty = (R)0;
         if (has) {
-            const int vs = ws.emit[it];
             vid = ws.vvid[vs];
             dv = ws.vdist[vs];
             tx = ws.vtan[2 * vs];
@@ -1013,10 +1051,12 @@ __device__ void emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, int
             }
             child_round<R>(m, ws, sm, hh, c, rc, lane);
         }
+        emitted += __popc(gm);
     }
     __syncwarp();
-    if (lane == 0) sm.nemit = 0;
+    if (lane == 0) sm.nemit = n_wait;   // inserting windows never touches the vertex list
     __syncwarp();
+    return emitted;
 }
 
 __device__ __forceinline__ double pot_dudl(const css_potential& p, double l) {
@@ -1140,6 +1180,77 @@ __device__ __noinline__ double query(const DMesh& m, const Ws<R>& ws, int f0, R 
     return best;
 }
 
+// Smallest and largest queued key.
+template <class R>
+__device__ __forceinline__ void pending_range(const Ws<R>& ws, int npend, int lane, float& kmin, float& kmax) {
+    kmin = INFINITY;
+    kmax = 0.0f;
+    for (int i = lane; i < npend; i += 32) {
+        const float k = ws.pk[i];
+        kmin = fminf(kmin, k);
+        kmax = fmaxf(kmax, k);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = fminf(kmin, __shfl_xor_sync(CSS_FULL, kmin, o));
+        kmax = fmaxf(kmax, __shfl_xor_sync(CSS_FULL, kmax, o));
+    }
+}
+
+// The next wave: up to 32 queued windows among those with the smallest keys.  A key
+// threshold T is bisected until 32..64 queued keys lie at or below it; the first 32 of
+// those in queue order are taken and the queue is compacted in place.  Processing in
+// (batched) key order keeps the work close to that of a priority queue: windows that a
+// shorter family would trim are mostly never unfolded.
+template <class R>
+__device__ int select_wave(Ws<R>& ws, WarpSm& sm, int npend, float kmin, float kmax, int lane) {
+    float T = kmax;
+    if (npend > 32) {
+        float lo = kmin, hi = kmax;
+        for (int it = 0; it < 12; ++it) {
+            const float mid = 0.5f * (lo + hi);
+            if (!(mid > lo && mid < hi)) break;
+            int c = 0;
+            for (int i = lane; i < npend; i += 32) c += ws.pk[i] <= mid ? 1 : 0;
+            c = (int)__reduce_add_sync(CSS_FULL, (unsigned)c);
+            if (c < 32) lo = mid;
+            else {
+                hi = mid;
+                T = mid;
+                if (c <= 64) break;
+            }
+        }
+    }
+    int taken = 0, kept = 0;
+    for (int base = 0; base < npend; base += 32) {
+        const int i = base + lane;
+        int id = -1;
+        float k = 0.0f;
+        if (i < npend) { id = ws.pq[i]; k = ws.pk[i]; }
+        __syncwarp();
+        const bool cand = i < npend && k <= T;
+        const unsigned cm = __ballot_sync(CSS_FULL, cand);
+        const int r = taken + __popc(cm & css::lanemask_lt());
+        const bool take = cand && r < 32;
+        const bool keep = i < npend && !take;
+        const unsigned km = __ballot_sync(CSS_FULL, keep);
+        if (take) sm.sel[r] = id;
+        if (keep) {   // kept entries move forward only: p <= i
+            const int p = kept + __popc(km & css::lanemask_lt());
+            ws.pq[p] = id;
+            ws.pk[p] = k;
+        }
+        taken = min(32, taken + __popc(cm));
+        kept += __popc(km);
+    }
+    __syncwarp();
+    const int mine = lane < taken ? sm.sel[lane] : -1;
+    __syncwarp();
+    if (lane == 0) sm.npend = kept;
+    __syncwarp();
+    return mine;
+}
+
 template <class R>
 __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, int lane, int* status,
                            unsigned long long* counters) {
@@ -1150,7 +1261,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
     const double qxd = b[1] * m.lay[3 * f0] + b[2] * m.lay[3 * f0 + 1];
     const double qyd = b[2] * m.lay[3 * f0 + 2];
     ws_clear_shared<R>(ws, lane);
-    if (lane == 0) { sm.nwin = 0; sm.head = 0; sm.nface = 0; sm.nemit = 0; sm.err = 0; }
+    if (lane == 0) { sm.nwin = 0; sm.npend = 0; sm.nface = 0; sm.nemit = 0; sm.err = 0; }
     __syncwarp();
     if (lane == 0) face_add(ws, sm, f0);
     {   // the source's own pseudo-source corners
@@ -1199,18 +1310,23 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
         }
         child_round<R>(m, ws, sm, has, c, rc, lane);
     }
-    emit_round<R>(m, ws, sm, rc, lane);
     unsigned long long n_prop = 0;
+    const int max_waves = 4 * ws.wcap + 64;
     for (int wave = 0;; ++wave) {
         __syncwarp();
-        const int head = sm.head, nwin = min(sm.nwin, ws.wcap);
-        if (head >= nwin || sm.err) break;
-        __syncwarp();
-        if (lane == 0) sm.head = min(head + 32, nwin);
-        const int idx = head + lane;
+        const int npend = min(sm.npend, ws.wcap);
+        if ((npend == 0 && sm.nemit == 0) || sm.err) break;
+        if (wave > max_waves) { if (lane == 0) atomicOr(&sm.err, css::ST_ITER_LIMIT); break; }
+        float kmin, kmax;
+        pending_range<R>(ws, npend, lane, kmin, kmax);
+        // vertices whose distance no queued window can improve emit first; their windows
+        // join the queue and the smallest keys are looked at again
+        if (sm.nemit > 0 && emit_round<R>(m, ws, sm, rc, npend ? (double)kmin : INFINITY, lane) > 0) continue;
+        if (npend == 0) continue;
+        const int idx = select_wave<R>(ws, sm, npend, kmin, kmax, lane);
         Win<R> w;
         bool act = false;
-        if (idx < nwin) {
+        if (idx >= 0) {
             w = ws.win[idx];
             act = (w.flags & WIN_ALIVE) && !(w.flags & WIN_DONE) && (double)win_key<R>(w) < rc;
             if (act) ws.win[idx].flags = w.flags | WIN_DONE;
@@ -1225,7 +1341,6 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
         for (int q = 0; q < 3; ++q) vertex_round<R>(m, ws, sm, q < nvc, vc[q], rc, lane);
 #pragma unroll
         for (int q = 0; q < 2; ++q) child_round<R>(m, ws, sm, q < nch, ch[q], rc, lane);
-        emit_round<R>(m, ws, sm, rc, lane);
     }
     __syncwarp();
     const int err = sm.err;
@@ -1383,7 +1498,7 @@ size_t geo_ws_bytes_per_warp(int precision, int win_cap, int* log_eh, int* log_v
     *log_eh = le; *log_vh = lv; *log_fh = lf;
     *fcap = 1 << (lf - 1);
     *emcap = 1 << lv;
-    size_t off[11];
+    size_t off[13];
     return precision == CSS_FP32 ? ws_layout<float>(le, lv, lf, win_cap, *fcap, *emcap, off)
                                  : ws_layout<double>(le, lv, lf, win_cap, *fcap, *emcap, off);
 }
