@@ -92,8 +92,10 @@ int css_create(css_ctx** out, int device, void* stream);
 int css_destroy(css_ctx* ctx);
 const char* css_last_error(const css_ctx* ctx);
 /* Device-side counters of the last neighbour / force evaluation:
- * [0] sources, [1] windows created, [2] windows propagated, [3] pairs found,
- * [4] vertex emissions, [5] workspace retries. */
+ * [0] sources, [1] windows created, [2] windows propagated, [3] pairs found (all summed
+ * over the sources that completed), [4] sources deferred from the first pass to the
+ * second (their patch overflowed the first pass's tables or window pool),
+ * [5] workspace retries of the call. */
 int css_last_counters(const css_ctx* ctx, int64_t out[6]);
 
 /* ---------------------------------------------------------------- mesh (Sec. 2.2)
@@ -204,8 +206,9 @@ int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* f
 
 /* ---------------------------------------------------------------- measurement
  * css_last_kernel_ms: device time (ms) between CUDA events recorded on the context
- * stream immediately before and after the last neighbour/force kernel launch
- * (inside captured graphs too).  CSS_ERR_INVALID_ARG before any launch.
+ * stream immediately before the first and after the second pass of the last
+ * neighbour/force evaluation (inside captured graphs too).  CSS_ERR_INVALID_ARG before
+ * any launch.
  * css_fma_peak: measured dense FMA throughput (flop/s, 2 per FMA) of this GPU's
  * FP32 or FP64 pipes, from an FMA-chain kernel filling every SM; it has no
  * counterpart in the paper and serves as the ALU roofline denominator. */
@@ -213,10 +216,41 @@ int css_last_kernel_ms(css_ctx* ctx, double* ms);
 int css_fma_peak(css_ctx* ctx, int precision, double* flops_per_s);
 
 /* ---------------------------------------------------------------- tuning
- * Launch shape of the neighbour/force kernel: warps per CTA (1..8) and the
- * per-warp window-workspace capacity (windows; rounded up to a power of two).
- * 0 keeps the current value.  The batched form's autotuner calls this. */
-int css_set_launch(css_ctx* ctx, int32_t warps_per_cta, int32_t window_capacity);
+ * Launch shape of the neighbour/force evaluation (no counterpart in the paper, whose
+ * method runs one source per CPU process).  Every source runs in a first pass: one
+ * warp per source, per-warp hash tables (edges, pseudo-source vertices, faces) in
+ * shared memory and a window pool in global memory.  A source whose patch overflows
+ * them is deferred, and a second pass re-runs the deferred sources with global-memory
+ * tables and a larger pool on fewer warps.  Results do not depend on the shape.
+ *   warps_per_cta      first pass, 1..8
+ *   ctas_per_sm        first pass resident CTAs per SM, 0 = as many as fit, else a cap
+ *                      (fewer resident warps keep more of each warp's pool in L2)
+ *   tile               work items (sources) a warp claims per atomic, 1..64
+ *   shared_scale       first-pass table size, 0 (global tables), 1, 2, 4 or 8 times
+ *                      512 edges / 256 vertices / 512 faces per warp
+ *   window_capacity    first-pass windows per warp, 64..2^20 (rounded up to 2^k)
+ *   window_capacity2   second-pass windows per warp (grown on overflow)
+ *   warps2_per_sm      second-pass warps per SM, 1..8
+ * css_set_launch fails with CSS_ERR_INVALID_ARG when a value is out of range or the
+ * shape's shared memory does not fit an SM. */
+typedef struct css_launch {
+    int32_t warps_per_cta, ctas_per_sm, tile, shared_scale;
+    int32_t window_capacity, window_capacity2, warps2_per_sm;
+} css_launch;
+int css_set_launch(css_ctx* ctx, const css_launch* launch);
+int css_get_launch(const css_ctx* ctx, css_launch* launch);
+
+/* Autotuner: times the force evaluation of the given sets (one persistent launch over
+ * all their sources, as the batched form runs it) under candidate launch shapes --
+ * shared_scale x warps_per_cta x ctas_per_sm, with a first-pass pool of the context's
+ * window_capacity times the scale (4 times for global tables), then the tile on the
+ * best -- and keeps
+ * the fastest in the context.  Each candidate runs `reps` times (>= 1) after one
+ * untimed run; `sample` > 0 restricts every run to about that many sources spread over
+ * the sets (0: all).  best (may be NULL) receives the chosen shape and best_ms its
+ * time.  Particle states are unchanged; stored forces are marked stale.  Synchronises. */
+int css_autotune(css_ctx* ctx, css_parts* const* sets, int32_t n_sets, const css_potential* pot, double r_c,
+                 int precision, int32_t reps, int64_t sample, css_launch* best, double* best_ms);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,7 @@ SYMBOLS = ("css_create", "css_destroy", "css_last_error", "css_last_counters", "
            "css_mesh_upload", "css_mesh_free", "css_mesh_counts", "css_particles_set",
            "css_particles_get", "css_particles_free", "css_geodesic_neighbors", "css_compute_forces",
            "css_integrate_step", "css_batch_create", "css_batch_step", "css_batch_free",
-           "css_last_kernel_ms", "css_fma_peak", "css_particles_update")
+           "css_last_kernel_ms", "css_fma_peak", "css_particles_update", "css_get_launch", "css_autotune")
 
 
 class CssError(RuntimeError):
@@ -39,6 +39,16 @@ class CssError(RuntimeError):
 class Potential(C.Structure):
     _fields_ = [("kind", C.c_int32), ("eps", C.c_double), ("sigma", C.c_double),
                 ("r_cut", C.c_double), ("A", C.c_double)]
+
+
+class Launch(C.Structure):
+    """Launch shape of the neighbour/force evaluation (see css_launch in css.h)."""
+    _fields_ = [("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("tile", C.c_int32),
+                ("shared_scale", C.c_int32), ("window_capacity", C.c_int32), ("window_capacity2", C.c_int32),
+                ("warps2_per_sm", C.c_int32)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Integrator(C.Structure):
@@ -64,7 +74,9 @@ def load(path: str = LIB_PATH):
         "css_destroy": [P],
         "css_last_error": [P],
         "css_last_counters": [P, P],
-        "css_set_launch": [P, I32, I32],
+        "css_set_launch": [P, P],
+        "css_get_launch": [P, P],
+        "css_autotune": [P, P, I32, P, D, C.c_int, I32, I64, P, C.POINTER(D)],
         "css_mesh_upload": [P, P, I64, P, I64, P, C.POINTER(C.c_void_p)],
         "css_mesh_free": [P],
         "css_mesh_counts": [P, P],
@@ -142,7 +154,7 @@ class Context:
     def last_counters(self):
         out = np.zeros(6, np.int64)
         self.check(load().css_last_counters(self.h, out.ctypes.data))
-        return dict(zip(["sources", "windows", "propagated", "pairs", "emissions", "retries"], out.tolist()))
+        return dict(zip(["sources", "windows", "propagated", "pairs", "deferred", "retries"], out.tolist()))
 
     def last_kernel_ms(self) -> float:
         ms = C.c_double(0.0)
@@ -154,8 +166,30 @@ class Context:
         self.check(load().css_fma_peak(self.h, int(precision), C.byref(f)))
         return f.value
 
-    def set_launch(self, warps_per_cta: int = 0, window_capacity: int = 0):
-        self.check(load().css_set_launch(self.h, int(warps_per_cta), int(window_capacity)))
+    def get_launch(self) -> dict:
+        L = Launch()
+        self.check(load().css_get_launch(self.h, C.byref(L)))
+        return L.asdict()
+
+    def set_launch(self, **kw):
+        """Change fields of the launch shape (the others keep their values)."""
+        cur = self.get_launch()
+        unknown = set(kw) - set(cur)
+        if unknown:
+            raise KeyError(unknown)
+        cur.update(kw)
+        L = Launch(**{k: int(v) for k, v in cur.items()})
+        self.check(load().css_set_launch(self.h, C.byref(L)))
+
+    def autotune(self, sets, pot, r_c: float, precision: int, reps: int = 1, sample: int = 0):
+        """Pick the fastest launch shape for these particle sets; returns (shape, ms)."""
+        arr = (C.c_void_p * len(sets))(*[p.h.value for p in sets])
+        P = _pot(pot)
+        L = Launch()
+        ms = C.c_double(0.0)
+        self.check(load().css_autotune(self.h, arr, len(sets), C.byref(P), float(r_c), int(precision), int(reps),
+                                       int(sample), C.byref(L), C.byref(ms)))
+        return L.asdict(), ms.value
 
 
 def create(device: int = 0, stream: Optional[int] = None) -> Context:

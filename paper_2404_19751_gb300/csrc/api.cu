@@ -67,44 +67,80 @@ int next_pow2(int x) {
     return p;
 }
 
-// ---- workspace for the persistent neighbour/force kernel
-int ensure_ws(css_ctx* c, int precision, int shared, GeoWs* out, int* nctas) {
-    int bps = cssi::geodesic_blocks_per_sm(precision, c->warps_per_cta, shared);
-    if (bps < 1) bps = 1;
-    const int ncta = c->sm_count * bps;
-    const int nwarps = ncta * c->warps_per_cta;
+// ---- workspaces of the two passes of the persistent neighbour/force kernel
+struct GeoPlan {
+    GeoWs g1, g2;
+    int wpc1 = 0, nctas1 = 0, wpc2 = 0, nctas2 = 0;
+};
+
+// size (and zero on a layout change, so old bytes never look like valid hash tags) one
+// pass's workspace
+int ensure_buf(css_ctx* c, cssi::WsBuf& b, int precision, int win_cap, int shared, int nwarps, GeoWs* out) {
     GeoWs g{};
     g.shared = shared;
-    g.stride = cssi::geo_ws_bytes_per_warp(precision, c->win_cap, &g.log_eh, &g.log_vh, &g.log_fh, &g.fcap, &g.emcap);
-    g.wcap = c->win_cap;
+    g.stride = cssi::geo_ws_bytes_per_warp(precision, win_cap, &g.log_eh, &g.log_vh, &g.log_fh, &g.fcap, &g.emcap);
+    g.wcap = win_cap;
     g.nwarps = nwarps;
     const size_t need = g.stride * (size_t)nwarps;
-    // a layout change re-zeroes the workspace so old bytes never look like valid hash tags
-    const int64_t key = (int64_t)precision * 1000003 + (int64_t)c->win_cap * 31 + c->warps_per_cta + 17 * shared;
-    const bool relayout = (need > c->ws_bytes) || (c->ws_warps < nwarps) || (c->ws_key != key);
-    if (need > c->ws_bytes) {
-        cudaFree(c->ws);
-        c->ws = nullptr;
-        c->ws_bytes = 0;
-        TRY(c, "workspace", cudaMalloc(&c->ws, need));
-        c->ws_bytes = need;
+    const int64_t key = ((int64_t)precision * 1000003 + (int64_t)win_cap * 31 + nwarps) * 16 + shared;
+    const bool relayout = (need > b.bytes) || (b.warps < nwarps) || (b.key != key);
+    if (need > b.bytes) {
+        cudaFree(b.ws);
+        b.ws = nullptr;
+        b.bytes = 0;
+        TRY(c, "workspace", cudaMalloc(&b.ws, need));
+        b.bytes = need;
     }
-    if (c->ws_warps < nwarps) {
-        cudaFree(c->ws_gen);
-        c->ws_gen = nullptr;
-        TRY(c, "workspace", cudaMalloc(&c->ws_gen, nwarps * sizeof(uint32_t)));
-        c->ws_warps = nwarps;
+    if (b.warps < nwarps) {
+        cudaFree(b.gen);
+        b.gen = nullptr;
+        TRY(c, "workspace", cudaMalloc(&b.gen, nwarps * sizeof(uint32_t)));
+        b.warps = nwarps;
     }
     if (relayout) {
-        TRY(c, "workspace", cudaMemsetAsync(c->ws, 0, c->ws_bytes, c->stream));
-        TRY(c, "workspace", cudaMemsetAsync(c->ws_gen, 0, c->ws_warps * sizeof(uint32_t), c->stream));
-        c->ws_key = key;
+        TRY(c, "workspace", cudaMemsetAsync(b.ws, 0, b.bytes, c->stream));
+        TRY(c, "workspace", cudaMemsetAsync(b.gen, 0, b.warps * sizeof(uint32_t), c->stream));
+        b.key = key;
     }
-    g.base = (char*)c->ws;
-    g.gen = c->ws_gen;
+    g.base = (char*)b.ws;
+    g.gen = b.gen;
     *out = g;
-    *nctas = ncta;
     return CSS_OK;
+}
+
+// both passes for the context's launch shape and up to `nitems` work items
+int ensure_plan(css_ctx* c, int precision, int64_t nitems, GeoPlan* P) {
+    const cssi::LaunchCfg& L = c->cfg;
+    int bps = cssi::geodesic_blocks_per_sm(precision, L.warps_per_cta, L.shared_scale);
+    if (bps < 1) {
+        c->err = "launch shape does not fit an SM (" + std::to_string(L.warps_per_cta) + " warps per CTA, shared scale " +
+                 std::to_string(L.shared_scale) + ")";
+        return CSS_ERR_INVALID_ARG;
+    }
+    if (L.ctas_per_sm > 0) bps = std::min(bps, L.ctas_per_sm);
+    P->wpc1 = L.warps_per_cta;
+    P->nctas1 = c->sm_count * bps;
+    int rc = ensure_buf(c, c->ws1, precision, L.win_cap, L.shared_scale, P->nctas1 * P->wpc1, &P->g1);
+    if (rc) return rc;
+    P->wpc2 = L.warps2_per_sm;
+    P->nctas2 = c->sm_count;
+    rc = ensure_buf(c, c->ws2, precision, L.win_cap2, 0, P->nctas2 * P->wpc2, &P->g2);
+    if (rc) return rc;
+    if (c->defer_cap < nitems) {
+        cudaFree(c->defer);
+        c->defer = nullptr;
+        c->defer_cap = 0;
+        TRY(c, "deferral list", cudaMalloc(&c->defer, std::max<int64_t>(nitems, 1) * sizeof(int32_t)));
+        c->defer_cap = nitems;
+    }
+    return CSS_OK;
+}
+
+// the plan's identity, for keying captured graphs
+std::string plan_key(const css_ctx* c, const GeoPlan& P) {
+    const int64_t v[8] = {c->ws1.key, c->ws2.key, (int64_t)(uintptr_t)c->ws1.ws, (int64_t)(uintptr_t)c->ws2.ws,
+                          (int64_t)(uintptr_t)c->defer, P.nctas1, c->cfg.tile, P.nctas2};
+    return std::string((const char*)v, sizeof(v));
 }
 
 int ensure_pairs(css_parts* p, int cap) {
@@ -128,7 +164,7 @@ GeoJob make_job(css_parts* p, double rc, int want_pairs, int want_forces, const 
     j.bary = p->bary;
     j.fstart = p->fstart;
     j.fitems = p->fitems;
-    j.order = nullptr;
+    j.order = p->fitems;   // sources in face-rank (Morton) order
     j.rc = rc;
     j.want_pairs = want_pairs;
     j.pair_cap = p->pair_cap_alloc;
@@ -152,20 +188,31 @@ cudaError_t record_ev(css_ctx* c, cudaEvent_t ev) {
     return cudaEventRecord(ev, c->stream);
 }
 
-// one bucket + neighbour/force launch (no synchronisation)
-int enqueue_geo(css_parts* p, double rc, int prec, int want_pairs, int want_forces, const css_potential* pot,
-                const GeoWs& g, int nctas) {
-    css_ctx* c = p->ctx;
+// the two passes over a work queue, timed by the context's events (no synchronisation)
+int enqueue_passes(css_ctx* c, const GeoJob& j0, const GeoJob* djobs, const int32_t* job_of_item,
+                   const int32_t* src_of_item, int32_t nitems, int prec, const GeoPlan& P) {
     cudaStream_t st = c->stream;
-    TRY(c, "bucket", cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->fcnt, p->fstart, p->fitems,
-                                         p->scan_tmp, st));
     TRY(c, "reset", cudaMemsetAsync(c->dscal, 0, sizeof(int), st));
-    GeoJob j = make_job(p, rc, want_pairs, want_forces, pot);
+    TRY(c, "reset", cudaMemsetAsync(c->dscal + 2, 0, 2 * sizeof(int), st));
     TRY(c, "event", record_ev(c, c->ev_geo0));
-    TRY(c, "geodesic", cssi::launch_geodesic(j, nullptr, nullptr, nullptr, (int32_t)p->n, prec, g, c->warps_per_cta,
-                                             nctas, c->dscal, c->dscal + 1, c->dcount, st));
+    cssi::GeoQueue q1{job_of_item, src_of_item, nitems, nullptr, nullptr, c->defer, c->dscal + 2, c->cfg.tile};
+    TRY(c, "geodesic", cssi::launch_geodesic(j0, djobs, q1, prec, P.g1, P.wpc1, P.nctas1, c->dscal, c->dscal + 1,
+                                             c->dcount, st));
+    cssi::GeoQueue q2{job_of_item, src_of_item, nitems, c->defer, c->dscal + 2, nullptr, nullptr, 1};
+    TRY(c, "geodesic", cssi::launch_geodesic(j0, djobs, q2, prec, P.g2, P.wpc2, P.nctas2, c->dscal + 3, c->dscal + 1,
+                                             c->dcount, st));
     TRY(c, "event", record_ev(c, c->ev_geo1));
     return CSS_OK;
+}
+
+// one bucket + neighbour/force evaluation of one set (no synchronisation)
+int enqueue_geo(css_parts* p, double rc, int prec, int want_pairs, int want_forces, const css_potential* pot,
+                const GeoPlan& P) {
+    css_ctx* c = p->ctx;
+    TRY(c, "bucket", cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->mesh->frank, p->fcnt, p->fstart, p->fitems,
+                                         p->scan_tmp, c->stream));
+    GeoJob j = make_job(p, rc, want_pairs, want_forces, pot);
+    return enqueue_passes(c, j, nullptr, nullptr, nullptr, (int32_t)p->n, prec, P);
 }
 
 int read_status(css_ctx* c, int* status) {
@@ -173,33 +220,29 @@ int read_status(css_ctx* c, int* status) {
     TRY(c, "status", cudaMemcpyAsync(c->hcount, c->dcount, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
     TRY(c, "sync", cudaStreamSynchronize(c->stream));
     *status = *c->hstat;
-    for (int k = 0; k < 4; ++k) c->last_counters[k] = (int64_t)c->hcount[k];
+    for (int k = 0; k < 5; ++k) c->last_counters[k] = (int64_t)c->hcount[k];
     return CSS_OK;
 }
 
-// grow the capacity that overflowed; false when nothing can grow any more.  A table
-// overflow of a launch with shared-memory tables sets *to_global instead: the patch is
-// too large for them and the launch is repeated with the global tables.
-bool grow_for(css_ctx* c, int status, int* retries, int shared, bool* to_global) {
+// grow the capacity that overflowed in the second pass (the first pass defers instead of
+// failing); false when nothing can grow any more
+bool grow_for(css_ctx* c, int status, int* retries) {
     ++*retries;
-    *to_global = false;
+    ++c->last_counters[5];
     if (*retries > MAX_RETRY) return false;
     bool grown = false;
-    if ((status & css::ST_HASH_OVERFLOW) && shared) { *to_global = true; grown = true; status &= ~css::ST_HASH_OVERFLOW; }
     if (status & (css::ST_WIN_OVERFLOW | css::ST_HASH_OVERFLOW | css::ST_ITER_LIMIT)) {
-        if (c->win_cap >= WIN_CAP_MAX) return false;
-        c->win_cap *= 2;
+        if (c->cfg.win_cap2 >= WIN_CAP_MAX) return false;
+        c->cfg.win_cap2 *= 2;
         grown = true;
     }
     if (status & css::ST_PAIR_OVERFLOW) { c->pair_cap *= 2; grown = true; }
     return grown;
 }
 
-int use_shared(const css_parts* p) { return p->ctx->shared_tables && !p->global_tables; }
-
 int status_error(css_ctx* c, int status) {
     if (status & (css::ST_WIN_OVERFLOW | css::ST_HASH_OVERFLOW)) {
-        c->err = "window workspace exhausted (capacity " + std::to_string(c->win_cap) + ")";
+        c->err = "window workspace exhausted (capacity " + std::to_string(c->cfg.win_cap2) + ")";
         return CSS_ERR_QUEUE_OVERFLOW;
     }
     if (status & (css::ST_ITER_LIMIT | css::ST_WALK_LIMIT)) { c->err = "device loop reached its iteration cap"; return CSS_ERR_ITER_LIMIT; }
@@ -213,26 +256,22 @@ int status_error(css_ctx* c, int status) {
 int run_geo(css_parts* p, double rc, int prec, int want_pairs, int want_forces, const css_potential* pot) {
     css_ctx* c = p->ctx;
     int retries = 0;
-    TRY(c, "reset", cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), c->stream));
+    c->last_counters[5] = 0;
     for (;;) {
         if (want_pairs) { int rc2 = ensure_pairs(p, c->pair_cap); if (rc2) return rc2; }
-        GeoWs g;
-        int nctas = 0;
-        const int shared = use_shared(p);
-        int rc1 = ensure_ws(c, prec, shared, &g, &nctas);
+        GeoPlan P;
+        int rc1 = ensure_plan(c, prec, p->n, &P);
         if (rc1) return rc1;
+        TRY(c, "reset", cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), c->stream));
         TRY(c, "reset", cudaMemsetAsync(c->dscal + 1, 0, sizeof(int), c->stream));
         TRY(c, "reset", cudaMemsetAsync(c->depot, 0, sizeof(double), c->stream));
-        rc1 = enqueue_geo(p, rc, prec, want_pairs, want_forces, pot, g, nctas);
+        rc1 = enqueue_geo(p, rc, prec, want_pairs, want_forces, pot, P);
         if (rc1) return rc1;
         int status = 0;
         rc1 = read_status(c, &status);
         if (rc1) return rc1;
         if (status == 0) return CSS_OK;
-        c->last_counters[4] += 1;
-        bool to_global = false;
-        if (!grow_for(c, status, &retries, shared, &to_global)) return status_error(c, status);
-        if (to_global) p->global_tables = 1;
+        if (!grow_for(c, status, &retries)) return status_error(c, status);
     }
 }
 
@@ -286,8 +325,11 @@ int css_create(css_ctx** out, int device, void* stream) {
 
 int css_destroy(css_ctx* c) {
     if (!c) return CSS_ERR_INVALID_ARG;
-    cudaFree(c->ws);
-    cudaFree(c->ws_gen);
+    cudaFree(c->ws1.ws);
+    cudaFree(c->ws1.gen);
+    cudaFree(c->ws2.ws);
+    cudaFree(c->ws2.gen);
+    cudaFree(c->defer);
     cudaFree(c->dscal);
     cudaFree(c->dcount);
     cudaFree(c->depot);
@@ -304,12 +346,7 @@ const char* css_last_error(const css_ctx* c) { return c ? c->err.c_str() : "null
 
 int css_last_counters(const css_ctx* c, int64_t out[6]) {
     if (!c || !out) return CSS_ERR_INVALID_ARG;
-    out[0] = c->last_counters[0];
-    out[1] = c->last_counters[1];
-    out[2] = c->last_counters[2];
-    out[3] = c->last_counters[3];
-    out[4] = 0;
-    out[5] = c->last_counters[4];
+    for (int k = 0; k < 6; ++k) out[k] = c->last_counters[k];
     return CSS_OK;
 }
 
@@ -328,10 +365,40 @@ int css_fma_peak(css_ctx* c, int precision, double* flops_per_s) {
     return CSS_OK;
 }
 
-int css_set_launch(css_ctx* c, int32_t warps_per_cta, int32_t window_capacity) {
-    if (!c || warps_per_cta < 0 || warps_per_cta > 8 || window_capacity < 0) return CSS_ERR_INVALID_ARG;
-    if (warps_per_cta) c->warps_per_cta = warps_per_cta;
-    if (window_capacity) c->win_cap = next_pow2(window_capacity);
+static bool launch_ok(const css_launch* l) {
+    const int s = l->shared_scale;
+    return l->warps_per_cta >= 1 && l->warps_per_cta <= 8 && l->ctas_per_sm >= 0 && l->ctas_per_sm <= 32 &&
+           l->tile >= 1 && l->tile <= 64 && (s == 0 || s == 1 || s == 2 || s == 4 || s == 8) &&
+           l->window_capacity >= 64 && l->window_capacity <= (1 << 20) && l->window_capacity2 >= 64 &&
+           l->window_capacity2 <= (1 << 20) && l->warps2_per_sm >= 1 && l->warps2_per_sm <= 8;
+}
+
+int css_set_launch(css_ctx* c, const css_launch* l) {
+    if (!c || !l || !launch_ok(l)) return CSS_ERR_INVALID_ARG;
+    for (int prec : {CSS_FP32, CSS_FP64})
+        if (cssi::geodesic_blocks_per_sm(prec, l->warps_per_cta, l->shared_scale) < 1) {
+            c->err = "launch shape does not fit an SM";
+            return CSS_ERR_INVALID_ARG;
+        }
+    c->cfg.warps_per_cta = l->warps_per_cta;
+    c->cfg.ctas_per_sm = l->ctas_per_sm;
+    c->cfg.tile = l->tile;
+    c->cfg.shared_scale = l->shared_scale;
+    c->cfg.win_cap = next_pow2(l->window_capacity);
+    c->cfg.win_cap2 = next_pow2(l->window_capacity2);
+    c->cfg.warps2_per_sm = l->warps2_per_sm;
+    return CSS_OK;
+}
+
+int css_get_launch(const css_ctx* c, css_launch* l) {
+    if (!c || !l) return CSS_ERR_INVALID_ARG;
+    l->warps_per_cta = c->cfg.warps_per_cta;
+    l->ctas_per_sm = c->cfg.ctas_per_sm;
+    l->tile = c->cfg.tile;
+    l->shared_scale = c->cfg.shared_scale;
+    l->window_capacity = c->cfg.win_cap;
+    l->window_capacity2 = c->cfg.win_cap2;
+    l->warps2_per_sm = c->cfg.warps2_per_sm;
     return CSS_OK;
 }
 
@@ -361,6 +428,7 @@ int css_mesh_free(css_mesh* m) {
     cudaFree(m->he); cudaFree(m->twin); cudaFree(m->edge); cudaFree(m->fv); cudaFree(m->lay);
     cudaFree(m->frame); cudaFree(m->theta); cudaFree(m->pseudo); cudaFree(m->bnd);
     cudaFree(m->ring_start); cudaFree(m->ring); cudaFree(m->X); cudaFree(m->he32); cudaFree(m->lay32);
+    cudaFree(m->frank);
     delete m;
     return CSS_OK;
 }
@@ -571,12 +639,12 @@ int enqueue_move(css_parts* p, const css_integrator* it, const double* noise, in
 
 // enqueue one full step (no synchronisation); noise: device pointer to n x 2 normals or NULL
 int enqueue_step(css_parts* p, const css_potential* pot, const css_integrator* it, double rc, int prec,
-                 const double* noise, const GeoWs& g, int nctas) {
+                 const double* noise, const GeoPlan& P) {
     css_ctx* c = p->ctx;
     int r = enqueue_move(p, it, noise, 0);
     if (r) return r;
     TRY(c, "reset", cudaMemsetAsync(c->depot, 0, sizeof(double), c->stream));
-    r = enqueue_geo(p, rc, prec, 0, 1, pot, g, nctas);
+    r = enqueue_geo(p, rc, prec, 0, 1, pot, P);
     if (r) return r;
     return enqueue_move(p, it, noise, 1);
 }
@@ -624,13 +692,12 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
         }
     }
     int retries = 0;
+    c->last_counters[5] = 0;
     int rc = CSS_OK;
     for (;;) {
         TRY(c, "snapshot", snap_take(p));
-        GeoWs g;
-        int nctas = 0;
-        const int shared = use_shared(p);
-        rc = ensure_ws(c, precision, shared, &g, &nctas);
+        GeoPlan P;
+        rc = ensure_plan(c, precision, p->n, &P);
         if (rc) break;
         TRY(c, "reset", cudaMemsetAsync(c->dscal + 1, 0, sizeof(int), st));
         TRY(c, "reset", cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), st));
@@ -639,11 +706,11 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
             std::string key((const char*)pot, sizeof(*pot));
             key.append((const char*)it, sizeof(*it));
             key.append((const char*)&r_c, sizeof(r_c));
-            const int64_t shape[5] = {precision, c->ws_key, nctas, (int64_t)(uintptr_t)c->ws, shared};
-            key.append((const char*)shape, sizeof(shape));
+            key.append((const char*)&precision, sizeof(precision));
+            key.append(plan_key(c, P));
             if (!p->graph || p->graph_key != key) {
                 if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
-                rc = capture(c, [&]() { return enqueue_step(p, pot, it, r_c, precision, nullptr, g, nctas); }, &p->graph);
+                rc = capture(c, [&]() { return enqueue_step(p, pot, it, r_c, precision, nullptr, P); }, &p->graph);
                 if (rc == CSS_OK) p->graph_key = key;
             }
             for (int64_t s = 0; s < n_steps && rc == CSS_OK; ++s) {
@@ -652,16 +719,14 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
             }
         } else {
             for (int64_t s = 0; s < n_steps && rc == CSS_OK; ++s)
-                rc = enqueue_step(p, pot, it, r_c, precision, dnoise ? dnoise + (size_t)s * p->n * 2 : nullptr, g, nctas);
+                rc = enqueue_step(p, pot, it, r_c, precision, dnoise ? dnoise + (size_t)s * p->n * 2 : nullptr, P);
         }
         if (rc) break;
         int status = 0;
         rc = read_status(c, &status);
         if (rc) break;
         if (status == 0) break;
-        bool to_global = false;
-        if (!grow_for(c, status, &retries, shared, &to_global)) { rc = status_error(c, status); break; }
-        if (to_global) p->global_tables = 1;
+        if (!grow_for(c, status, &retries)) { rc = status_error(c, status); break; }
         TRY(c, "restore", snap_restore(p));
     }
     if (noise && !is_device_ptr(noise)) cudaFree(dnoise);
@@ -686,6 +751,9 @@ struct css_batch {
     int32_t* job_of_item = nullptr;
     int32_t* src_of_item = nullptr;
     int32_t nitems = 0;
+    // captured single step and the parameters it was captured for
+    cudaGraphExec_t graph = nullptr;
+    std::string graph_key;
 };
 
 int css_batch_create(css_ctx* c, css_parts* const* parts, int32_t n_sets, css_batch** out) {
@@ -722,6 +790,7 @@ int css_batch_create(css_ctx* c, css_parts* const* parts, int32_t n_sets, css_ba
 
 int css_batch_free(css_batch* b) {
     if (!b) return CSS_ERR_INVALID_ARG;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->djobs);
     cudaFree(b->job_of_item);
     cudaFree(b->src_of_item);
@@ -731,20 +800,15 @@ int css_batch_free(css_batch* b) {
 
 namespace {
 
-int batch_enqueue_forces(css_batch* b, const css_potential* pot, double rc, int prec, const GeoWs& g, int nctas) {
+int batch_enqueue_forces(css_batch* b, const css_potential* pot, double rc, int prec, const GeoPlan& P) {
     css_ctx* c = b->ctx;
     cudaStream_t st = c->stream;
     for (css_parts* p : b->sets)
-        TRY(c, "bucket", cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->fcnt, p->fstart,
+        TRY(c, "bucket", cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->mesh->frank, p->fcnt, p->fstart,
                                              p->fitems, p->scan_tmp, st));
-    TRY(c, "reset", cudaMemsetAsync(c->dscal, 0, sizeof(int), st));
     TRY(c, "reset", cudaMemsetAsync(c->depot, 0, sizeof(double), st));
     GeoJob j0 = make_job(b->sets[0], rc, 0, 1, pot);
-    TRY(c, "event", record_ev(c, c->ev_geo0));
-    TRY(c, "geodesic", cssi::launch_geodesic(j0, b->djobs, b->job_of_item, b->src_of_item, b->nitems, prec, g,
-                                             c->warps_per_cta, nctas, c->dscal, c->dscal + 1, c->dcount, st));
-    TRY(c, "event", record_ev(c, c->ev_geo1));
-    return CSS_OK;
+    return enqueue_passes(c, j0, b->djobs, b->job_of_item, b->src_of_item, b->nitems, prec, P);
 }
 
 }  // namespace
@@ -773,42 +837,46 @@ int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator*
         nve = !valid;
     }
     int retries = 0;
+    c->last_counters[5] = 0;
     for (;;) {
         for (css_parts* p : b->sets) TRY(c, "snapshot", snap_take(p));
-        GeoWs g;
-        int nctas = 0;
-        int shared = c->shared_tables;
-        for (css_parts* p : b->sets) shared = shared && !p->global_tables;
-        int rc = ensure_ws(c, precision, shared, &g, &nctas);
+        GeoPlan P;
+        int rc = ensure_plan(c, precision, b->nitems, &P);
         if (rc) return rc;
         TRY(c, "reset", cudaMemsetAsync(c->dscal + 1, 0, sizeof(int), st));
         TRY(c, "reset", cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), st));
         if (nve) {   // forces at the starting positions
-            rc = batch_enqueue_forces(b, pot, r_c, precision, g, nctas);
+            rc = batch_enqueue_forces(b, pot, r_c, precision, P);
             if (rc) return rc;
         }
         auto one_step = [&]() -> int {
             for (css_parts* p : b->sets) { int r = enqueue_move(p, it, nullptr, 0); if (r) return r; }
-            int r = batch_enqueue_forces(b, pot, r_c, precision, g, nctas);
+            int r = batch_enqueue_forces(b, pot, r_c, precision, P);
             if (r) return r;
             for (css_parts* p : b->sets) { r = enqueue_move(p, it, nullptr, 1); if (r) return r; }
             return CSS_OK;
         };
-        cudaGraphExec_t exec = nullptr;
-        rc = capture(c, one_step, &exec);
+        std::string key((const char*)pot, sizeof(*pot));
+        key.append((const char*)it, sizeof(*it));
+        key.append((const char*)&r_c, sizeof(r_c));
+        key.append((const char*)&precision, sizeof(precision));
+        key.append(plan_key(c, P));
+        if (!b->graph || b->graph_key != key) {
+            if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+            rc = capture(c, one_step, &b->graph);
+            if (rc) return rc;
+            b->graph_key = key;
+        }
         for (int64_t s = 0; s < n_steps && rc == CSS_OK; ++s) {
-            cudaError_t e = cudaGraphLaunch(exec, st);
+            cudaError_t e = cudaGraphLaunch(b->graph, st);
             if (e != cudaSuccess) rc = cuda_fail(c, "graph launch", e);
         }
-        if (exec) cudaGraphExecDestroy(exec);
         if (rc) return rc;
         int status = 0;
         rc = read_status(c, &status);
         if (rc) return rc;
         if (status == 0) break;
-        bool to_global = false;
-        if (!grow_for(c, status, &retries, shared, &to_global)) return status_error(c, status);
-        if (to_global) for (css_parts* p : b->sets) p->global_tables = 1;
+        if (!grow_for(c, status, &retries)) return status_error(c, status);
         for (css_parts* p : b->sets) TRY(c, "restore", snap_restore(p));
     }
     for (css_parts* p : b->sets) {
@@ -821,3 +889,126 @@ int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator*
     return CSS_OK;
 }
 
+
+// ------------------------------------------------------------------------------ autotuner
+namespace {
+
+// one timed force evaluation of the tuning queue under the context's current shape;
+// second-pass overflows grow its pool and repeat
+int tune_run(css_ctx* c, const GeoJob* djobs, const GeoJob& j0, const int32_t* job_of_item, const int32_t* src_of_item,
+             int32_t nitems, int prec, double* ms) {
+    int retries = 0;
+    for (;;) {
+        GeoPlan P;
+        int rc = ensure_plan(c, prec, nitems, &P);
+        if (rc) return rc;
+        TRY(c, "reset", cudaMemsetAsync(c->dscal + 1, 0, sizeof(int), c->stream));
+        TRY(c, "reset", cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), c->stream));
+        TRY(c, "reset", cudaMemsetAsync(c->depot, 0, sizeof(double), c->stream));
+        rc = enqueue_passes(c, j0, djobs, job_of_item, src_of_item, nitems, prec, P);
+        if (rc) return rc;
+        int status = 0;
+        rc = read_status(c, &status);
+        if (rc) return rc;
+        if (status == 0) {
+            float f = 0.f;
+            TRY(c, "tune timing", cudaEventElapsedTime(&f, c->ev_geo0, c->ev_geo1));
+            *ms = (double)f;
+            return CSS_OK;
+        }
+        if (!grow_for(c, status, &retries)) return status_error(c, status);
+    }
+}
+
+}  // namespace
+
+int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_potential* pot, double r_c,
+                 int precision, int32_t reps, int64_t sample, css_launch* best, double* best_ms) {
+    if (!c || !sets || n_sets < 1 || !pot || bad_prec(precision) || bad_rc(r_c) || reps < 1 || sample < 0)
+        return CSS_ERR_INVALID_ARG;
+    int64_t total = 0;
+    for (int k = 0; k < n_sets; ++k) {
+        if (!sets[k] || sets[k]->ctx != c) return CSS_ERR_INVALID_ARG;
+        total += sets[k]->n;
+    }
+    if (total < 1 || total > INT32_MAX) return CSS_ERR_INVALID_ARG;
+    cudaStream_t st = c->stream;
+    // the tuning queue: every source, or about `sample` of them spread evenly over the sets
+    const int64_t stride = (sample > 0 && sample < total) ? total / sample : 1;
+    std::vector<int32_t> hj, hs;
+    std::vector<GeoJob> jobs;
+    int64_t g = 0;
+    for (int k = 0; k < n_sets; ++k) {
+        jobs.push_back(make_job(sets[k], r_c, 0, 1, pot));
+        for (int64_t i = 0; i < sets[k]->n; ++i, ++g)
+            if (g % stride == 0) { hj.push_back(k); hs.push_back((int32_t)i); }
+    }
+    GeoJob* djobs = nullptr;
+    int32_t *dj = nullptr, *ds = nullptr;
+    auto cleanup = [&]() { cudaFree(djobs); cudaFree(dj); cudaFree(ds); };
+    cudaError_t e = cudaMalloc(&djobs, jobs.size() * sizeof(GeoJob));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(GeoJob), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = stage_in(hj.data(), hj.size(), &dj, st);
+    if (e == cudaSuccess) e = stage_in(hs.data(), hs.size(), &ds, st);
+    for (int k = 0; k < n_sets && e == cudaSuccess; ++k) {
+        css_parts* p = sets[k];
+        e = cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->mesh->frank, p->fcnt, p->fstart, p->fitems,
+                                p->scan_tmp, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(c, "autotune", e); }
+    const int32_t nitems = (int32_t)hj.size();
+    const cssi::LaunchCfg base = c->cfg;
+    cssi::LaunchCfg pick = base;
+    double pick_ms = INFINITY;
+    auto measure = [&](const cssi::LaunchCfg& L, double* out) -> int {
+        c->cfg = L;
+        c->cfg.win_cap2 = std::max(c->cfg.win_cap2, pick.win_cap2);
+        double t = 0.0;
+        int rc = tune_run(c, djobs, jobs[0], dj, ds, nitems, precision, &t);   // untimed: layout, warm caches
+        double m = INFINITY;
+        for (int r = 0; r < reps && rc == CSS_OK; ++r) {
+            rc = tune_run(c, djobs, jobs[0], dj, ds, nitems, precision, &t);
+            m = std::min(m, t);
+        }
+        *out = m;
+        return rc;
+    };
+    int rc = CSS_OK;
+    for (int s : {1, 2, 4, 0}) {
+        for (int wpc : {2, 4, 8}) {
+            const int bps = cssi::geodesic_blocks_per_sm(precision, wpc, s);
+            if (bps < 1) continue;
+            for (int cps : {0, 1}) {
+                if (cps == 1 && bps == 1) continue;   // same shape as "as many as fit"
+                cssi::LaunchCfg L = base;
+                L.shared_scale = s;
+                L.win_cap = base.win_cap * (s ? s : 4);   // the pool grows with the patch the tables hold
+                L.warps_per_cta = wpc;
+                L.ctas_per_sm = cps;
+                L.tile = 1;
+                double t = 0.0;
+                rc = measure(L, &t);
+                if (rc) break;
+                if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
+            }
+            if (rc) break;
+        }
+        if (rc) break;
+    }
+    for (int tile : {2, 4, 8}) {
+        if (rc) break;
+        cssi::LaunchCfg L = pick;
+        L.tile = tile;
+        double t = 0.0;
+        rc = measure(L, &t);
+        if (rc == CSS_OK && t < pick_ms) { pick_ms = t; pick = c->cfg; }
+    }
+    cleanup();
+    c->cfg = rc == CSS_OK ? pick : base;
+    for (int k = 0; k < n_sets; ++k) sets[k]->force_valid = 0;   // forces of the sample only
+    if (rc) return rc;
+    if (best) css_get_launch(c, best);
+    if (best_ms) *best_ms = pick_ms;
+    return CSS_OK;
+}

@@ -45,6 +45,7 @@ struct DMesh {
     const int32_t* ring;          // 3 nf corners h with fv[h] == v, grouped by vertex
     const HeRec32* he32;          // 3 nf, FP32 copies of he
     const float* lay32;           // 3 nf, FP32 copies of lay
+    const int32_t* frank;         // nf: rank of each face along a Morton curve (bucket order)
 };
 
 __device__ __forceinline__ double cross2(double ax, double ay, double bx, double by) { return ax * by - ay * bx; }

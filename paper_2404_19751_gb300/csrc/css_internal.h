@@ -9,23 +9,45 @@
 #include "../../include/css.h"
 #include "css_dev.cuh"
 
+namespace cssi {
+// Launch shape of the neighbour / force evaluation.  The first pass runs every source
+// with per-warp tables in shared memory (scaled by `shared_scale`, 0: global tables) and a
+// window pool of `win_cap`; sources whose patch overflows either are deferred to a
+// second pass with global tables and a pool of `win_cap2`, on fewer warps.
+struct LaunchCfg {
+    int warps_per_cta = 4;   // first pass
+    int ctas_per_sm = 0;     // 0: as many as fit
+    int tile = 1;            // work items a warp claims at a time
+    int shared_scale = 1;    // 0, 1, 2, 4, 8
+    int win_cap = 2048;
+    int win_cap2 = 16384;
+    int warps2_per_sm = 2;   // second pass: warps per SM (one CTA each)
+};
+// a second-pass workspace (global tables)
+struct WsBuf {
+    void* ws = nullptr;
+    size_t bytes = 0;
+    uint32_t* gen = nullptr;
+    int warps = 0;
+    int64_t key = -1;        // layout the bytes were zeroed for
+};
+}  // namespace cssi
+
 struct css_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int own_stream = 0;
     int sm_count = 0;
     std::string err;
-    // neighbour/force workspace (grown on demand)
-    void* ws = nullptr;
-    size_t ws_bytes = 0;
-    uint32_t* ws_gen = nullptr;      // per warp generation counters
-    int ws_warps = 0;
-    int64_t ws_key = -1;             // layout the workspace bytes were zeroed for
-    int warps_per_cta = 4;
-    int win_cap = 2048;              // windows per warp workspace
+    // neighbour/force workspaces of the two passes (grown on demand)
+    cssi::WsBuf ws1, ws2;
+    cssi::LaunchCfg cfg;
     int pair_cap = 64;               // pairs per source slab
-    int shared_tables = 1;           // try shared-memory tables first
-    // small device scalars: [0] work counter, [1] status, [2..] counters
+    // deferral list of the first pass (one entry per work item at most)
+    int32_t* defer = nullptr;
+    int64_t defer_cap = 0;
+    // small device scalars: [0] first-pass work counter, [1] status, [2] deferred count,
+    // [3] second-pass work counter
     int* dscal = nullptr;
     unsigned long long* dcount = nullptr;   // 8 counters
     double* depot = nullptr;
@@ -56,6 +78,7 @@ struct css_mesh {
     double* X = nullptr;
     css::HeRec32* he32 = nullptr;
     float* lay32 = nullptr;
+    int32_t* frank = nullptr;   // nf: Morton rank of each face
     css::DMesh view() const;
 };
 
@@ -90,7 +113,6 @@ struct css_parts {
     double* pd = nullptr;
     double* pt = nullptr;
     int pair_cap_alloc = 0;
-    int global_tables = 0;      // this set's patches overflowed the shared-memory tables
     // captured single-step graph and the launch parameters it was captured for
     cudaGraphExec_t graph = nullptr;
     std::string graph_key;
@@ -121,8 +143,20 @@ struct GeoJob {
     double* epot;
 };
 
+// where a launch takes its work items from
+struct GeoQueue {
+    const int32_t* job_of_item;   // NULL: one job
+    const int32_t* src_of_item;   // NULL: item = source index (or the job's order)
+    int32_t nitems;
+    const int32_t* item_list;     // second pass: items from the deferral list ...
+    const int* item_count;        // ... of this many entries (device)
+    int32_t* defer_list;          // first pass: where overflowing items go (NULL: report)
+    int* defer_count;
+    int tile;
+};
+
 struct GeoWs {
-    int shared;              // keyed tables in shared memory (else in the global slice)
+    int shared;              // scale of the keyed tables in shared memory, 0: global slice
     char* base;
     size_t stride;           // bytes per warp
     int log_eh, log_vh, log_fh;
@@ -134,18 +168,20 @@ struct GeoWs {
 // geodesic.cu
 size_t geo_ws_bytes_per_warp(int precision, int win_cap, int* log_eh, int* log_vh, int* log_fh,
                              int* fcap, int* emcap);
-cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const int32_t* job_of_item,
-                            const int32_t* src_of_item, int32_t nitems, int precision,
+cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const GeoQueue& q, int precision,
                             const GeoWs& ws, int warps_per_cta, int nctas, int* work_counter,
                             int* status, unsigned long long* counters, cudaStream_t st);
-int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared);
+int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared_scale);
+size_t geodesic_shared_bytes(int precision, int warps_per_cta, int shared_scale);
 cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd,
                                  const double* pt, int pair_cap, const int64_t* row_start,
                                  int32_t* out_j, double* out_d, double* out_t, cudaStream_t st);
 
 // dynamics.cu
-cudaError_t launch_bucket(int32_t n, int32_t nf, const int32_t* face, int32_t* fcnt, int32_t* fstart,
-                          int32_t* fitems, int32_t* scan_tmp, cudaStream_t st);
+// particles bucketed by face rank: fstart (nf + 1) is indexed by frank[face] (NULL: by
+// face), fitems lists the particles in rank order
+cudaError_t launch_bucket(int32_t n, int32_t nf, const int32_t* face, const int32_t* frank, int32_t* fcnt,
+                          int32_t* fstart, int32_t* fitems, int32_t* scan_tmp, cudaStream_t st);
 size_t scan_tmp_ints(int64_t count);
 cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t count, int32_t* tmp,
                             cudaStream_t st);

@@ -95,16 +95,17 @@ __global__ void k_tile_apply(const Ti* in, int64_t n_in, int64_t n, const To* su
 }
 
 // ------------------------------------------------------------------ bucketing (face CSR)
-__global__ void k_count(int32_t n, const int32_t* face, int32_t* cnt) {
+__global__ void k_count(int32_t n, const int32_t* face, const int32_t* frank, int32_t* cnt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd(cnt + face[i], 1);
+    if (i < n) atomicAdd(cnt + (frank ? frank[face[i]] : face[i]), 1);
 }
 
 // decrements the counts back to zero while placing particles
-__global__ void k_scatter(int32_t n, const int32_t* face, int32_t* cnt, const int32_t* start, int32_t* items) {
+__global__ void k_scatter(int32_t n, const int32_t* face, const int32_t* frank, int32_t* cnt, const int32_t* start,
+                          int32_t* items) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int f = face[i];
+    const int f = frank ? frank[face[i]] : face[i];
     const int p = atomicSub(cnt + f, 1) - 1;
     items[start[f] + p] = i;
 }
@@ -389,12 +390,12 @@ cudaError_t launch_scan_rows(const int32_t* cnt, int64_t* row_start, int32_t n, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_bucket(int32_t n, int32_t nf, const int32_t* face, int32_t* fcnt, int32_t* fstart, int32_t* fitems,
-                          int32_t* scan_tmp, cudaStream_t st) {
-    k_count<<<nb(n), 256, 0, st>>>(n, face, fcnt);
+cudaError_t launch_bucket(int32_t n, int32_t nf, const int32_t* face, const int32_t* frank, int32_t* fcnt,
+                          int32_t* fstart, int32_t* fitems, int32_t* scan_tmp, cudaStream_t st) {
+    k_count<<<nb(n), 256, 0, st>>>(n, face, frank, fcnt);
     cudaError_t e = launch_scan_i32(fcnt, fstart, (int64_t)nf + 1, scan_tmp, st);
     if (e != cudaSuccess) return e;
-    k_scatter<<<nb(n), 256, 0, st>>>(n, face, fcnt, fstart, fitems);
+    k_scatter<<<nb(n), 256, 0, st>>>(n, face, frank, fcnt, fstart, fitems);
     return cudaGetLastError();
 }
 

@@ -185,32 +185,42 @@ __device__ inline Ws<R> ws_bind(const cssi::GeoWs& g, int warp) {
     return w;
 }
 
-// shared-memory tables of one warp (sizes are powers of two; overflow makes the host rerun
-// the launch with the global tables)
+// shared-memory tables of one warp.  Their sizes are the base sizes below times a
+// power-of-two scale chosen per launch (larger patches, fewer warps per SM); a source
+// whose patch overflows them is handed to the second, global-table pass.
 constexpr int SH_LOG_EH = 9, SH_LOG_VH = 8, SH_LOG_FH = 9;
 constexpr int SH_FCAP = 512, SH_EMCAP = 256;
 
-template <class R>
-__host__ __device__ constexpr size_t sh_bytes_per_warp() {
-    return (size_t)(1 << SH_LOG_EH) * 8 + (size_t)(1 << SH_LOG_VH) * (4 + 8 + 2 * sizeof(R) + 4) +
-           (size_t)(1 << SH_LOG_FH) * 4 + (size_t)SH_FCAP * 4 + (size_t)SH_EMCAP * 4;
+__host__ __device__ inline int sh_log2(int scale) {
+    int l = 0;
+    while ((1 << l) < scale) ++l;
+    return l;
 }
 
 template <class R>
-__device__ inline void ws_bind_shared(Ws<R>& w, unsigned char* base) {
+__host__ __device__ inline size_t sh_bytes_per_warp(int scale) {
+    const size_t s = (size_t)1 << sh_log2(scale);
+    return s * ((size_t)(1 << SH_LOG_EH) * 8 + (size_t)(1 << SH_LOG_VH) * (4 + 8 + 2 * sizeof(R) + 4) +
+                (size_t)(1 << SH_LOG_FH) * 4 + (size_t)SH_FCAP * 4 + (size_t)SH_EMCAP * 4);
+}
+
+template <class R>
+__device__ inline void ws_bind_shared(Ws<R>& w, unsigned char* base, int scale) {
+    const int ls = sh_log2(scale);
+    const int eh = 1 << (SH_LOG_EH + ls), vh = 1 << (SH_LOG_VH + ls), fh = 1 << (SH_LOG_FH + ls);
     unsigned char* p = base;
-    w.sekey = (int32_t*)p; p += (1 << SH_LOG_EH) * 4;
-    w.ehead = (int32_t*)p; p += (1 << SH_LOG_EH) * 4;
-    w.vdist = (double*)p; p += (1 << SH_LOG_VH) * 8;
-    w.vtan = (R*)p; p += (1 << SH_LOG_VH) * 2 * sizeof(R);
-    w.svkey = (int32_t*)p; p += (1 << SH_LOG_VH) * 4;
-    w.vflag = (int32_t*)p; p += (1 << SH_LOG_VH) * 4;
-    w.sfkey = (int32_t*)p; p += (1 << SH_LOG_FH) * 4;
-    w.flist = (int32_t*)p; p += SH_FCAP * 4;
+    w.sekey = (int32_t*)p; p += eh * 4;
+    w.ehead = (int32_t*)p; p += eh * 4;
+    w.vdist = (double*)p; p += vh * 8;
+    w.vtan = (R*)p; p += vh * 2 * sizeof(R);
+    w.svkey = (int32_t*)p; p += vh * 4;
+    w.vflag = (int32_t*)p; p += vh * 4;
+    w.sfkey = (int32_t*)p; p += fh * 4;
+    w.flist = (int32_t*)p; p += (SH_FCAP << ls) * 4;
     w.emit = (int32_t*)p;
     w.vvid = w.svkey;   // the key is the vertex id
-    w.log_eh = SH_LOG_EH; w.log_vh = SH_LOG_VH; w.log_fh = SH_LOG_FH;
-    w.fcap = SH_FCAP; w.emcap = SH_EMCAP;
+    w.log_eh = SH_LOG_EH + ls; w.log_vh = SH_LOG_VH + ls; w.log_fh = SH_LOG_FH + ls;
+    w.fcap = SH_FCAP << ls; w.emcap = SH_EMCAP << ls;
     w.shared = true;
 }
 
@@ -268,9 +278,9 @@ __device__ __forceinline__ int ws_fins(Ws<R>& ws, int32_t key, bool& claimed) {
 template <class R>
 __device__ __forceinline__ void ws_clear_shared(Ws<R>& ws, int lane) {
     if (!ws.shared) return;
-    for (int k = lane; k < (1 << SH_LOG_EH); k += 32) ws.sekey[k] = -1;
-    for (int k = lane; k < (1 << SH_LOG_VH); k += 32) ws.svkey[k] = -1;
-    for (int k = lane; k < (1 << SH_LOG_FH); k += 32) ws.sfkey[k] = -1;
+    for (int k = lane; k < (1 << ws.log_eh); k += 32) ws.sekey[k] = -1;
+    for (int k = lane; k < (1 << ws.log_vh); k += 32) ws.svkey[k] = -1;
+    for (int k = lane; k < (1 << ws.log_fh); k += 32) ws.sfkey[k] = -1;
     __syncwarp();
 }
 
@@ -1253,7 +1263,7 @@ __device__ int select_wave(Ws<R>& ws, WarpSm& sm, int npend, float kmin, float k
 
 template <class R>
 __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, int lane, int* status,
-                           unsigned long long* counters) {
+                           unsigned long long* counters, int item, int32_t* defer_list, int* defer_count) {
     const DMesh& m = J.m;
     const double rc = J.rc;
     const int f0 = J.face[i];
@@ -1344,6 +1354,15 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
     }
     __syncwarp();
     const int err = sm.err;
+    // a patch too large for this pass's tables or pool: hand the source to the second pass
+    if (defer_list && (err & (css::ST_WIN_OVERFLOW | css::ST_HASH_OVERFLOW | css::ST_ITER_LIMIT))) {
+        if (lane == 0) {
+            defer_list[atomicAdd(defer_count, 1)] = item;
+            atomicAdd(counters + 4, 1ull);
+        }
+        __syncwarp();
+        return;
+    }
     const int nface = min(sm.nface, ws.fcap);
     // ---- target evaluation (+ forces)
     const R qx = (R)qxd, qy = (R)qyd;
@@ -1353,7 +1372,12 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
     for (int fb = 0; fb < nface; fb += 32) {
         const int fi = fb + lane;
         int fl = -1, st = 0, cnt = 0;
-        if (fi < nface) { fl = ws.flist[fi]; st = J.fstart[fl]; cnt = J.fstart[fl + 1] - st; }
+        if (fi < nface) {
+            fl = ws.flist[fi];
+            const int key = m.frank ? m.frank[fl] : fl;
+            st = J.fstart[key];
+            cnt = J.fstart[key + 1] - st;
+        }
         int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(CSS_FULL, incl, o);
@@ -1428,9 +1452,8 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
 }
 
 template <class R>
-__global__ void __launch_bounds__(256) k_geodesic(cssi::GeoJob job0, const cssi::GeoJob* jobs,
-                                                  const int32_t* job_of_item, const int32_t* src_of_item,
-                                                  int32_t nitems, cssi::GeoWs g, int* work, int* status,
+__global__ void __launch_bounds__(256) k_geodesic(cssi::GeoJob job0, const cssi::GeoJob* jobs, cssi::GeoQueue q,
+                                                  cssi::GeoWs g, int* work, int* status,
                                                   unsigned long long* counters) {
     __shared__ WarpSm smem[MAX_WARPS_CTA];
     const int lane = threadIdx.x & 31;
@@ -1440,22 +1463,30 @@ __global__ void __launch_bounds__(256) k_geodesic(cssi::GeoJob job0, const cssi:
     WarpSm& sm = smem[wib];
     Ws<R> ws = ws_bind<R>(g, gw);
     extern __shared__ __align__(16) unsigned char dsm[];
-    if (g.shared) ws_bind_shared<R>(ws, dsm + (size_t)wib * sh_bytes_per_warp<R>());
+    if (g.shared) ws_bind_shared<R>(ws, dsm + (size_t)wib * sh_bytes_per_warp<R>(g.shared), g.shared);
     uint32_t gen = 0;
     if (lane == 0) gen = g.gen[gw];
     gen = __shfl_sync(CSS_FULL, gen, 0);
+    // the second pass takes its work items from the first pass's deferral list
+    const int nitems = q.item_count ? min(*(volatile const int*)q.item_count, q.nitems) : q.nitems;
+    const int tile = max(1, q.tile);
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(work, 1);
-        item = __shfl_sync(CSS_FULL, item, 0);
-        if (item >= nitems) break;
-        const int jid = job_of_item ? job_of_item[item] : 0;
-        const cssi::GeoJob& J = jobs ? jobs[jid] : job0;
-        const int src = src_of_item ? src_of_item[item] : (J.order ? J.order[item] : item);
-        ++gen;
-        if (gen == 0) gen = 1;   // 0 marks never-used entries
-        ws.gen = gen;
-        run_source<R>(J, src, ws, sm, lane, status, counters);
+        int base = 0;
+        if (lane == 0) base = atomicAdd(work, tile);
+        base = __shfl_sync(CSS_FULL, base, 0);
+        if (base >= nitems) break;
+        const int end = min(base + tile, nitems);
+        for (int k = base; k < end; ++k) {
+            const int item = q.item_list ? q.item_list[k] : k;
+            const int jid = q.job_of_item ? q.job_of_item[item] : 0;
+            const cssi::GeoJob& J = jobs ? jobs[jid] : job0;
+            const int pos = q.src_of_item ? q.src_of_item[item] : item;   // position in the set's order
+            const int src = J.order ? J.order[pos] : pos;
+            ++gen;
+            if (gen == 0) gen = 1;   // 0 marks never-used entries
+            ws.gen = gen;
+            run_source<R>(J, src, ws, sm, lane, status, counters, item, q.defer_list, q.defer_count);
+        }
     }
     if (lane == 0) g.gen[gw] = gen;
 }
@@ -1503,35 +1534,49 @@ size_t geo_ws_bytes_per_warp(int precision, int win_cap, int* log_eh, int* log_v
                                  : ws_layout<double>(le, lv, lf, win_cap, *fcap, *emcap, off);
 }
 
-cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const int32_t* job_of_item,
-                            const int32_t* src_of_item, int32_t nitems, int precision, const GeoWs& ws,
-                            int warps_per_cta, int nctas, int* work_counter, int* status,
+size_t geodesic_shared_bytes(int precision, int warps_per_cta, int shared_scale) {
+    if (!shared_scale) return 0;
+    return (size_t)warps_per_cta * (precision == CSS_FP32 ? sh_bytes_per_warp<float>(shared_scale)
+                                                          : sh_bytes_per_warp<double>(shared_scale));
+}
+
+cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const GeoQueue& q, int precision,
+                            const GeoWs& ws, int warps_per_cta, int nctas, int* work_counter, int* status,
                             unsigned long long* counters, cudaStream_t st) {
     const dim3 block(32 * warps_per_cta);
-    if (precision == CSS_FP32) {
-        const size_t sm = ws.shared ? warps_per_cta * sh_bytes_per_warp<float>() : 0;
-        k_geodesic<float><<<nctas, block, sm, st>>>(job0, djobs, job_of_item, src_of_item, nitems, ws, work_counter,
-                                                    status, counters);
-    } else {
-        const size_t sm = ws.shared ? warps_per_cta * sh_bytes_per_warp<double>() : 0;
-        k_geodesic<double><<<nctas, block, sm, st>>>(job0, djobs, job_of_item, src_of_item, nitems, ws, work_counter,
-                                                     status, counters);
-    }
+    const size_t sm = geodesic_shared_bytes(precision, warps_per_cta, ws.shared);
+    if (precision == CSS_FP32)
+        k_geodesic<float><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
+    else
+        k_geodesic<double><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
     return cudaGetLastError();
 }
 
-int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared) {
+// resident CTAs per SM for a launch shape (0: the shape does not fit an SM)
+template <class R>
+static int blocks_per_sm(int warps_per_cta, size_t dyn) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_geodesic<R>) != cudaSuccess) { cudaGetLastError(); return 0; }
+    const int room = optin - (int)fa.sharedSizeBytes;   // dynamic shared memory a CTA may take
+    if (dyn > (size_t)room) return 0;
+    if (cudaFuncSetAttribute(k_geodesic<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, room) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     int nb = 0;
-    if (precision == CSS_FP32) {
-        const size_t sm = shared ? warps_per_cta * sh_bytes_per_warp<float>() : 0;
-        cudaFuncSetAttribute(k_geodesic<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * sh_bytes_per_warp<float>()));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<float>, 32 * warps_per_cta, sm);
-    } else {
-        const size_t sm = shared ? warps_per_cta * sh_bytes_per_warp<double>() : 0;
-        cudaFuncSetAttribute(k_geodesic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * sh_bytes_per_warp<double>()));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<double>, 32 * warps_per_cta, sm);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<R>, 32 * warps_per_cta, dyn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
     }
     return nb;
+}
+
+int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared_scale) {
+    const size_t dyn = geodesic_shared_bytes(precision, warps_per_cta, shared_scale);
+    return precision == CSS_FP32 ? blocks_per_sm<float>(warps_per_cta, dyn) : blocks_per_sm<double>(warps_per_cta, dyn);
 }
 
 cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd,
@@ -1625,13 +1670,15 @@ int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* f
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, 256 + 8 * 8, st);
     if (e == cudaSuccess && e_pot) e = cudaMemsetAsync(e_pot, 0, sizeof(double), st);
-    if (e == cudaSuccess) e = cssi::launch_bucket((int32_t)n, (int32_t)mesh->nf, face, fcnt, fstart, fitems, scan, st);
+    if (e == cudaSuccess)
+        e = cssi::launch_bucket((int32_t)n, (int32_t)mesh->nf, face, mesh->frank, fcnt, fstart, fitems, scan, st);
     cssi::GeoJob j{};
     j.m = mesh->view();
     j.n = (int32_t)n;
     j.face = face;
     j.bary = bary;
     j.fstart = fstart;
+    j.order = fitems;
     j.fitems = fitems;
     j.rc = r_c;
     j.pcnt = pcnt;
@@ -1639,9 +1686,11 @@ int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* f
     j.pot = *pot;
     j.force = forces;
     j.epot = e_pot;
-    if (e == cudaSuccess)
-        e = cssi::launch_geodesic(j, nullptr, nullptr, nullptr, (int32_t)n, precision, g, NA_WARPS_PER_CTA,
-                                  g.nwarps / NA_WARPS_PER_CTA, scal, scal + 1, cnt, st);
+    if (e == cudaSuccess) {   // one pass, global tables; a source overflowing them is reported
+        const cssi::GeoQueue q{nullptr, nullptr, (int32_t)n, nullptr, nullptr, nullptr, nullptr, 1};
+        e = cssi::launch_geodesic(j, nullptr, q, precision, g, NA_WARPS_PER_CTA, g.nwarps / NA_WARPS_PER_CTA, scal,
+                                  scal + 1, cnt, st);
+    }
     int status = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, scal + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

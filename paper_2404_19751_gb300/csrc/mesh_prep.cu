@@ -5,9 +5,15 @@
 // three or more make the mesh non-manifold.  Geometry: per-face planar layout
 // (minimum-image edge vectors on periodic meshes), per-half-edge frame and the
 // rotations into the two neighbouring frames, vertex angle sums (summed over the
-// sorted one-ring, so the result does not depend on thread timing).
+// sorted one-ring, so the result does not depend on thread timing).  Faces are also
+// ranked along a Morton curve through their first corners: particle buckets are kept in
+// that order, so sources processed at the same time sit close together and their
+// patches share the L2.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "css_internal.h"
 
@@ -189,6 +195,26 @@ inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b
 
 }  // namespace
 
+namespace {
+// first corner of every face (world), for the face ranking
+__global__ void k_origin(const double* frame, int64_t nf, float* out) {
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    out[3 * f] = (float)frame[9 * f];
+    out[3 * f + 1] = (float)frame[9 * f + 1];
+    out[3 * f + 2] = (float)frame[9 * f + 2];
+}
+
+uint32_t spread10(uint32_t v) {   // 10 bits to every third of 30
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+}  // namespace
+
 css::DMesh css_mesh::view() const {
     css::DMesh d;
     d.nv = (int32_t)nv;
@@ -209,6 +235,7 @@ css::DMesh css_mesh::view() const {
     d.ring = ring;
     d.he32 = he32;
     d.lay32 = lay32;
+    d.frank = frank;
     return d;
 }
 
@@ -263,6 +290,7 @@ int build_mesh(css_ctx* ctx, const double* dX, int64_t nv, const int32_t* dF, in
     CK(cudaMalloc(&m->X, 3 * nv * sizeof(double)));
     CK(cudaMalloc(&m->he32, nh * sizeof(css::HeRec32)));
     CK(cudaMalloc(&m->lay32, 3 * nf * sizeof(float)));
+    CK(cudaMalloc(&m->frank, nf * sizeof(int32_t)));
     CK(cudaMalloc(&ring_cnt, (nv + 1) * sizeof(int32_t)));
     CK(cudaMalloc(&tmp, scan_tmp_ints(nv + 1) * sizeof(int32_t)));
     CK(cudaMemcpyAsync(m->X, dX, 3 * nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -298,6 +326,34 @@ int build_mesh(css_ctx* ctx, const double* dX, int64_t nv, const int32_t* dF, in
     CK(cudaStreamSynchronize(st));
     m->ne = (int64_t)hcnt[0];
     m->npseudo = (int64_t)hcnt[1];
+    {   // Morton rank of every face (host sort, once per mesh)
+        float* dorg = nullptr;
+        CK(cudaMalloc(&dorg, 3 * nf * sizeof(float)));
+        k_origin<<<nblk(nf), 256, 0, st>>>(m->frame, nf, dorg);
+        std::vector<float> org(3 * nf);
+        cudaError_t e = cudaMemcpyAsync(org.data(), dorg, 3 * nf * sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(dorg);
+        CK(e);
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t f = 0; f < nf; ++f)
+            for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], org[3 * f + a]); hi[a] = std::max(hi[a], org[3 * f + a]); }
+        std::vector<uint64_t> key(nf);
+        for (int64_t f = 0; f < nf; ++f) {
+            uint32_t code = 0;
+            for (int a = 0; a < 3; ++a) {
+                const float ext = hi[a] - lo[a];
+                const uint32_t q = ext > 0.f ? (uint32_t)std::min(1023.f, (org[3 * f + a] - lo[a]) / ext * 1024.f) : 0u;
+                code |= spread10(q) << a;
+            }
+            key[f] = ((uint64_t)code << 32) | (uint64_t)f;
+        }
+        std::sort(key.begin(), key.end());
+        std::vector<int32_t> rank(nf);
+        for (int64_t r = 0; r < nf; ++r) rank[(int64_t)(key[r] & 0xffffffffu)] = (int32_t)r;
+        CK(cudaMemcpyAsync(m->frank, rank.data(), nf * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
 done:
     cudaFree(t.key);
     cudaFree(t.cnt);

@@ -1,0 +1,100 @@
+"""Launch shapes, the two-pass deferral and the autotuner (needs a GB300).
+
+The result of a neighbour / force evaluation must not depend on how it is launched:
+every shape below -- shared-memory tables of each scale or global tables, 1 to 8 warps
+per CTA, capped residency, tiled work claims, and first-pass pools so small that most
+sources overflow and are re-run by the second pass -- gives bit-identical neighbour rows
+and FP64 forces equal up to summation order, and they match the oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import oracle as O
+from tests._common import FP64_RTOL, compare_pairs
+
+css = pytest.importorskip("paper_2404_19751_gb300")
+pytestmark = pytest.mark.gpu
+
+BASE = dict(warps_per_cta=4, ctas_per_sm=0, tile=1, shared_scale=1, window_capacity=2048,
+            window_capacity2=16384, warps2_per_sm=2)
+
+SHAPES = [
+    dict(),
+    dict(shared_scale=0),
+    dict(shared_scale=2, warps_per_cta=2),
+    dict(shared_scale=4, warps_per_cta=2, ctas_per_sm=1),
+    dict(warps_per_cta=1, tile=4),
+    dict(warps_per_cta=8, tile=16),
+    dict(window_capacity=64, window_capacity2=128),        # nearly every source deferred
+    dict(shared_scale=1, window_capacity=256, warps2_per_sm=1),
+]
+
+
+@pytest.fixture(scope="module")
+def case():
+    m = synth.icosphere(4, 1.0, noise=0.015, seed=4)
+    face, bary = synth.place_uniform(m, 1500, 6)
+    r_c = 0.3
+    pot = dict(kind=css.POT_HARMONIC, eps=1.0, sigma=r_c, r_cut=r_c)
+    om = O.OracleMesh(m)
+    F0, E0 = om.forces(face, bary, r_c, pot)
+    rows = om.neighbors_gap(face, bary, r_c)
+    return m, face, bary, r_c, pot, F0, E0, rows
+
+
+def test_results_do_not_depend_on_launch_shape(case):
+    m, face, bary, r_c, pot, F0, E0, rows = case
+    ctx = css.create(0)
+    mesh = css.mesh_upload(ctx, m.verts, m.faces)
+    parts = css.particles_set(ctx, mesh, face, bary)
+    ref = None
+    deferred = []
+    for sh in SHAPES:
+        ctx.set_launch(**dict(BASE, **sh))
+        F, E = css.compute_forces(parts, pot, r_c, css.FP64)
+        deferred.append(ctx.last_counters()["deferred"])
+        assert ctx.last_counters()["sources"] == len(face)
+        assert np.max(np.abs(F - F0)) <= FP64_RTOL * np.max(np.abs(F0)), sh
+        assert E == pytest.approx(E0, rel=1e-10)
+        g = css.geodesic_neighbors(parts, r_c, css.FP64)
+        compare_pairs(g, rows, r_c, FP64_RTOL, 1e-7)
+        if ref is None:
+            ref = (F, g)
+        else:
+            # each pair's distance and tangent is the same computation in every shape; only the
+            # order of a row's force sum may differ (which lane claims a face first)
+            assert np.max(np.abs(F - ref[0])) <= 1e-13 * np.max(np.abs(F0)), sh
+            assert np.array_equal(g[0], ref[1][0]) and np.array_equal(g[1], ref[1][1])
+            assert np.array_equal(g[2], ref[1][2])
+    assert deferred[0] == 0 and deferred[6] > len(face) // 2   # the tiny pool defers most sources
+    parts.free()
+    mesh.free()
+    ctx.close()
+
+
+def test_launch_shape_validation():
+    ctx = css.create(0)
+    for bad in (dict(warps_per_cta=0), dict(warps_per_cta=9), dict(shared_scale=3), dict(tile=0),
+                dict(window_capacity=10), dict(warps2_per_sm=0), dict(shared_scale=8, warps_per_cta=8)):
+        with pytest.raises(css.CssError):
+            ctx.set_launch(**dict(BASE, **bad))
+    assert ctx.get_launch() == dict(BASE)    # a rejected shape leaves the old one
+    ctx.close()
+
+
+def test_autotuner_keeps_results_and_state(case):
+    m, face, bary, r_c, pot, F0, E0, rows = case
+    ctx = css.create(0)
+    mesh = css.mesh_upload(ctx, m.verts, m.faces)
+    parts = css.particles_set(ctx, mesh, face, bary)
+    before = css.particles_get(parts)
+    shape, ms = ctx.autotune([parts], pot, r_c, css.FP32, reps=1, sample=600)
+    assert ms > 0 and shape == ctx.get_launch()
+    after = css.particles_get(parts)
+    assert np.array_equal(before["face"], after["face"]) and np.array_equal(before["bary"], after["bary"])
+    F, E = css.compute_forces(parts, pot, r_c, css.FP64)
+    assert np.max(np.abs(F - F0)) <= FP64_RTOL * np.max(np.abs(F0))
+    parts.free()
+    mesh.free()
+    ctx.close()
