@@ -791,10 +791,9 @@ __device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R>& ws, Wa
         npc.n = 0; lost.n = 0;
 #pragma unroll
         for (int k = 0; k < MAXP; ++k) { npc.a[k] = npc.b[k] = lost.a[k] = lost.b[k] = (R)0; }
-#pragma unroll
-        for (int p = 0; p < MAXP; ++p) {
-            if (p >= pc.n) break;
-            const R a0 = pc.a[p], a1 = pc.b[p];
+#pragma unroll 1
+        for (int p = 0; p < pc.n; ++p) {      // one copy of the comparison code (instruction cache)
+            const R a0 = ivl_get<R>(pc.a, p), a1 = ivl_get<R>(pc.b, p);
             const R lo = a0 > o0 ? a0 : o0, hi = a1 < o1 ? a1 : o1;
             if (!(hi - lo > tolw)) { ivl_add<R>(npc, a0, a1); continue; }
             int cmp = CMP_SPLIT;
@@ -931,7 +930,7 @@ __device__ __forceinline__ int group_rounds(bool has, int key, int lane, int& ra
 }
 
 template <class R>
-__device__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, const VCand<R>& c, double rc,
+__device__ __noinline__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, const VCand<R>& c, double rc,
                              int lane) {
     if (!__any_sync(CSS_FULL, has)) return;
     bool claimed = false;
@@ -973,7 +972,8 @@ __device__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, co
 }
 
 template <class R>
-__device__ void child_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, const Win<R>& c, double rc, int lane) {
+__device__ __noinline__ void child_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, const Win<R>& c, double rc,
+                                         int lane) {
     if (!__any_sync(CSS_FULL, has)) return;
     bool claimed = false;
     int slot = -1;
@@ -998,7 +998,7 @@ __device__ void child_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, con
 // d(v) <= kmin (the smallest queued key) go now and the others wait.  Returns the number
 // of vertices emitted.
 template <class R>
-__device__ int emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, double kmin, int lane) {
+__device__ __noinline__ int emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, double kmin, int lane) {
     __syncwarp();
     const int ne = min(sm.nemit, ws.emcap);
     if (ne == 0) return 0;
@@ -1033,12 +1033,33 @@ __device__ int emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, doub
             rs = m.ring_start[vid];
             len = m.ring_start[vid + 1] - rs;
         }
-        const int maxlen = (int)__reduce_max_sync(CSS_FULL, (unsigned)len);
-        for (int q = 0; q < maxlen; ++q) {
-            bool hh = q < len;
+        // one window per (emitting vertex, opposite edge), 32 at a time: lane t takes the
+        // t-th pair of the flattened list (owner = the vertex whose ring holds it)
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(CSS_FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(CSS_FULL, incl, 31);
+        for (int tb = 0; tb < total; tb += 32) {
+            const int t = tb + lane;
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int v = __shfl_sync(CSS_FULL, incl, owner + step - 1);
+                if (v <= t) owner += step;
+            }
+            owner = min(owner, 31);
+            const int o_rs = __shfl_sync(CSS_FULL, rs, owner);
+            const int o_ex = __shfl_sync(CSS_FULL, incl - len, owner);
+            const double o_dv = __shfl_sync(CSS_FULL, dv, owner);
+            const R o_tx = __shfl_sync(CSS_FULL, tx, owner);
+            const R o_ty = __shfl_sync(CSS_FULL, ty, owner);
+            bool hh = t < total;
             Win<R> c;
             if (hh) {
-                const int hc = m.ring[rs + q];
+                const int hc = m.ring[o_rs + (t - o_ex)];
                 const int f = hc / 3, k = hc - 3 * f;
                 const int hop = 3 * f + (k == 2 ? 0 : k + 1);
                 face_add(ws, sm, f);
@@ -1051,10 +1072,10 @@ __device__ int emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, doub
                     c.b1 = (R)r.L;
                     c.sx = r.L - r.cx;
                     c.sy = -r.cy;
-                    c.sig = dv;
+                    c.sig = o_dv;
                     set_fast(c);
-                    c.ta = tx;
-                    c.tb = ty;
+                    c.ta = o_tx;
+                    c.tb = o_ty;
                     c.flags = WIN_FIXED | WIN_ALIVE;
                     c.next = -1;
                 }
@@ -1347,10 +1368,12 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
         if (act) propagate<R>(m, w, rc, vc, nvc, ch, nch);
         n_prop += __popc(__ballot_sync(CSS_FULL, act));
         __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 3; ++q) vertex_round<R>(m, ws, sm, q < nvc, vc[q], rc, lane);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) child_round<R>(m, ws, sm, q < nch, ch[q], rc, lane);
+        // one call site per round kind keeps the kernel's instruction footprint small
+        // (divergent insertion code otherwise thrashes the instruction cache)
+#pragma unroll 1
+        for (int q = 0; q < 3; ++q) vertex_round<R>(m, ws, sm, q < nvc, q == 0 ? vc[0] : (q == 1 ? vc[1] : vc[2]), rc, lane);
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) child_round<R>(m, ws, sm, q < nch, q == 0 ? ch[0] : ch[1], rc, lane);
     }
     __syncwarp();
     const int err = sm.err;
