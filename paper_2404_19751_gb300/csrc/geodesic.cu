@@ -809,62 +809,54 @@ __device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R>& ws, Wa
             // equal sigma: the exact bisector split below is cheaper than any FP32 attempt
             if (cmp == CMP_EXISTING) { ivl_add<R>(npc, a0, lo); ivl_add<R>(npc, hi, a1); continue; }
             if (cmp == CMP_CANDIDATE) { ivl_add<R>(npc, a0, a1); ivl_add<R>(lost, lo, hi, false); continue; }
+            // split of the overlap at the equal-distance points: FP32 with rigorous margins
+            // where it can decide, else exact
+            R bq[4];
+            bool cw[3];
+            int npz = 0;
+            bool done32 = false;
             if (sizeof(R) == sizeof(float) && !eq_sig) {
                 float bpf[4];
-                bool cw[3];
-                int npz = 0;
-                if (split_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi, bpf, cw, npz)) {
-                    ivl_add<R>(npc, a0, lo);
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        if (q >= npz) break;
-                        if (cw[q]) {
-                            ivl_add<R>(npc, (R)bpf[q], (R)bpf[q + 1]);
-                            ivl_add<R>(lost, (R)bpf[q], (R)bpf[q + 1], false);
-                        }
-                    }
-                    ivl_add<R>(npc, hi, a1);
-                    continue;
-                }
+                done32 = split_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi, bpf, cw, npz);
+                if (done32) { bq[0] = (R)bpf[0]; bq[1] = (R)bpf[1]; bq[2] = (R)bpf[2]; bq[3] = (R)bpf[3]; }
             }
-            // exact split of the overlap at the equal-distance points
-            {
+            if (!done32) {
                 const double osx = same ? o.sx : Ld - o.sx, osy = same ? o.sy : -o.sy;
                 double bp[4];
-                bool cw[3];
-                const int npz = split_exact(c.sx, c.sy, c.sig, osx, osy, o.sig, (double)lo, (double)hi,
-                                            c_direct && (o.flags & WIN_FIXED), bp, cw);
-                ivl_add<R>(npc, a0, lo);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    if (q >= npz) break;
-                    if (cw[q]) {
-                        ivl_add<R>(npc, (R)bp[q], (R)bp[q + 1]);
-                        ivl_add<R>(lost, (R)bp[q], (R)bp[q + 1], false);
-                    }
-                }
+                npz = split_exact(c.sx, c.sy, c.sig, osx, osy, o.sig, (double)lo, (double)hi,
+                                  c_direct && (o.flags & WIN_FIXED), bp, cw);
+                bq[0] = (R)bp[0]; bq[1] = (R)bp[1]; bq[2] = (R)bp[2]; bq[3] = (R)bp[3];
             }
+            ivl_add<R>(npc, a0, lo);
+#pragma unroll 1
+            for (int q = 0; q < npz; ++q)
+                if (cw[q]) {
+                    ivl_add<R>(npc, bq[q], bq[q + 1]);
+                    ivl_add<R>(lost, bq[q], bq[q + 1], false);
+                }
             ivl_add<R>(npc, hi, a1);
         }
         pc.n = 0;
-#pragma unroll
-        for (int p = 0; p < MAXP; ++p)
-            if (p < npc.n && npc.b[p] - npc.a[p] > tolw) {
-                ivl_set<R>(pc.a, pc.n, npc.a[p]);
-                ivl_set<R>(pc.b, pc.n, npc.b[p]);
+#pragma unroll 1
+        for (int p = 0; p < npc.n; ++p) {
+            const R x0 = ivl_get<R>(npc.a, p), x1 = ivl_get<R>(npc.b, p);
+            if (x1 - x0 > tolw) {
+                ivl_set<R>(pc.a, pc.n, x0);
+                ivl_set<R>(pc.b, pc.n, x1);
                 ++pc.n;
             }
+        }
         if (lost.n > 0) {
             Ivl<R> keep;
             keep.n = 0;
 #pragma unroll
             for (int k = 0; k < MAXP; ++k) { keep.a[k] = keep.b[k] = (R)0; }
             R cur = o0;
-#pragma unroll
-            for (int q = 0; q < MAXP; ++q) {
-                if (q >= lost.n) break;
-                if (lost.a[q] - cur > tolw) ivl_add<R>(keep, cur, lost.a[q]);
-                if (lost.b[q] > cur) cur = lost.b[q];
+#pragma unroll 1
+            for (int q = 0; q < lost.n; ++q) {
+                const R l0 = ivl_get<R>(lost.a, q), l1 = ivl_get<R>(lost.b, q);
+                if (l0 - cur > tolw) ivl_add<R>(keep, cur, l0);
+                if (l1 > cur) cur = l1;
             }
             if (o1 - cur > tolw) ivl_add<R>(keep, cur, o1);
             if (keep.n == 0) {
@@ -875,11 +867,11 @@ __device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R>& ws, Wa
             }
             int tail = oi;
             const R wpad = (R)Widen<R>::mu * Lr;   // outward rounding of the kept parts
-#pragma unroll
-            for (int q = 0; q < MAXP; ++q) {
-                if (q >= keep.n) break;
-                R k0 = (same ? keep.a[q] : Lr - keep.b[q]) - wpad;
-                R k1 = (same ? keep.b[q] : Lr - keep.a[q]) + wpad;
+#pragma unroll 1
+            for (int q = 0; q < keep.n; ++q) {
+                const R ka = ivl_get<R>(keep.a, q), kb = ivl_get<R>(keep.b, q);
+                R k0 = (same ? ka : Lr - kb) - wpad;
+                R k1 = (same ? kb : Lr - ka) + wpad;
                 k0 = k0 < (R)0 ? (R)0 : k0;
                 k1 = k1 > Lr ? Lr : k1;
                 if (q == 0) { ws.win[oi].b0 = k0; ws.win[oi].b1 = k1; }
@@ -903,11 +895,11 @@ __device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R>& ws, Wa
     }
     if (err) atomicOr(&sm.err, err);
     bool added = false;
-#pragma unroll
-    for (int p = 0; p < MAXP; ++p) {
-        if (p >= pc.n) break;
+#pragma unroll 1
+    for (int p = 0; p < pc.n; ++p) {
         Win<R> w = c;
-        w.b0 = pc.a[p]; w.b1 = pc.b[p];
+        w.b0 = ivl_get<R>(pc.a, p);
+        w.b1 = ivl_get<R>(pc.b, p);
         w.flags = (c.flags & WIN_FIXED) | WIN_ALIVE;
         if (!((double)win_key<R>(w) < rc)) continue;
         const int id = win_alloc<R>(sm, ws.wcap);
