@@ -966,10 +966,12 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
         c->cfg.win_cap2 = std::max(c->cfg.win_cap2, pick.win_cap2);
         double t = 0.0;
         int rc = tune_run(c, djobs, jobs[0], dj, ds, nitems, precision, &t);   // untimed: layout, warm caches
-        double m = INFINITY;
-        for (int r = 0; r < reps && rc == CSS_OK; ++r) {
+        double m = INFINITY, tot = 0.0;
+        // at least `reps` runs, and short launches repeated until ~5 ms were timed (noise)
+        for (int r = 0; rc == CSS_OK && (r < reps || (tot < 5.0 && r < 64)); ++r) {
             rc = tune_run(c, djobs, jobs[0], dj, ds, nitems, precision, &t);
             m = std::min(m, t);
+            tot += t;
         }
         *out = m;
         return rc;
