@@ -398,7 +398,7 @@ def run_single(args, cfg, css, ctx, torch, stream, timer, rank, world):
         "pairs_per_step": r32["pairs"] / k32,
         "fp64": {"value": world * r64["pairs"] / t64, "unit": UNIT, "md_steps_per_s": world * k64 / t64,
                  "ms_per_step": 1e3 * t64 / k64, "kernel_ms": statistics.mean(r64["kernel_ms"]),
-                 "clocks": r64["clocks"]},
+                 "clocks": r64["clocks"], "launch": r64["launch"]},
         "fp32_over_fp64": (r32["pairs"] / t32) / (r64["pairs"] / t64),
         "accuracy_vs_oracle": acc,
         "roofline": roof,
