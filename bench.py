@@ -38,6 +38,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FLOPS_PER_PROPAGATION = 150.0   # one window unfolding + child trimming (FP arithmetic)
 FLOPS_PER_PAIR = 20.0           # one target evaluation
 BYTES_PER_FACE = 64.0           # patch mesh data a source must read per face reached
+# DRAM bytes (read + write) of one first-pass launch of the FP32 neighbour kernel, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernel on the
+# icosphere workload; other workloads were not captured at full size
+TRAFFIC_BYTES = {"ico5_n1024": 12.225e6 + 2.223e6}
 
 
 def parse():
@@ -273,7 +277,7 @@ def accuracy(css, ctx, cases):
     return acc
 
 
-def roofline(css, ctx, pk, props_per_src, n, pairs_per_launch, kern_s, kernel_name):
+def roofline(css, ctx, pk, props_per_src, n, pairs_per_launch, kern_s, kernel_name, traffic=None):
     fp32_peak_nominal = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     alg_flops = n * props_per_src * FLOPS_PER_PROPAGATION + pairs_per_launch * FLOPS_PER_PAIR
     achieved = alg_flops / kern_s
@@ -281,7 +285,7 @@ def roofline(css, ctx, pk, props_per_src, n, pairs_per_launch, kern_s, kernel_na
     alg_bytes = n * faces_per_src * BYTES_PER_FACE + pairs_per_launch * 24.0
     hbm = float(pk.get("hbm_gbs", 6800.0)) * 1e9
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak_nominal / 1e12,
-            "unit": "TFLOP/s", "frac": achieved / fp32_peak_nominal, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak_nominal, "traffic": traffic,
             "kernel": kernel_name, "kernel_ms": kern_s * 1e3,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
             "fma_probe_tflops": {"fp32": ctx.fma_peak(css.FP32) / 1e12, "fp64": ctx.fma_peak(css.FP64) / 1e12},
@@ -388,7 +392,8 @@ def run_single(args, cfg, css, ctx, torch, stream, timer, rank, world):
     else:
         props_per_src = r32["props"] / max(1, k32 * n)
     roof, mem = roofline(css, ctx, pk, props_per_src, n, r32["pairs"] / k32,
-                         statistics.mean(r32["kernel_ms"]) / 1e3, "k_geodesic<float>")
+                         statistics.mean(r32["kernel_ms"]) / 1e3, "k_geodesic<float>",
+                         traffic=TRAFFIC_BYTES.get(cfg["name"]))
     line = {
         "metric": METRIC, "value": world * r32["pairs"] / t32, "unit": UNIT, "n_gpus": world, "steps": k32,
         "warmup": args.warmup, "ms_per_step": 1e3 * t32 / k32, "higher_is_better": True, "scaling": "weak",
