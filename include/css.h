@@ -242,9 +242,9 @@ int css_get_launch(const css_ctx* ctx, css_launch* launch);
 
 /* Autotuner: times the force evaluation of the given sets (one persistent launch over
  * all their sources, as the batched form runs it) under candidate launch shapes --
- * shared_scale x warps_per_cta x ctas_per_sm, with a first-pass pool of the context's
- * window_capacity times the scale (4 times for global tables), then the tile on the
- * best -- and keeps
+ * shared_scale x warps_per_cta x ctas_per_sm, with a first-pass pool of 2048 windows
+ * times the scale (8192 for global tables), and four times that pool where more than 1 %
+ * of the sources were deferred, then the tile on the best -- and keeps
  * the fastest in the context.  Each candidate runs `reps` times (>= 1) after one
  * untimed run; `sample` > 0 restricts every run to about that many sources spread over
  * the sets (0: all).  best (may be NULL) receives the chosen shape and best_ms its

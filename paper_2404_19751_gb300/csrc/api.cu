@@ -959,6 +959,7 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
     if (e != cudaSuccess) { cleanup(); return cuda_fail(c, "autotune", e); }
     const int32_t nitems = (int32_t)hj.size();
     const cssi::LaunchCfg base = c->cfg;
+    constexpr int POOL_UNIT = 2048;   // first-pass windows per warp at table scale 1
     cssi::LaunchCfg pick = base;
     double pick_ms = INFINITY;
     auto measure = [&](const cssi::LaunchCfg& L, double* out) -> int {
@@ -985,7 +986,7 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
                 if (cps == 1 && bps == 1) continue;   // same shape as "as many as fit"
                 cssi::LaunchCfg L = base;
                 L.shared_scale = s;
-                L.win_cap = base.win_cap * (s ? s : 4);   // the pool grows with the patch the tables hold
+                L.win_cap = POOL_UNIT * (s ? s : 4);   // the pool grows with the patch the tables hold
                 L.warps_per_cta = wpc;
                 L.ctas_per_sm = cps;
                 L.tile = 1;
@@ -993,6 +994,13 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
                 rc = measure(L, &t);
                 if (rc) break;
                 if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
+                // sources deferred for want of pool run twice: try a pool four times larger
+                if (c->last_counters[4] * 100 > nitems && L.win_cap * 4 <= (1 << 20)) {
+                    L.win_cap *= 4;
+                    rc = measure(L, &t);
+                    if (rc) break;
+                    if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
+                }
             }
             if (rc) break;
         }
