@@ -231,11 +231,14 @@ int css_fma_peak(css_ctx* ctx, int precision, double* flops_per_s);
  *   window_capacity    first-pass windows per warp, 64..2^20 (rounded up to 2^k)
  *   window_capacity2   second-pass windows per warp (grown on overflow)
  *   warps2_per_sm      second-pass warps per SM, 1..8
+ *   occupancy          first-pass register budget: 1 = up to 255 registers a thread (at
+ *                      most 8 resident warps per SM, no spills), 2 = at most 128 (twice
+ *                      the resident warps, some spills to local memory)
  * css_set_launch fails with CSS_ERR_INVALID_ARG when a value is out of range or the
  * shape's shared memory does not fit an SM. */
 typedef struct css_launch {
     int32_t warps_per_cta, ctas_per_sm, tile, shared_scale;
-    int32_t window_capacity, window_capacity2, warps2_per_sm;
+    int32_t window_capacity, window_capacity2, warps2_per_sm, occupancy;
 } css_launch;
 int css_set_launch(css_ctx* ctx, const css_launch* launch);
 int css_get_launch(const css_ctx* ctx, css_launch* launch);
@@ -244,7 +247,9 @@ int css_get_launch(const css_ctx* ctx, css_launch* launch);
  * all their sources, as the batched form runs it) under candidate launch shapes --
  * shared_scale x warps_per_cta x ctas_per_sm, with a first-pass pool of 2048 windows
  * times the scale (8192 for global tables), and four times that pool where more than 1 %
- * of the sources were deferred, then the tile on the best -- and keeps
+ * of the sources were deferred, then occupancy 2 with 4 or 8 warps per CTA (global tables
+ * with pools of 8192 and 32768 windows, and the best pick's tables), then the tile on the
+ * best -- and keeps
  * the fastest in the context.  Each candidate runs `reps` times (>= 1) after one
  * untimed run; `sample` > 0 restricts every run to about that many sources spread over
  * the sets (0: all).  best (may be NULL) receives the chosen shape and best_ms its

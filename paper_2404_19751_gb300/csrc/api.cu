@@ -111,7 +111,7 @@ int ensure_buf(css_ctx* c, cssi::WsBuf& b, int precision, int win_cap, int share
 // both passes for the context's launch shape and up to `nitems` work items
 int ensure_plan(css_ctx* c, int precision, int64_t nitems, GeoPlan* P) {
     const cssi::LaunchCfg& L = c->cfg;
-    int bps = cssi::geodesic_blocks_per_sm(precision, L.warps_per_cta, L.shared_scale);
+    int bps = cssi::geodesic_blocks_per_sm(precision, L.warps_per_cta, L.shared_scale, L.occupancy);
     if (bps < 1) {
         c->err = "launch shape does not fit an SM (" + std::to_string(L.warps_per_cta) + " warps per CTA, shared scale " +
                  std::to_string(L.shared_scale) + ")";
@@ -122,10 +122,12 @@ int ensure_plan(css_ctx* c, int precision, int64_t nitems, GeoPlan* P) {
     P->nctas1 = c->sm_count * bps;
     int rc = ensure_buf(c, c->ws1, precision, L.win_cap, L.shared_scale, P->nctas1 * P->wpc1, &P->g1);
     if (rc) return rc;
+    P->g1.occupancy = L.occupancy;
     P->wpc2 = L.warps2_per_sm;
     P->nctas2 = c->sm_count;
     rc = ensure_buf(c, c->ws2, precision, L.win_cap2, 0, P->nctas2 * P->wpc2, &P->g2);
     if (rc) return rc;
+    P->g2.occupancy = 1;
     if (c->defer_cap < nitems) {
         cudaFree(c->defer);
         c->defer = nullptr;
@@ -139,7 +141,7 @@ int ensure_plan(css_ctx* c, int precision, int64_t nitems, GeoPlan* P) {
 // the plan's identity, for keying captured graphs
 std::string plan_key(const css_ctx* c, const GeoPlan& P) {
     const int64_t v[8] = {c->ws1.key, c->ws2.key, (int64_t)(uintptr_t)c->ws1.ws, (int64_t)(uintptr_t)c->ws2.ws,
-                          (int64_t)(uintptr_t)c->defer, P.nctas1, c->cfg.tile, P.nctas2};
+                          (int64_t)(uintptr_t)c->defer, P.nctas1, c->cfg.tile * 8 + c->cfg.occupancy, P.nctas2};
     return std::string((const char*)v, sizeof(v));
 }
 
@@ -370,13 +372,14 @@ static bool launch_ok(const css_launch* l) {
     return l->warps_per_cta >= 1 && l->warps_per_cta <= 8 && l->ctas_per_sm >= 0 && l->ctas_per_sm <= 32 &&
            l->tile >= 1 && l->tile <= 64 && (s == 0 || s == 1 || s == 2 || s == 4 || s == 8) &&
            l->window_capacity >= 64 && l->window_capacity <= (1 << 20) && l->window_capacity2 >= 64 &&
-           l->window_capacity2 <= (1 << 20) && l->warps2_per_sm >= 1 && l->warps2_per_sm <= 8;
+           l->window_capacity2 <= (1 << 20) && l->warps2_per_sm >= 1 && l->warps2_per_sm <= 8 &&
+           (l->occupancy == 1 || l->occupancy == 2);
 }
 
 int css_set_launch(css_ctx* c, const css_launch* l) {
     if (!c || !l || !launch_ok(l)) return CSS_ERR_INVALID_ARG;
     for (int prec : {CSS_FP32, CSS_FP64})
-        if (cssi::geodesic_blocks_per_sm(prec, l->warps_per_cta, l->shared_scale) < 1) {
+        if (cssi::geodesic_blocks_per_sm(prec, l->warps_per_cta, l->shared_scale, l->occupancy) < 1) {
             c->err = "launch shape does not fit an SM";
             return CSS_ERR_INVALID_ARG;
         }
@@ -387,6 +390,7 @@ int css_set_launch(css_ctx* c, const css_launch* l) {
     c->cfg.win_cap = next_pow2(l->window_capacity);
     c->cfg.win_cap2 = next_pow2(l->window_capacity2);
     c->cfg.warps2_per_sm = l->warps2_per_sm;
+    c->cfg.occupancy = l->occupancy;
     return CSS_OK;
 }
 
@@ -399,6 +403,7 @@ int css_get_launch(const css_ctx* c, css_launch* l) {
     l->window_capacity = c->cfg.win_cap;
     l->window_capacity2 = c->cfg.win_cap2;
     l->warps2_per_sm = c->cfg.warps2_per_sm;
+    l->occupancy = c->cfg.occupancy;
     return CSS_OK;
 }
 
@@ -980,11 +985,12 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
     int rc = CSS_OK;
     for (int s : {1, 2, 4, 0}) {
         for (int wpc : {2, 4, 8}) {
-            const int bps = cssi::geodesic_blocks_per_sm(precision, wpc, s);
+            const int bps = cssi::geodesic_blocks_per_sm(precision, wpc, s, 1);
             if (bps < 1) continue;
             for (int cps : {0, 1}) {
                 if (cps == 1 && bps == 1) continue;   // same shape as "as many as fit"
                 cssi::LaunchCfg L = base;
+                L.occupancy = 1;
                 L.shared_scale = s;
                 L.win_cap = POOL_UNIT * (s ? s : 4);   // the pool grows with the patch the tables hold
                 L.warps_per_cta = wpc;
@@ -1005,6 +1011,28 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
             if (rc) break;
         }
         if (rc) break;
+    }
+    // the register-light variant (twice the resident warps, some spills): with global tables
+    // (shared tables leave no room for 16 warps per SM) and with the best pick's tables
+    for (int variant = 0; variant < 3 && rc == CSS_OK; ++variant) {
+        cssi::LaunchCfg T = pick;
+        if (variant < 2) {
+            T.shared_scale = 0;
+            T.win_cap = POOL_UNIT * 4 * (variant == 1 ? 4 : 1);
+            if (variant == 1 && T.win_cap <= pick.win_cap && pick.shared_scale == 0) continue;
+        } else if (pick.shared_scale == 0) continue;
+        for (int wpc : {4, 8}) {
+            cssi::LaunchCfg L = T;
+            L.occupancy = 2;
+            L.warps_per_cta = wpc;
+            L.ctas_per_sm = 0;
+            L.tile = 1;
+            if (cssi::geodesic_blocks_per_sm(precision, wpc, L.shared_scale, 2) < 1) continue;
+            double t = 0.0;
+            rc = measure(L, &t);
+            if (rc) break;
+            if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
+        }
     }
     for (int tile : {2, 4, 8}) {
         if (rc) break;

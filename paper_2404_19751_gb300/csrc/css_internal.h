@@ -22,6 +22,7 @@ struct LaunchCfg {
     int win_cap = 2048;
     int win_cap2 = 16384;
     int warps2_per_sm = 2;   // second pass: warps per SM (one CTA each)
+    int occupancy = 1;       // register budget of the first pass: 1 (255 regs) or 2 (128 regs)
 };
 // a second-pass workspace (global tables)
 struct WsBuf {
@@ -163,6 +164,7 @@ struct GeoWs {
     int wcap, fcap, emcap;
     uint32_t* gen;
     int nwarps;
+    int occupancy;           // kernel variant: 1 (255 registers a thread) or 2 (128)
 };
 
 // geodesic.cu
@@ -171,7 +173,7 @@ size_t geo_ws_bytes_per_warp(int precision, int win_cap, int* log_eh, int* log_v
 cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const GeoQueue& q, int precision,
                             const GeoWs& ws, int warps_per_cta, int nctas, int* work_counter,
                             int* status, unsigned long long* counters, cudaStream_t st);
-int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared_scale);
+int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared_scale, int occupancy);
 size_t geodesic_shared_bytes(int precision, int warps_per_cta, int shared_scale);
 cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd,
                                  const double* pt, int pair_cap, const int64_t* row_start,

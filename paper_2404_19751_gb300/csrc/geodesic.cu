@@ -1466,8 +1466,11 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
     __syncwarp();
 }
 
-template <class R>
-__global__ void __launch_bounds__(256) k_geodesic(cssi::GeoJob job0, const cssi::GeoJob* jobs, cssi::GeoQueue q,
+// OCC = CTAs of 256 threads per SM the register budget must allow: 1 gives up to 255
+// registers a thread (fewer resident warps, no spills), 2 caps them at 128 (twice the
+// resident warps, some spills); which is faster depends on the workload.
+template <class R, int OCC>
+__global__ void __launch_bounds__(256, OCC) k_geodesic(cssi::GeoJob job0, const cssi::GeoJob* jobs, cssi::GeoQueue q,
                                                   cssi::GeoWs g, int* work, int* status,
                                                   unsigned long long* counters) {
     __shared__ WarpSm smem[MAX_WARPS_CTA];
@@ -1560,38 +1563,44 @@ cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const GeoQu
                             unsigned long long* counters, cudaStream_t st) {
     const dim3 block(32 * warps_per_cta);
     const size_t sm = geodesic_shared_bytes(precision, warps_per_cta, ws.shared);
-    if (precision == CSS_FP32)
-        k_geodesic<float><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
-    else
-        k_geodesic<double><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
+    const bool light = ws.occupancy == 2;
+    if (precision == CSS_FP32) {
+        if (light) k_geodesic<float, 2><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
+        else k_geodesic<float, 1><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
+    } else {
+        if (light) k_geodesic<double, 2><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
+        else k_geodesic<double, 1><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
+    }
     return cudaGetLastError();
 }
 
 // resident CTAs per SM for a launch shape (0: the shape does not fit an SM)
-template <class R>
+template <class R, int OCC>
 static int blocks_per_sm(int warps_per_cta, size_t dyn) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_geodesic<R>) != cudaSuccess) { cudaGetLastError(); return 0; }
+    if (cudaFuncGetAttributes(&fa, k_geodesic<R, OCC>) != cudaSuccess) { cudaGetLastError(); return 0; }
     const int room = optin - (int)fa.sharedSizeBytes;   // dynamic shared memory a CTA may take
     if (dyn > (size_t)room) return 0;
-    if (cudaFuncSetAttribute(k_geodesic<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, room) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_geodesic<R, OCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, room) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<R>, 32 * warps_per_cta, dyn) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<R, OCC>, 32 * warps_per_cta, dyn) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return nb;
 }
 
-int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared_scale) {
+int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared_scale, int occupancy) {
     const size_t dyn = geodesic_shared_bytes(precision, warps_per_cta, shared_scale);
-    return precision == CSS_FP32 ? blocks_per_sm<float>(warps_per_cta, dyn) : blocks_per_sm<double>(warps_per_cta, dyn);
+    if (occupancy == 2)
+        return precision == CSS_FP32 ? blocks_per_sm<float, 2>(warps_per_cta, dyn) : blocks_per_sm<double, 2>(warps_per_cta, dyn);
+    return precision == CSS_FP32 ? blocks_per_sm<float, 1>(warps_per_cta, dyn) : blocks_per_sm<double, 1>(warps_per_cta, dyn);
 }
 
 cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd,

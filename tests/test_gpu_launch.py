@@ -17,7 +17,7 @@ css = pytest.importorskip("paper_2404_19751_gb300")
 pytestmark = pytest.mark.gpu
 
 BASE = dict(warps_per_cta=4, ctas_per_sm=0, tile=1, shared_scale=1, window_capacity=2048,
-            window_capacity2=16384, warps2_per_sm=2)
+            window_capacity2=16384, warps2_per_sm=2, occupancy=1)
 
 SHAPES = [
     dict(),
@@ -28,6 +28,8 @@ SHAPES = [
     dict(warps_per_cta=8, tile=16),
     dict(window_capacity=64, window_capacity2=128),        # nearly every source deferred
     dict(shared_scale=1, window_capacity=256, warps2_per_sm=1),
+    dict(occupancy=2, warps_per_cta=8),
+    dict(occupancy=2, shared_scale=0, window_capacity=8192, tile=2),
 ]
 
 
@@ -76,7 +78,8 @@ def test_results_do_not_depend_on_launch_shape(case):
 def test_launch_shape_validation():
     ctx = css.create(0)
     for bad in (dict(warps_per_cta=0), dict(warps_per_cta=9), dict(shared_scale=3), dict(tile=0),
-                dict(window_capacity=10), dict(warps2_per_sm=0), dict(shared_scale=8, warps_per_cta=8)):
+                dict(window_capacity=10), dict(warps2_per_sm=0), dict(shared_scale=8, warps_per_cta=8),
+                dict(occupancy=3)):
         with pytest.raises(css.CssError):
             ctx.set_launch(**dict(BASE, **bad))
     assert ctx.get_launch() == dict(BASE)    # a rejected shape leaves the old one
