@@ -756,6 +756,9 @@ struct css_batch {
     int32_t* job_of_item = nullptr;
     int32_t* src_of_item = nullptr;
     int32_t nitems = 0;
+    // the sets as the batched move / bucket kernels see them, and their particle offsets
+    cssi::SetView* dviews = nullptr;
+    int32_t* doffs = nullptr;
     // captured single step and the parameters it was captured for
     cudaGraphExec_t graph = nullptr;
     std::string graph_key;
@@ -784,7 +787,19 @@ int css_batch_create(css_ctx* c, css_parts* const* parts, int32_t n_sets, css_ba
     for (int k : ord)
         for (int64_t i = 0; i < b->sets[k]->n; ++i) { hj.push_back(k); hs.push_back((int32_t)i); }
     b->nitems = (int32_t)total;
+    std::vector<cssi::SetView> hv;
+    std::vector<int32_t> hoff(1, 0);
+    for (css_parts* p : b->sets) {
+        cssi::SetView v{};
+        v.m = p->mesh->view();
+        v.face = p->face; v.bary = p->bary; v.vel = p->vel; v.orient = p->orient; v.force = p->force;
+        v.fcnt = p->fcnt; v.fstart = p->fstart; v.fitems = p->fitems; v.dstep = p->dstep; v.seed = p->seed;
+        hv.push_back(v);
+        hoff.push_back(hoff.back() + (int32_t)p->n);
+    }
     cudaError_t e = cudaMalloc(&b->djobs, n_sets * sizeof(GeoJob));
+    if (e == cudaSuccess) e = stage_in(hv.data(), hv.size(), &b->dviews, c->stream);
+    if (e == cudaSuccess) e = stage_in(hoff.data(), hoff.size(), &b->doffs, c->stream);
     if (e == cudaSuccess) e = stage_in(hj.data(), hj.size(), &b->job_of_item, c->stream);
     if (e == cudaSuccess) e = stage_in(hs.data(), hs.size(), &b->src_of_item, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -796,6 +811,8 @@ int css_batch_create(css_ctx* c, css_parts* const* parts, int32_t n_sets, css_ba
 int css_batch_free(css_batch* b) {
     if (!b) return CSS_ERR_INVALID_ARG;
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->dviews);
+    cudaFree(b->doffs);
     cudaFree(b->djobs);
     cudaFree(b->job_of_item);
     cudaFree(b->src_of_item);
@@ -808,9 +825,7 @@ namespace {
 int batch_enqueue_forces(css_batch* b, const css_potential* pot, double rc, int prec, const GeoPlan& P) {
     css_ctx* c = b->ctx;
     cudaStream_t st = c->stream;
-    for (css_parts* p : b->sets)
-        TRY(c, "bucket", cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->mesh->frank, p->fcnt, p->fstart,
-                                             p->fitems, p->scan_tmp, st));
+    TRY(c, "bucket", cssi::launch_batch_bucket(b->dviews, b->doffs, (int)b->sets.size(), b->nitems, st));
     TRY(c, "reset", cudaMemsetAsync(c->depot, 0, sizeof(double), st));
     GeoJob j0 = make_job(b->sets[0], rc, 0, 1, pot);
     return enqueue_passes(c, j0, b->djobs, b->job_of_item, b->src_of_item, b->nitems, prec, P);
@@ -854,11 +869,13 @@ int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator*
             rc = batch_enqueue_forces(b, pot, r_c, precision, P);
             if (rc) return rc;
         }
+        // one step: every set moves in one launch, buckets in three, forces in the two passes
+        const int ns = (int)b->sets.size();
         auto one_step = [&]() -> int {
-            for (css_parts* p : b->sets) { int r = enqueue_move(p, it, nullptr, 0); if (r) return r; }
+            TRY(c, "move", cssi::launch_batch_move(b->dviews, b->doffs, ns, b->nitems, *it, 0, c->dscal + 1, st));
             int r = batch_enqueue_forces(b, pot, r_c, precision, P);
             if (r) return r;
-            for (css_parts* p : b->sets) { r = enqueue_move(p, it, nullptr, 1); if (r) return r; }
+            TRY(c, "move", cssi::launch_batch_move(b->dviews, b->doffs, ns, b->nitems, *it, 1, c->dscal + 1, st));
             return CSS_OK;
         };
         std::string key((const char*)pot, sizeof(*pot));

@@ -144,6 +144,21 @@ struct GeoJob {
     double* epot;
 };
 
+// one particle set as the batched move / bucket kernels see it
+struct SetView {
+    css::DMesh m;
+    int32_t* face;
+    double* bary;
+    double* vel;
+    double* orient;
+    double* force;
+    int32_t* fcnt;
+    int32_t* fstart;
+    int32_t* fitems;
+    int64_t* dstep;
+    uint64_t seed;
+};
+
 // where a launch takes its work items from
 struct GeoQueue {
     const int32_t* job_of_item;   // NULL: one job
@@ -198,6 +213,11 @@ cudaError_t launch_overdamped_move(const css::DMesh& m, int32_t n, int32_t* face
                                    uint64_t seed, const int64_t* dstep, const double* noise, int* status,
                                    cudaStream_t st);
 cudaError_t launch_step_inc(int64_t* dstep, cudaStream_t st);
+// batched forms over the sets of a batch: item k belongs to set s with offs[s] <= k < offs[s+1]
+// (offs has nsets + 1 entries on the device; total = offs[nsets])
+cudaError_t launch_batch_bucket(const SetView* sv, const int32_t* offs, int nsets, int64_t total, cudaStream_t st);
+cudaError_t launch_batch_move(const SetView* sv, const int32_t* offs, int nsets, int64_t total, css_integrator it,
+                              int half, int* status, cudaStream_t st);
 
 // peak.cu
 cudaError_t measure_fma_peak(int precision, int sm_count, cudaStream_t st, double* flops);

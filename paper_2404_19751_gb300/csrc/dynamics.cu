@@ -303,10 +303,9 @@ __device__ __forceinline__ void normal_pair(uint64_t seed, uint64_t particle, ui
 }
 
 // ------------------------------------------------------------------ integrators
-__global__ void k_nve_kick_drift(DMesh m, int32_t n, int32_t* face, double* bary, double* vel, const double* force,
-                                 css_integrator it, int* status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// first half kick and drift of particle i (velocity Verlet, Sec. 2.1)
+__device__ void kick_drift_one(const DMesh& m, int i, int32_t* face, double* bary, double* vel, const double* force,
+                               const css_integrator& it, int* status) {
     const double h = 0.5 * it.dt / it.mass;
     double v[3], d[3];
     for (int a = 0; a < 3; ++a) { v[a] = vel[3 * i + a] + h * force[3 * i + a]; d[a] = it.dt * v[a]; }
@@ -317,6 +316,11 @@ __global__ void k_nve_kick_drift(DMesh m, int32_t n, int32_t* face, double* bary
     face[i] = f;
     for (int a = 0; a < 3; ++a) { bary[3 * i + a] = b[a]; vel[3 * i + a] = v[a]; }
 }
+__global__ void k_nve_kick_drift(DMesh m, int32_t n, int32_t* face, double* bary, double* vel, const double* force,
+                                 css_integrator it, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) kick_drift_one(m, i, face, bary, vel, force, it, status);
+}
 
 __global__ void k_nve_kick(int32_t n, double* vel, const double* force, double h) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -324,10 +328,10 @@ __global__ void k_nve_kick(int32_t n, double* vel, const double* force, double h
     vel[i] += h * force[i];
 }
 
-__global__ void k_overdamped(DMesh m, int32_t n, int32_t* face, double* bary, double* orient, const double* force,
-                             css_integrator it, uint64_t seed, const int64_t* dstep, const double* noise, int* status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// overdamped (Brownian or active) move of particle i (Sec. 2.1)
+__device__ void overdamped_one(const DMesh& m, int i, int32_t* face, double* bary, double* orient, const double* force,
+                               const css_integrator& it, uint64_t seed, const int64_t* dstep, const double* noise,
+                               int* status) {
     double z0, z1;
     if (noise) { z0 = noise[2 * (size_t)i]; z1 = noise[2 * (size_t)i + 1]; }
     else normal_pair(seed, (uint64_t)i, (uint64_t)*dstep, z0, z1);
@@ -359,8 +363,98 @@ __global__ void k_overdamped(DMesh m, int32_t n, int32_t* face, double* bary, do
     face[i] = f;
     for (int a = 0; a < 3; ++a) bary[3 * i + a] = b[a];
 }
+__global__ void k_overdamped(DMesh m, int32_t n, int32_t* face, double* bary, double* orient, const double* force,
+                             css_integrator it, uint64_t seed, const int64_t* dstep, const double* noise, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) overdamped_one(m, i, face, bary, orient, force, it, seed, dstep, noise, status);
+}
 
 __global__ void k_step_inc(int64_t* dstep) { *dstep += 1; }
+
+// ------------------------------------------------------------------ many sets in one launch
+// Work item k of a batch belongs to the set s with offs[s] <= k < offs[s+1] (a handful of
+// bisection steps over the set offsets) and is that set's particle k - offs[s].
+__device__ __forceinline__ int set_of(const int32_t* offs, int nsets, int k) {
+    int lo = 0, hi = nsets;   // offs[lo] <= k < offs[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (offs[mid] <= k) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_batch_kick_drift(const cssi::SetView* sv, const int32_t* offs, int nsets, css_integrator it,
+                                   int* status) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= offs[nsets]) return;
+    const int s = set_of(offs, nsets, k);
+    const cssi::SetView& V = sv[s];
+    kick_drift_one(V.m, k - offs[s], V.face, V.bary, V.vel, V.force, it, status);
+}
+
+__global__ void k_batch_kick(const cssi::SetView* sv, const int32_t* offs, int nsets, double h) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= offs[nsets]) return;
+    const int s = set_of(offs, nsets, k);
+    const int i = k - offs[s];
+    double* v = sv[s].vel + 3 * (size_t)i;
+    const double* f = sv[s].force + 3 * (size_t)i;
+    v[0] += h * f[0];
+    v[1] += h * f[1];
+    v[2] += h * f[2];
+}
+
+__global__ void k_batch_overdamped(const cssi::SetView* sv, const int32_t* offs, int nsets, css_integrator it,
+                                   int* status) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= offs[nsets]) return;
+    const int s = set_of(offs, nsets, k);
+    const cssi::SetView& V = sv[s];
+    overdamped_one(V.m, k - offs[s], V.face, V.bary, V.orient, V.force, it, V.seed, V.dstep, nullptr, status);
+}
+
+__global__ void k_batch_step_inc(const cssi::SetView* sv, int nsets) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsets) *sv[s].dstep += 1;
+}
+
+__global__ void k_batch_count(const cssi::SetView* sv, const int32_t* offs, int nsets) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= offs[nsets]) return;
+    const int s = set_of(offs, nsets, k);
+    const cssi::SetView& V = sv[s];
+    const int f = V.face[k - offs[s]];
+    atomicAdd(V.fcnt + (V.m.frank ? V.m.frank[f] : f), 1);
+}
+
+// one block per set: exclusive scan of its nf + 1 face counts (the last count is zero)
+__global__ void __launch_bounds__(SCAN_THREADS) k_batch_scan(const cssi::SetView* sv) {
+    __shared__ int32_t sh[SCAN_THREADS / 32];
+    const cssi::SetView& V = sv[blockIdx.x];
+    const int64_t n = (int64_t)V.m.nf + 1;
+    int32_t carry = 0;
+    for (int64_t base = 0; base < n; base += SCAN_THREADS) {
+        const int64_t i = base + threadIdx.x;
+        const int32_t v = i < V.m.nf ? V.fcnt[i] : 0;
+        int32_t total = 0;
+        const int32_t ex = block_excl_scan<int32_t, int32_t>(v, sh, total);
+        if (i < n) V.fstart[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void k_batch_scatter(const cssi::SetView* sv, const int32_t* offs, int nsets) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= offs[nsets]) return;
+    const int s = set_of(offs, nsets, k);
+    const cssi::SetView& V = sv[s];
+    const int i = k - offs[s];
+    const int f = V.face[i];
+    const int key = V.m.frank ? V.m.frank[f] : f;
+    const int p = atomicSub(V.fcnt + key, 1) - 1;
+    V.fitems[V.fstart[key] + p] = i;
+}
+
 
 inline unsigned nb(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
 
@@ -421,5 +515,27 @@ cudaError_t launch_step_inc(int64_t* dstep, cudaStream_t st) {
     k_step_inc<<<1, 1, 0, st>>>(dstep);
     return cudaGetLastError();
 }
+
+cudaError_t launch_batch_bucket(const SetView* sv, const int32_t* offs, int nsets, int64_t total, cudaStream_t st) {
+    if (total < 1) return cudaSuccess;
+    k_batch_count<<<nb(total), 256, 0, st>>>(sv, offs, nsets);
+    k_batch_scan<<<nsets, SCAN_THREADS, 0, st>>>(sv);
+    k_batch_scatter<<<nb(total), 256, 0, st>>>(sv, offs, nsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_move(const SetView* sv, const int32_t* offs, int nsets, int64_t total, css_integrator it,
+                              int half, int* status, cudaStream_t st) {
+    if (total < 1) return cudaSuccess;
+    if (it.kind == CSS_INT_NVE) {
+        if (half == 0) k_batch_kick_drift<<<nb(total, 128), 128, 0, st>>>(sv, offs, nsets, it, status);
+        else k_batch_kick<<<nb(total), 256, 0, st>>>(sv, offs, nsets, 0.5 * it.dt / it.mass);
+    } else if (half == 1) {
+        k_batch_overdamped<<<nb(total, 128), 128, 0, st>>>(sv, offs, nsets, it, status);
+        k_batch_step_inc<<<nb(nsets), 256, 0, st>>>(sv, nsets);
+    }
+    return cudaGetLastError();
+}
+
 
 }  // namespace cssi
