@@ -111,7 +111,12 @@ int ensure_buf(css_ctx* c, cssi::WsBuf& b, int precision, int win_cap, int share
 // both passes for the context's launch shape and up to `nitems` work items
 int ensure_plan(css_ctx* c, int precision, int64_t nitems, GeoPlan* P) {
     const cssi::LaunchCfg& L = c->cfg;
-    int bps = cssi::geodesic_blocks_per_sm(precision, L.warps_per_cta, L.shared_scale, L.occupancy);
+    // the occupancy query costs host time on every call: cached per shape
+    const int64_t bkey = ((int64_t)precision * 64 + L.warps_per_cta) * 64 + L.shared_scale * 4 + L.occupancy;
+    auto hit = c->bps_cache.find(bkey);
+    int bps = hit != c->bps_cache.end() ? hit->second
+                                        : (c->bps_cache[bkey] = cssi::geodesic_blocks_per_sm(precision, L.warps_per_cta,
+                                                                                              L.shared_scale, L.occupancy));
     if (bps < 1) {
         c->err = "launch shape does not fit an SM (" + std::to_string(L.warps_per_cta) + " warps per CTA, shared scale " +
                  std::to_string(L.shared_scale) + ")";

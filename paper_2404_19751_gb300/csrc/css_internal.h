@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -43,6 +44,7 @@ struct css_ctx {
     // neighbour/force workspaces of the two passes (grown on demand)
     cssi::WsBuf ws1, ws2;
     cssi::LaunchCfg cfg;
+    std::map<int64_t, int> bps_cache;   // resident CTAs per SM by (precision, shape)
     int pair_cap = 64;               // pairs per source slab
     // deferral list of the first pass (one entry per work item at most)
     int32_t* defer = nullptr;
