@@ -101,3 +101,39 @@ def test_autotuner_keeps_results_and_state(case):
     parts.free()
     mesh.free()
     ctx.close()
+
+
+def test_autotuner_on_a_batch_then_batched_steps_match_single_sets():
+    """The tuner times one launch over all sets of a batch; the batched steps that follow
+    in the tuned shape equal the same sets stepped alone in the default shape."""
+    ctx = css.create(0)
+    pot = dict(kind=css.POT_HARMONIC, eps=1.0, sigma=0.1, r_cut=0.1)
+    integ = dict(kind=css.INT_NVE, dt=0.002, kT=0.1, lam=1.0, v0=0.0, Dr=0.0, mass=1.0, max_disp=float("inf"))
+    meshes, sets, states = [], [], []
+    for k in range(4):
+        m = synth.configs.torus_for_faces(2500 + 2000 * k, 2.0 + 0.2 * k, 0.4 + 0.1 * k)
+        face, bary = synth.place_uniform(m, 300 + 150 * k, 80 + k)
+        vel = synth.gaussian_tangent_velocities(m, face, 0.1, 1.0, 90 + k)
+        mesh = css.mesh_upload(ctx, m.verts, m.faces)
+        meshes.append(mesh)
+        sets.append(css.particles_set(ctx, mesh, face, bary, vel))
+        states.append((face, bary, vel))
+    ctx.set_launch(**BASE)
+    singles = [css.particles_set(ctx, mh, *st) for mh, st in zip(meshes, states)]
+    for p in singles:
+        css.integrate_step(p, pot, integ, 0.1, css.FP64, 4)
+    shape, ms = ctx.autotune(sets, pot, 0.1, css.FP64, reps=1, sample=500)
+    assert ms > 0 and shape == ctx.get_launch()
+    b = css.batch_create(ctx, sets)
+    css.batch_step(b, pot, integ, 0.1, css.FP64, 4)
+    for pb, ps in zip(sets, singles):
+        a, c = css.particles_get(pb), css.particles_get(ps)
+        assert np.array_equal(a["face"], c["face"])
+        np.testing.assert_allclose(a["bary"], c["bary"], atol=1e-12)
+        np.testing.assert_allclose(a["vel"], c["vel"], atol=1e-12)
+    b.free()
+    for p in sets + singles:
+        p.free()
+    for mh in meshes:
+        mh.free()
+    ctx.close()
