@@ -1097,6 +1097,16 @@ int om_integrate(const om_mesh* m, int64_t n, int32_t* face, double* bary, doubl
             if (rc) return rc;
             for (int64_t i = 0; i < n; ++i)
                 for (int a = 0; a < 3; ++a) vel[3 * i + a] += h * force[3 * i + a];
+        } else if (it->kind == 3) {
+            /* steepest descent (the relaxation of Fig. 3): dr = (dt / lambda) f, no noise */
+            rc = om_forces(m, n, face, bary, r_c, pot, force, epot, nthreads);
+            if (rc) return rc;
+            for (int64_t i = 0; i < n; ++i) {
+                double d[3];
+                for (int a = 0; a < 3; ++a) d[a] = it->dt / it->lam * force[3 * i + a];
+                clamp_disp(d, it->max_disp);
+                if (om_shift(m, face + i, bary + 3 * i, d, 0, NULL) < 0) return -6;
+            }
         } else {
             rc = om_forces(m, n, face, bary, r_c, pot, force, epot, nthreads);
             if (rc) return rc;
@@ -1131,4 +1141,52 @@ int om_integrate(const om_mesh* m, int64_t n, int32_t* face, double* bary, doubl
         }
     }
     return rc;
+}
+
+/* ------------------------------------------------------------------ FIRE minimiser
+ * Fast inertial relaxation (Bitzek et al., PRL 97, 170201, 2006) on the surface: each step
+ * (1) P = sum_i f_i . v_i; (2) v_i <- (1 - alpha) v_i + alpha |v| f_i / |f| with the norms of
+ * the whole system's vectors; (3) if P > 0 count it, and after more than N_min such steps
+ * in a row grow dt (x f_inc, at most dt_max) and shrink alpha (x f_alpha); (4) if P <= 0
+ * halve dt, set v = 0, alpha = alpha_start and restart the count; then one velocity-Verlet
+ * step with the current dt (drift = face walk carrying v). Forces must hold the forces at
+ * the current positions on entry and hold them at the final positions on exit.
+ * state[3] = {dt, alpha, steps with P > 0} in/out. */
+int om_fire(const om_mesh* m, int64_t n, int32_t* face, double* bary, double* vel, double* force,
+            const om_potential* pot, const om_integrator* it, double r_c, int64_t nsteps, double* state,
+            double* epot, int nthreads) {
+    const double alpha0 = OM_FIRE_ALPHA0, f_inc = OM_FIRE_FINC, f_dec = OM_FIRE_FDEC, f_alpha = OM_FIRE_FALPHA;
+    const double dt_max = OM_FIRE_DTMAX * it->dt;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        double P = 0.0, vv = 0.0, ff = 0.0;
+        for (int64_t i = 0; i < 3 * n; ++i) { P += force[i] * vel[i]; vv += vel[i] * vel[i]; ff += force[i] * force[i]; }
+        const double alpha = state[1];
+        if (ff > 0.0) {
+            const double c = alpha * sqrt(vv) / sqrt(ff);
+            for (int64_t i = 0; i < 3 * n; ++i) vel[i] = (1.0 - alpha) * vel[i] + c * force[i];
+        }
+        if (P > 0.0) {
+            state[2] += 1.0;
+            if (state[2] > OM_FIRE_NMIN) {
+                state[0] = fmin(state[0] * f_inc, dt_max);
+                state[1] = alpha * f_alpha;
+            }
+        } else {
+            state[2] = 0.0;
+            state[0] *= f_dec;
+            state[1] = alpha0;
+            for (int64_t i = 0; i < 3 * n; ++i) vel[i] = 0.0;
+        }
+        const double dt = state[0], h = 0.5 * dt / it->mass;
+        for (int64_t i = 0; i < n; ++i) {
+            double d[3];
+            for (int a = 0; a < 3; ++a) { vel[3 * i + a] += h * force[3 * i + a]; d[a] = dt * vel[3 * i + a]; }
+            clamp_disp(d, it->max_disp);
+            if (om_shift(m, face + i, bary + 3 * i, d, 1, vel + 3 * i) < 0) return -6;
+        }
+        const int rc = om_forces(m, n, face, bary, r_c, pot, force, epot, nthreads);
+        if (rc) return rc;
+        for (int64_t i = 0; i < 3 * n; ++i) vel[i] += h * force[i];
+    }
+    return 0;
 }

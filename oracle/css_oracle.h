@@ -40,7 +40,15 @@ typedef struct {
 } om_stats;
 
 typedef struct { int32_t kind; double eps, sigma, r_cut, A; } om_potential;      /* kind 0 harmonic, 1 WCA, 2 Gaussian */
-typedef struct { int32_t kind; double dt, kT, lam, v0, Dr, mass, max_disp; } om_integrator; /* kind 0 NVE, 1 BD, 2 ABP */
+typedef struct { int32_t kind; double dt, kT, lam, v0, Dr, mass, max_disp; } om_integrator; /* kind 0 NVE, 1 BD, 2 ABP, 3 GD, 4 FIRE */
+
+/* FIRE constants (the published defaults) */
+#define OM_FIRE_ALPHA0 0.1
+#define OM_FIRE_FINC 1.1
+#define OM_FIRE_FDEC 0.5
+#define OM_FIRE_FALPHA 0.99
+#define OM_FIRE_NMIN 5
+#define OM_FIRE_DTMAX 10.0   /* times the initial dt */
 
 /* mesh: X (nv x 3), F (nf x 3, CCW outward), period NULL or {Lx, Ly}.  Returns 0 or <0. */
 int  om_mesh_create(const double* X, int64_t nv, const int32_t* F, int64_t nf,
@@ -104,6 +112,10 @@ int om_integrate(const om_mesh* m, int64_t n, int32_t* face, double* bary, doubl
                  int64_t step0, const double* noise, double* epot, int nthreads);
 
 void om_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* FIRE minimisation steps (see css_oracle.c); state[3] = {dt, alpha, steps with P > 0}. */
+int om_fire(const om_mesh* m, int64_t n, int32_t* face, double* bary, double* vel, double* force,
+            const om_potential* pot, const om_integrator* it, double r_c, int64_t nsteps, double* state,
+            double* epot, int nthreads);
 void om_normal_pair(uint64_t seed, uint64_t particle, uint64_t step, double* z0, double* z1);
 
 #ifdef __cplusplus

@@ -49,6 +49,8 @@ def lib():
         L.om_integrate.argtypes = [P, C.c_int64, P, P, P, P, P, P, P, C.c_double, C.c_int64,
                                    C.c_uint64, C.c_int64, P, P, C.c_int]
         L.om_integrate.restype = C.c_int
+        L.om_fire.argtypes = [P, C.c_int64, P, P, P, P, P, P, C.c_double, C.c_int64, P, P, C.c_int]
+        L.om_fire.restype = C.c_int
         L.om_philox4x32_10.argtypes = [P, P, P]
         L.om_normal_pair.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, P, P]
         _lib = L
@@ -269,6 +271,25 @@ class OracleMesh:
         if rc != 0:
             raise ValueError(f"oracle integrate failed ({rc})")
         return dict(face=face, bary=bary, vel=vel, orient=orient, force=force, epot=e.value)
+
+
+    def fire(self, face, bary, vel, force, pot: dict, integ: dict, r_c: float, nsteps: int, state=None,
+             nthreads: int = 0):
+        """FIRE minimisation steps; force must hold the forces at the given positions.
+        state = [dt, alpha, steps with P > 0] (default: the integrator's dt, 0.1, 0)."""
+        face = _i32(face).copy()
+        bary = _f64(bary).copy()
+        n = face.shape[0]
+        vel = np.zeros((n, 3)) if vel is None else _f64(vel).copy()
+        force = _f64(force).copy()
+        st = np.array([integ["dt"], 0.1, 0.0] if state is None else state, dtype=np.float64)
+        P, I = potential(pot), integrator(integ)
+        e = C.c_double(0.0)
+        rc = lib().om_fire(self.h, n, _p(face), _p(bary), _p(vel), _p(force), C.byref(P), C.byref(I),
+                           float(r_c), int(nsteps), _p(st), C.byref(e), int(nthreads))
+        if rc != 0:
+            raise ValueError(f"oracle fire failed ({rc})")
+        return dict(face=face, bary=bary, vel=vel, force=force, state=st, epot=e.value)
 
 
 def pair_energy(pot: dict, l: float) -> float:

@@ -18,7 +18,7 @@ CONFIG_NAMES = ("flat64", "ico5_n1024", "hfield256_n8192", "tori64", "noisy_ico8
 # potential kinds, shared numbering with the C ABI header and the oracle
 POT_HARMONIC, POT_WCA, POT_GAUSSIAN = 0, 1, 2
 # integrator kinds
-INT_NVE, INT_BD, INT_ABP = 0, 1, 2
+INT_NVE, INT_BD, INT_ABP, INT_GD, INT_FIRE = 0, 1, 2, 3, 4
 
 WCA_RCUT = 2.0 ** (1.0 / 6.0)
 

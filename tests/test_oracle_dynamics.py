@@ -6,7 +6,7 @@ import pytest
 
 import synth
 from oracle import oracle as O
-from synth.configs import POT_HARMONIC, POT_WCA, POT_GAUSSIAN, INT_NVE, INT_BD, INT_ABP
+from synth.configs import POT_HARMONIC, POT_WCA, POT_GAUSSIAN, INT_NVE, INT_BD, INT_ABP, INT_GD, INT_FIRE
 
 
 def _bary_at(m, f, p):
@@ -303,3 +303,71 @@ def test_displacement_clamp():
     s = om.integrate([f], [b], None, np.array([[1.0, 0.0, 0.0]]), None, pot, integ, 1e-3, 1,
                      noise=np.zeros((1, 2)))
     np.testing.assert_allclose(om.world(s["face"], s["bary"])[0], [0.35, 0.2, 0.0], atol=1e-13)
+
+
+# ------------------------------------------------------------------ minimisers (Fig. 3)
+def _pair_on_plane(d):
+    m = synth.grid_plane(31, 31, -3, 3, -3, 3)
+    locs = [_find(m, np.array([-d / 2, 0.013, 0.0])), _find(m, np.array([d / 2, 0.013, 0.0]))]
+    face = np.array([f for f, _ in locs], np.int32)
+    bary = np.array([b for _, b in locs])
+    return m, face, bary
+
+
+def test_steepest_descent_step_closed_form():
+    """One descent step of two harmonic particles on a plane moves each away from the
+    other by (dt / lambda) |U'(d)|: d' = d + 2 (dt / lambda) 2 (1 - d / sigma) / sigma."""
+    d, sig, dt, lam = 0.3, 0.5, 0.01, 2.0
+    m, face, bary = _pair_on_plane(d)
+    om = O.OracleMesh(m)
+    pot = dict(kind=POT_HARMONIC, eps=1.0, sigma=sig, r_cut=sig)
+    integ = dict(kind=INT_GD, dt=dt, kT=5.0, lam=lam, v0=0.0, Dr=0.0, mass=1.0, max_disp=1.0)
+    o = om.integrate(face, bary, None, None, None, pot, integ, math.inf, 1)
+    x = om.world(o["face"], o["bary"])
+    expect = d + 2 * (dt / lam) * 2 * (1 - d / sig) / sig
+    assert np.linalg.norm(x[1] - x[0]) == pytest.approx(expect, rel=1e-12)
+    # kT is ignored: descent draws no noise
+    o2 = om.integrate(face, bary, None, None, None, pot, dict(integ, kT=0.0), math.inf, 1)
+    np.testing.assert_array_equal(o["bary"], o2["bary"])
+
+
+def test_fire_first_steps_closed_form():
+    """FIRE from rest: P = 0 halves dt and keeps v = 0, so the first step is a velocity-Verlet
+    step of dt/2 from rest (each particle moves (dt/2)^2/2 |F| / m); on the second step v is
+    parallel to F (P > 0, the mixing leaves it unchanged, dt unchanged before N_min)."""
+    d, sig, dt = 0.3, 0.5, 0.02
+    m, face, bary = _pair_on_plane(d)
+    om = O.OracleMesh(m)
+    pot = dict(kind=POT_HARMONIC, eps=1.0, sigma=sig, r_cut=sig)
+    integ = dict(kind=INT_FIRE, dt=dt, kT=0.0, lam=1.0, v0=0.0, Dr=0.0, mass=1.0, max_disp=1.0)
+    F0, _ = om.forces(face, bary, math.inf, pot)
+    o = om.fire(face, bary, None, F0, pot, integ, math.inf, 1)
+    fmag = 2 * (1 - d / sig) / sig
+    h = dt / 2
+    d1 = d + 2 * 0.5 * h * h * fmag
+    x = om.world(o["face"], o["bary"])
+    assert np.linalg.norm(x[1] - x[0]) == pytest.approx(d1, rel=1e-12)
+    np.testing.assert_allclose(o["state"], [dt / 2, 0.1, 0.0])
+    f1 = 2 * (1 - d1 / sig) / sig
+    assert np.linalg.norm(o["vel"][0]) == pytest.approx(0.5 * h * (fmag + f1), rel=1e-12)
+    o2 = om.fire(o["face"], o["bary"], o["vel"], o["force"], pot, integ, math.inf, 1, state=o["state"])
+    np.testing.assert_allclose(o2["state"], [dt / 2, 0.1, 1.0])
+    v1 = 0.5 * h * (fmag + f1)
+    d2 = d1 + 2 * (h * (v1 + 0.5 * h * f1))
+    x2 = om.world(o2["face"], o2["bary"])
+    assert np.linalg.norm(x2[1] - x2[0]) == pytest.approx(d2, rel=1e-12)
+
+
+def test_fire_relaxes_a_dilute_repulsive_system():
+    """Particles on a torus with soft repulsion relax to zero force (all pairs pushed apart
+    beyond the range): the energy ends far below its start and the forces vanish."""
+    m = synth.torus(3.0, 1.0, 48, 16)
+    face, bary = synth.place_uniform(m, 40, 3)
+    om = O.OracleMesh(m)
+    pot = dict(kind=POT_HARMONIC, eps=1.0, sigma=0.6, r_cut=0.6)
+    integ = dict(kind=INT_FIRE, dt=0.02, kT=0.0, lam=1.0, v0=0.0, Dr=0.0, mass=1.0, max_disp=0.1)
+    F0, E0 = om.forces(face, bary, 0.6, pot)
+    o = om.fire(face, bary, None, F0, pot, integ, 0.6, 400)
+    assert E0 > 0.1
+    assert o["epot"] < 1e-6 * E0
+    assert np.max(np.abs(o["force"])) < 1e-3
