@@ -62,6 +62,9 @@ extern "C" {
 #define CSS_INT_NVE 0   /* velocity Verlet: v += dt/2m F; shift by dt v; F(x); v += dt/2m F */
 #define CSS_INT_BD  1   /* lambda dr = dt F + sqrt(2 kT lambda dt) eta                      */
 #define CSS_INT_ABP 2   /* dr = dt (v0 n + F / lambda); n rotated by sqrt(2 Dr dt) xi       */
+#define CSS_INT_GD  3   /* steepest descent (Fig. 3 caption): dr = (dt / lambda) F, no noise */
+#define CSS_INT_FIRE 4  /* FIRE minimiser (Bitzek et al. 2006): velocity Verlet with velocity
+                           mixing and an adaptive step, see css_integrate_step             */
 
 typedef struct css_ctx css_ctx;
 typedef struct css_mesh css_mesh;
@@ -164,7 +167,14 @@ int css_compute_forces(css_parts* parts, const css_potential* pot, double r_c, i
  * on the first call).  noise: NULL (Philox stream) or a device/host array of
  * n_steps x n x 2 standard normals used instead (test mode).  The steps are
  * replayed from a captured CUDA graph when n_steps > 1 and noise is NULL.
- * e_pot (may be NULL) receives the potential energy of the last force pass. */
+ * e_pot (may be NULL) receives the potential energy of the last force pass.
+ * CSS_INT_FIRE (no counterpart in the paper's text beyond the minimisations of Fig. 3):
+ * each step computes P = sum F.v and the norms |v|, |F| over the set, mixes
+ * v <- (1 - a) v + a |v| F / |F|, then after more than 5 steps in a row with P > 0 grows
+ * the step (x 1.1, at most 10 x integ->dt) and shrinks a (x 0.99), while P <= 0 halves the
+ * step, zeroes v and resets a = 0.1; then one velocity-Verlet step with the current step.
+ * The state (step, a, count) lives on the device and starts from (integ->dt, 0.1, 0)
+ * whenever the integrator parameters change or the particle state is replaced. */
 int css_integrate_step(css_parts* parts, const css_potential* pot, const css_integrator* integ,
                        double r_c, int precision, int64_t n_steps, const double* noise,
                        double* e_pot);
@@ -174,7 +184,8 @@ int css_integrate_step(css_parts* parts, const css_potential* pot, const css_int
  * neighbour/force work of all sets runs in one persistent launch per step whose
  * warps pull (set, source) items from a device work queue ordered by estimated
  * cost, and the whole n_steps sequence is captured once into a CUDA graph.
- * The sets must come from the same context; they share pot/integ/r_c. */
+ * The sets must come from the same context; they share pot/integ/r_c.  CSS_INT_FIRE is
+ * per set (its norms are over one set) and is rejected here with CSS_ERR_INVALID_ARG. */
 int css_batch_create(css_ctx* ctx, css_parts* const* parts, int32_t n_sets, css_batch** out);
 int css_batch_step(css_batch* batch, const css_potential* pot, const css_integrator* integ,
                    double r_c, int precision, int64_t n_steps);

@@ -21,7 +21,7 @@ ERR_NAMES = {-1: "INVALID_ARG", -2: "NONMANIFOLD", -3: "OOM", -4: "CUDA", -5: "C
              -6: "QUEUE_OVERFLOW", -7: "ITER_LIMIT", -8: "NO_DEVICE"}
 FP64, FP32 = 0, 1
 POT_HARMONIC, POT_WCA, POT_GAUSSIAN = 0, 1, 2
-INT_NVE, INT_BD, INT_ABP = 0, 1, 2
+INT_NVE, INT_BD, INT_ABP, INT_GD, INT_FIRE = 0, 1, 2, 3, 4
 
 SYMBOLS = ("css_create", "css_destroy", "css_last_error", "css_last_counters", "css_set_launch",
            "css_mesh_upload", "css_mesh_free", "css_mesh_counts", "css_particles_set",

@@ -494,6 +494,7 @@ int css_particles_set(css_ctx* c, css_mesh* m, int64_t n, const int32_t* face, c
     if (e == cudaSuccess) e = cudaMalloc(&p->scan_tmp, cssi::scan_tmp_ints(nf + 1) * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->pcnt, n * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->dstep, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p->dfire, 16 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->dstep, 0, sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->fcnt, 0, (nf + 1) * sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->force, 0, 3 * n * sizeof(double), st);
@@ -538,6 +539,7 @@ int css_particles_update(css_parts* p, const int32_t* face, const double* bary, 
     if (vel) TRY(c, "particles_update", cudaMemcpyAsync(p->vel, vel, 3 * p->n * sizeof(double), kind(vel), st));
     if (orient) TRY(c, "particles_update", cudaMemcpyAsync(p->orient, orient, 3 * p->n * sizeof(double), kind(orient), st));
     if (face || bary) p->force_valid = 0;
+    if (face || bary || vel) p->fire_valid = 0;
     return CSS_OK;
 }
 
@@ -546,7 +548,7 @@ int css_particles_free(css_parts* p) {
     if (p->graph) cudaGraphExecDestroy(p->graph);
     cudaFree(p->state); cudaFree(p->snap);
     cudaFree(p->fcnt); cudaFree(p->fstart); cudaFree(p->fitems); cudaFree(p->scan_tmp); cudaFree(p->order);
-    cudaFree(p->pcnt); cudaFree(p->pj); cudaFree(p->pd); cudaFree(p->pt); cudaFree(p->dstep);
+    cudaFree(p->pcnt); cudaFree(p->pj); cudaFree(p->pd); cudaFree(p->pt); cudaFree(p->dstep); cudaFree(p->dfire);
     delete p;
     return CSS_OK;
 }
@@ -617,12 +619,16 @@ cudaError_t snap_take(css_parts* p) {
         cudaError_t e = cudaMalloc(&p->snap, p->state_bytes());
         if (e != cudaSuccess) return e;
     }
-    return cudaMemcpyAsync(p->snap, p->state, p->state_bytes(), cudaMemcpyDeviceToDevice, p->ctx->stream);
+    cudaError_t e = cudaMemcpyAsync(p->snap, p->state, p->state_bytes(), cudaMemcpyDeviceToDevice, p->ctx->stream);
+    if (e != cudaSuccess || !p->fire_valid) return e;
+    return cudaMemcpyAsync(p->dfire + 8, p->dfire, 8 * sizeof(double), cudaMemcpyDeviceToDevice, p->ctx->stream);
 }
 
 cudaError_t snap_restore(css_parts* p) {
     cudaStream_t st = p->ctx->stream;
     cudaError_t e = cudaMemcpyAsync(p->state, p->snap, p->state_bytes(), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && p->fire_valid)
+        e = cudaMemcpyAsync(p->dfire, p->dfire + 8, 8 * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(p->dstep, &p->step, sizeof(int64_t), cudaMemcpyHostToDevice, st);
 }
@@ -633,7 +639,10 @@ int enqueue_move(css_parts* p, const css_integrator* it, const double* noise, in
     css_ctx* c = p->ctx;
     cudaStream_t st = c->stream;
     const int32_t n = (int32_t)p->n;
-    if (it->kind == CSS_INT_NVE) {
+    if (it->kind == CSS_INT_FIRE) {
+        TRY(c, "fire", cssi::launch_fire_move(p->mesh->view(), n, p->face, p->bary, p->vel, p->force, p->dfire, *it,
+                                              half, c->dscal + 1, st));
+    } else if (it->kind == CSS_INT_NVE) {
         if (half == 0)
             TRY(c, "kick_drift", cssi::launch_nve_kick_drift(p->mesh->view(), n, p->face, p->bary, p->vel, p->force, *it,
                                                              c->dscal + 1, st));
@@ -679,18 +688,26 @@ int capture(css_ctx* c, Fn fn, cudaGraphExec_t* exec) {
 
 int css_integrate_step(css_parts* p, const css_potential* pot, const css_integrator* it, double r_c, int precision,
                        int64_t n_steps, const double* noise, double* e_pot) {
-    if (!p || !pot || !it || bad_prec(precision) || bad_rc(r_c) || n_steps < 0 || it->kind < 0 || it->kind > 2 ||
+    if (!p || !pot || !it || bad_prec(precision) || bad_rc(r_c) || n_steps < 0 || it->kind < 0 || it->kind > 4 ||
         !(it->dt > 0.0) || !(it->mass > 0.0) || !(it->lambda > 0.0) || !(it->max_disp > 0.0))
         return CSS_ERR_INVALID_ARG;
     css_ctx* c = p->ctx;
     cudaStream_t st = c->stream;
     if (n_steps == 0) return CSS_OK;
-    // NVE needs the force at the current positions
-    if (it->kind == CSS_INT_NVE &&
+    // NVE and FIRE need the force at the current positions
+    if ((it->kind == CSS_INT_NVE || it->kind == CSS_INT_FIRE) &&
         !(p->force_valid && p->force_rc == r_c && p->force_prec == precision &&
           memcmp(&p->force_pot, pot, sizeof(css_potential)) == 0)) {
         int rc = css_compute_forces(p, pot, r_c, precision, nullptr, nullptr);
         if (rc) return rc;
+    }
+    // FIRE starts from (dt, alpha 0.1, no step counted) for new parameters or a new state
+    if (it->kind == CSS_INT_FIRE && !(p->fire_valid && memcmp(&p->fire_it, it, sizeof(css_integrator)) == 0)) {
+        const double init[8] = {it->dt, 0.1, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        TRY(c, "fire state", cudaMemcpyAsync(p->dfire, init, sizeof(init), cudaMemcpyHostToDevice, st));
+        TRY(c, "fire state", cudaStreamSynchronize(st));
+        p->fire_valid = 1;
+        p->fire_it = *it;
     }
     double* dnoise = nullptr;
     if (noise) {
@@ -840,7 +857,7 @@ int batch_enqueue_forces(css_batch* b, const css_potential* pot, double rc, int 
 
 int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator* it, double r_c, int precision,
                    int64_t n_steps) {
-    if (!b || !pot || !it || bad_prec(precision) || bad_rc(r_c) || n_steps < 0 || it->kind < 0 || it->kind > 2 ||
+    if (!b || !pot || !it || bad_prec(precision) || bad_rc(r_c) || n_steps < 0 || it->kind < 0 || it->kind > 3 ||
         !(it->dt > 0.0) || !(it->mass > 0.0) || !(it->lambda > 0.0) || !(it->max_disp > 0.0))
         return CSS_ERR_INVALID_ARG;
     css_ctx* c = b->ctx;

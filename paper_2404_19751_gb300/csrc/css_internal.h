@@ -110,6 +110,9 @@ struct css_parts {
     int32_t* scan_tmp = nullptr;
     int32_t* order = nullptr;   // source processing order (n)
     int64_t* dstep = nullptr;   // device copy of the step counter (Philox counter word)
+    double* dfire = nullptr;    // FIRE state: 8 live doubles, then their snapshot
+    int fire_valid = 0;         // the FIRE state belongs to fire_it and the current particles
+    css_integrator fire_it{};
     // pair slab
     int32_t* pcnt = nullptr;    // n
     int32_t* pj = nullptr;
@@ -215,6 +218,11 @@ cudaError_t launch_overdamped_move(const css::DMesh& m, int32_t n, int32_t* face
                                    uint64_t seed, const int64_t* dstep, const double* noise, int* status,
                                    cudaStream_t st);
 cudaError_t launch_step_inc(int64_t* dstep, cudaStream_t st);
+// FIRE minimiser step halves (half 0: reductions, control, mixing, kick and drift; half 1:
+// the second kick); fire_state: 8 doubles on the device (see dynamics.cu)
+cudaError_t launch_fire_move(const css::DMesh& m, int32_t n, int32_t* face, double* bary, double* vel,
+                             const double* force, double* fire_state, css_integrator it, int half, int* status,
+                             cudaStream_t st);
 // batched forms over the sets of a batch: item k belongs to set s with offs[s] <= k < offs[s+1]
 // (offs has nsets + 1 entries on the device; total = offs[nsets])
 cudaError_t launch_batch_bucket(const SetView* sv, const int32_t* offs, int nsets, int64_t total, cudaStream_t st);

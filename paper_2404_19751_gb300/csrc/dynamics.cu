@@ -14,6 +14,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "css_internal.h"
 
 namespace {
@@ -332,16 +334,18 @@ __global__ void k_nve_kick(int32_t n, double* vel, const double* force, double h
 __device__ void overdamped_one(const DMesh& m, int i, int32_t* face, double* bary, double* orient, const double* force,
                                const css_integrator& it, uint64_t seed, const int64_t* dstep, const double* noise,
                                int* status) {
-    double z0, z1;
-    if (noise) { z0 = noise[2 * (size_t)i]; z1 = noise[2 * (size_t)i + 1]; }
-    else normal_pair(seed, (uint64_t)i, (uint64_t)*dstep, z0, z1);
+    double z0 = 0.0, z1 = 0.0;   // steepest descent draws no noise
+    if (it.kind != CSS_INT_GD) {
+        if (noise) { z0 = noise[2 * (size_t)i]; z1 = noise[2 * (size_t)i + 1]; }
+        else normal_pair(seed, (uint64_t)i, (uint64_t)*dstep, z0, z1);
+    }
     int f = face[i];
     const double* fr = m.frame + 9 * (size_t)f;
     double b[3] = {bary[3 * i], bary[3 * i + 1], bary[3 * i + 2]};
     double d[3];
     bool ok;
-    if (it.kind == CSS_INT_BD) {
-        const double amp = sqrt(2.0 * it.kT * it.dt / it.lambda);
+    if (it.kind == CSS_INT_BD || it.kind == CSS_INT_GD) {
+        const double amp = it.kind == CSS_INT_BD ? sqrt(2.0 * it.kT * it.dt / it.lambda) : 0.0;
         for (int a = 0; a < 3; ++a) d[a] = it.dt / it.lambda * force[3 * i + a] + amp * (z0 * fr[3 + a] + z1 * fr[6 + a]);
         clamp_disp(d, it.max_disp);
         ok = shift_particle(m, f, b, d, 0, nullptr, nullptr);
@@ -370,6 +374,77 @@ __global__ void k_overdamped(DMesh m, int32_t n, int32_t* face, double* bary, do
 }
 
 __global__ void k_step_inc(int64_t* dstep) { *dstep += 1; }
+
+// ------------------------------------------------------------------ FIRE minimiser
+// Device state of one set: [0] step, [1] alpha, [2] consecutive steps with P > 0,
+// [3] velocity factor, [4] force factor of the mixing, [5..7] sums P, |v|^2, |F|^2.
+constexpr double FIRE_ALPHA0 = 0.1, FIRE_FINC = 1.1, FIRE_FDEC = 0.5, FIRE_FALPHA = 0.99;
+constexpr int FIRE_NMIN = 5;
+
+__global__ void k_fire_reduce(int64_t n3, const double* vel, const double* force, double* st) {
+    double P = 0.0, vv = 0.0, ff = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = vel[i], f = force[i];
+        P += f * v;
+        vv += v * v;
+        ff += f * f;
+    }
+    P = css::warp_sum(P);
+    vv = css::warp_sum(vv);
+    ff = css::warp_sum(ff);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(st + 5, P);
+        atomicAdd(st + 6, vv);
+        atomicAdd(st + 7, ff);
+    }
+}
+
+// one thread: the mixing factors with the current alpha, then the step / alpha update
+__global__ void k_fire_control(double* st, double dt_max) {
+    const double P = st[5], vv = st[6], ff = st[7], alpha = st[1];
+    double c1 = 1.0, c2 = 0.0;
+    if (ff > 0.0) { c1 = 1.0 - alpha; c2 = alpha * sqrt(vv) / sqrt(ff); }
+    if (P > 0.0) {
+        st[2] += 1.0;
+        if (st[2] > FIRE_NMIN) {
+            st[0] = fmin(st[0] * FIRE_FINC, dt_max);
+            st[1] = alpha * FIRE_FALPHA;
+        }
+    } else {
+        st[2] = 0.0;
+        st[0] *= FIRE_FDEC;
+        st[1] = FIRE_ALPHA0;
+        c1 = 0.0;
+        c2 = 0.0;
+    }
+    st[3] = c1;
+    st[4] = c2;
+    st[5] = st[6] = st[7] = 0.0;
+}
+
+__global__ void k_fire_mix_kick_drift(DMesh m, int32_t n, int32_t* face, double* bary, double* vel,
+                                      const double* force, const double* st, css_integrator it, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double c1 = st[3], c2 = st[4], dt = st[0], h = 0.5 * dt / it.mass;
+    double v[3], d[3];
+    for (int a = 0; a < 3; ++a) {
+        v[a] = c1 * vel[3 * i + a] + c2 * force[3 * i + a];
+        v[a] += h * force[3 * i + a];
+        d[a] = dt * v[a];
+    }
+    clamp_disp(d, it.max_disp);
+    int f = face[i];
+    double b[3] = {bary[3 * i], bary[3 * i + 1], bary[3 * i + 2]};
+    if (!shift_particle(m, f, b, d, 1, v, nullptr)) atomicOr(status, css::ST_WALK_LIMIT);
+    face[i] = f;
+    for (int a = 0; a < 3; ++a) { bary[3 * i + a] = b[a]; vel[3 * i + a] = v[a]; }
+}
+
+__global__ void k_fire_kick(int64_t n3, double* vel, const double* force, const double* st, double mass) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n3) vel[i] += 0.5 * st[0] / mass * force[i];
+}
 
 // ------------------------------------------------------------------ many sets in one launch
 // Work item k of a batch belongs to the set s with offs[s] <= k < offs[s+1] (a handful of
@@ -513,6 +588,20 @@ cudaError_t launch_overdamped_move(const DMesh& m, int32_t n, int32_t* face, dou
 
 cudaError_t launch_step_inc(int64_t* dstep, cudaStream_t st) {
     k_step_inc<<<1, 1, 0, st>>>(dstep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fire_move(const DMesh& m, int32_t n, int32_t* face, double* bary, double* vel,
+                             const double* force, double* fire_state, css_integrator it, int half, int* status,
+                             cudaStream_t st) {
+    if (half == 0) {
+        const int64_t n3 = 3 * (int64_t)n;
+        k_fire_reduce<<<(unsigned)std::min<int64_t>(nb(n3), 1024), 256, 0, st>>>(n3, vel, force, fire_state);
+        k_fire_control<<<1, 1, 0, st>>>(fire_state, 10.0 * it.dt);
+        k_fire_mix_kick_drift<<<nb(n, 128), 128, 0, st>>>(m, n, face, bary, vel, force, fire_state, it, status);
+    } else {
+        k_fire_kick<<<nb(3 * (int64_t)n), 256, 0, st>>>(3 * (int64_t)n, vel, force, fire_state, it.mass);
+    }
     return cudaGetLastError();
 }
 

@@ -324,3 +324,69 @@ def test_batch_overdamped_equals_single_sets(ctx, kind):
         p.free()
     for mesh in meshes:
         mesh.free()
+
+
+def _torus_case(n=300, seed=5):
+    m = synth.torus(3.0, 1.0, 64, 24)
+    face, bary = synth.place_uniform(m, n, seed)
+    return m, face, bary
+
+
+def test_steepest_descent_matches_oracle(ctx):
+    """Steepest-descent relaxation (Fig. 3 caption): three steps equal the oracle's, and the
+    batched form gives the same steps."""
+    m, face, bary = _torus_case()
+    r_c = 0.4
+    pot = dict(kind=css.POT_HARMONIC, eps=1.0, sigma=r_c, r_cut=r_c)
+    integ = dict(kind=css.INT_GD, dt=0.01, kT=0.0, lam=1.0, v0=0.0, Dr=0.0, mass=1.0, max_disp=0.05)
+    o = O.OracleMesh(m).integrate(face, bary, None, None, None, pot, integ, r_c, 3)
+    mesh, parts = _setup(ctx, m, face, bary)
+    css.integrate_step(parts, pot, integ, r_c, css.FP64, 3)
+    s = css.particles_get(parts)
+    assert np.array_equal(s["face"], o["face"])
+    np.testing.assert_allclose(s["bary"], o["bary"], atol=1e-10)
+    p2 = css.particles_set(ctx, mesh, face, bary)
+    b = css.batch_create(ctx, [p2])
+    css.batch_step(b, pot, integ, r_c, css.FP64, 3)
+    s2 = css.particles_get(p2)
+    assert np.array_equal(s2["face"], o["face"])
+    np.testing.assert_allclose(s2["bary"], o["bary"], atol=1e-10)
+    b.free()
+    p2.free()
+    parts.free()
+    mesh.free()
+
+
+def test_fire_matches_oracle_and_relaxes(ctx):
+    """FIRE: twelve steps equal the oracle's (positions, velocities, adaptive state through
+    the P <= 0 restart of the first step and the growth after five P > 0 steps); the batched
+    form rejects it (its norms are per set)."""
+    m, face, bary = _torus_case()
+    r_c = 0.4
+    pot = dict(kind=css.POT_HARMONIC, eps=1.0, sigma=r_c, r_cut=r_c)
+    integ = dict(kind=css.INT_FIRE, dt=0.01, kT=0.0, lam=1.0, v0=0.0, Dr=0.0, mass=1.0, max_disp=0.05)
+    om = O.OracleMesh(m)
+    F0, E0 = om.forces(face, bary, r_c, pot)
+    o = om.fire(face, bary, None, F0, pot, integ, r_c, 12)
+    mesh, parts = _setup(ctx, m, face, bary)
+    E = css.integrate_step(parts, pot, integ, r_c, css.FP64, 12)
+    s = css.particles_get(parts)
+    assert np.array_equal(s["face"], o["face"])
+    np.testing.assert_allclose(s["bary"], o["bary"], atol=1e-9)
+    np.testing.assert_allclose(s["vel"], o["vel"], atol=1e-9 * max(1.0, np.max(np.abs(o["vel"]))))
+    assert E == pytest.approx(o["epot"], rel=1e-9)
+    assert o["epot"] < E0
+    # FP32 form: the same trajectory within the FP32 distance tolerance
+    p32 = css.particles_set(ctx, mesh, face, bary)
+    css.integrate_step(p32, pot, integ, r_c, css.FP32, 12)
+    s32 = css.particles_get(p32)
+    x32 = synth.particles.world_positions(m, s32["face"], s32["bary"])
+    x64 = synth.particles.world_positions(m, o["face"], o["bary"])
+    assert np.max(np.linalg.norm(x32 - x64, axis=1)) <= FP32_REL_DIAM * synth.bbox_diagonal(m)
+    b = css.batch_create(ctx, [p32])
+    with pytest.raises(css.CssError):
+        css.batch_step(b, pot, integ, r_c, css.FP32, 1)
+    b.free()
+    p32.free()
+    parts.free()
+    mesh.free()
