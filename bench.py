@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ico5_n1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", choices=["n", "v"], default=None,
+                    help="time per MD step against particle count (n) or mesh size (v) on a torus, "
+                         "with the fitted power-law exponents (not the benchmark line)")
     return ap.parse_args()
 
 
@@ -607,10 +610,76 @@ def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
     return line
 
 
+def run_sweep(args):
+    """Time per MD step against N (torus r=1, R=3, ~4616 faces, range 1) or against the face
+    count V (N = 100 on the same aspect-3 torus, range = one tenth of the span, and the
+    whole mesh without cutoff), both forms, each point the median of `--steps` graph-replayed
+    steps after `--warmup`; prints the points and the log-log slopes (the paper's Sec. 4
+    reports exponents of about 1.4 in N and 2.07 / 1.73 in V for its CPU code)."""
+    import numpy as np
+    import torch
+    import paper_2404_19751_gb300 as css
+    import synth
+    from synth.configs import torus_for_faces
+    ctx = css.create(0)
+    integ = dict(kind=css.INT_NVE, dt=1e-3, kT=0.0, lam=1.0, v0=0.0, Dr=0.0, mass=1.0, max_disp=math.inf)
+
+    def step_ms(m, n, r_c, prec, seed):
+        face, bary = synth.place_uniform(m, n, seed)
+        mesh = css.mesh_upload(ctx, m.verts, m.faces)
+        parts = css.particles_set(ctx, mesh, face, bary)
+        sig = r_c if math.isfinite(r_c) else 1.0
+        pot = dict(kind=css.POT_HARMONIC, eps=1.0, sigma=sig, r_cut=sig)
+        css.integrate_step(parts, pot, integ, r_c, prec, max(1, args.warmup))
+        t = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            css.integrate_step(parts, pot, integ, r_c, prec, 1)
+            b.record()
+            torch.cuda.synchronize()
+            t.append(a.elapsed_time(b))
+        parts.free()
+        mesh.free()
+        return float(np.median(t))
+
+    pts = []
+    if args.sweep == "n":
+        m = torus_for_faces(4616, 3.0, 1.0)
+        for n in (64, 128, 256, 512, 1024, 2048, 4096):
+            pts.append(dict(N=n, faces=m.nf, r_c=1.0, ms_fp32=step_ms(m, n, 1.0, css.FP32, 7),
+                            ms_fp64=step_ms(m, n, 1.0, css.FP64, 7)))
+        xs = [p["N"] for p in pts]
+        paper = {"submesh": 1.4, "full_mesh": 1.4}
+    else:
+        for F in (1000, 2000, 4000, 8000, 16000):
+            m = torus_for_faces(F, 3.0, 1.0)
+            span = 2 * (3.0 + 1.0)
+            pts.append(dict(N=100, faces=m.nf, r_c=span / 10, ms_fp32=step_ms(m, 100, span / 10, css.FP32, 8),
+                            ms_fp64=step_ms(m, 100, span / 10, css.FP64, 8),
+                            full_ms_fp32=step_ms(m, 100, math.inf, css.FP32, 8)))
+        xs = [p["faces"] for p in pts]
+        paper = {"submesh": 1.73, "full_mesh": 2.07}
+
+    def slope(key):
+        ys = [p[key] for p in pts]
+        return float(np.polyfit(np.log(xs), np.log(ys), 1)[0])
+    out = {"sweep": args.sweep, "points": pts, "exponent_fp32": slope("ms_fp32"), "exponent_fp64": slope("ms_fp64"),
+           "paper_exponents_cpu": paper}
+    if args.sweep == "v":
+        out["exponent_full_mesh_fp32"] = slope("full_ms_fp32")
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
