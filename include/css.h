@@ -182,8 +182,9 @@ int css_integrate_step(css_parts* parts, const css_potential* pot, const css_int
 /* ---------------------------------------------------------------- batched form
  * Many independent particle sets (each on its own mesh) advanced together: the
  * neighbour/force work of all sets runs in one persistent launch per step whose
- * warps pull (set, source) items from a device work queue ordered by estimated
- * cost, and the whole n_steps sequence is captured once into a CUDA graph.
+ * warps pull (set, source) items from a device work queue (sets with more particles
+ * first), moves and face bucketing of all sets run as single launches, and one step is
+ * captured into a CUDA graph (kept while the parameters stay the same) and replayed.
  * The sets must come from the same context; they share pot/integ/r_c.  CSS_INT_FIRE is
  * per set (its norms are over one set) and is rejected here with CSS_ERR_INVALID_ARG. */
 int css_batch_create(css_ctx* ctx, css_parts* const* parts, int32_t n_sets, css_batch** out);

@@ -17,14 +17,16 @@
 // F_i = sum_j U'(l_ij) t_ij is accumulated in the same pass.
 //
 // GPU organisation: one warp owns one source at a time (persistent grid pulling
-// sources from a device counter).  The warp pops up to 32 windows per wave (FIFO
-// over the window pool = creation order, a relaxed label-correcting order that is
-// exact because every window only ever carries the length of a real path and
-// trimming keeps the pointwise minimum), unfolds them in parallel, then inserts
-// the children: lanes that target the same edge are grouped with __match_any_sync
-// and take turns, lanes on different edges trim in parallel.  Per-warp state
-// (edge, vertex and face hash tables with generation tags, the window pool)
-// lives in a global-memory workspace slice that stays L1/L2 resident.
+// sources, in Morton order of their faces, from a device counter).  Each wave takes
+// up to 32 pending windows among those with the smallest keys (a relaxed priority
+// order; exact because every window only ever carries the length of a real path and
+// trimming keeps the pointwise minimum), unfolds them in parallel, then inserts the
+// children: lanes that target the same edge are grouped with __match_any_sync and take
+// turns, lanes on different edges trim in parallel.  A pseudo-source vertex emits its
+// windows once no pending key is below its distance.  Two passes: the first keeps the
+// per-warp hash tables (edge list heads, pseudo-source vertices, face set) in shared
+// memory; a source whose patch overflows them or the window pool is deferred to a second
+// pass with generation-tagged tables in the warp's global-memory workspace slice.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
