@@ -247,7 +247,10 @@ int css_fma_peak(css_ctx* ctx, int precision, double* flops_per_s);
  *                      most 8 resident warps per SM, no spills), 2 = at most 128 (twice
  *                      the resident warps, some spills to local memory)
  * css_set_launch fails with CSS_ERR_INVALID_ARG when a value is out of range or the
- * shape's shared memory does not fit an SM. */
+ * shape's shared memory does not fit an SM.  Until a shape is set or tuned, a context
+ * starts from {4, 0, 1, 1, 2048, 16384, 2, 1} and adapts by itself: after an evaluation
+ * that deferred more than a quarter of its sources it switches the first pass to global
+ * tables with a four times larger pool (up to 2^17 windows). */
 typedef struct css_launch {
     int32_t warps_per_cta, ctas_per_sm, tile, shared_scale;
     int32_t window_capacity, window_capacity2, warps2_per_sm, occupancy;

@@ -259,6 +259,18 @@ int status_error(css_ctx* c, int status) {
     return CSS_ERR_CUDA;
 }
 
+// A context whose launch shape nobody set or tuned adapts its first pass: when more than a
+// quarter of the evaluated sources were deferred (patches too large for the shared tables
+// or the pool), later evaluations use global tables and a four times larger pool.
+void adapt_default(css_ctx* c) {
+    if (c->cfg_explicit) return;
+    const int64_t done = c->last_counters[0], deferred = c->last_counters[4];
+    if (done > 0 && deferred * 4 > done && c->cfg.win_cap < (1 << 17)) {
+        c->cfg.shared_scale = 0;
+        c->cfg.win_cap = std::max(c->cfg.win_cap * 4, 8192);
+    }
+}
+
 // synchronous neighbour / force evaluation with overflow retries
 int run_geo(css_parts* p, double rc, int prec, int want_pairs, int want_forces, const css_potential* pot) {
     css_ctx* c = p->ctx;
@@ -277,7 +289,7 @@ int run_geo(css_parts* p, double rc, int prec, int want_pairs, int want_forces, 
         int status = 0;
         rc1 = read_status(c, &status);
         if (rc1) return rc1;
-        if (status == 0) return CSS_OK;
+        if (status == 0) { adapt_default(c); return CSS_OK; }
         if (!grow_for(c, status, &retries)) return status_error(c, status);
     }
 }
@@ -396,6 +408,7 @@ int css_set_launch(css_ctx* c, const css_launch* l) {
     c->cfg.win_cap2 = next_pow2(l->window_capacity2);
     c->cfg.warps2_per_sm = l->warps2_per_sm;
     c->cfg.occupancy = l->occupancy;
+    c->cfg_explicit = 1;
     return CSS_OK;
 }
 
@@ -752,7 +765,7 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
         int status = 0;
         rc = read_status(c, &status);
         if (rc) break;
-        if (status == 0) break;
+        if (status == 0) { adapt_default(c); break; }
         if (!grow_for(c, status, &retries)) { rc = status_error(c, status); break; }
         TRY(c, "restore", snap_restore(p));
     }
@@ -919,7 +932,7 @@ int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator*
         int status = 0;
         rc = read_status(c, &status);
         if (rc) return rc;
-        if (status == 0) break;
+        if (status == 0) { adapt_default(c); break; }
         if (!grow_for(c, status, &retries)) return status_error(c, status);
         for (css_parts* p : b->sets) TRY(c, "restore", snap_restore(p));
     }
@@ -1083,6 +1096,7 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
     }
     cleanup();
     c->cfg = rc == CSS_OK ? pick : base;
+    if (rc == CSS_OK) c->cfg_explicit = 1;
     for (int k = 0; k < n_sets; ++k) sets[k]->force_valid = 0;   // forces of the sample only
     if (rc) return rc;
     if (best) css_get_launch(c, best);

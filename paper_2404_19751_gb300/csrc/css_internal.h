@@ -45,6 +45,7 @@ struct css_ctx {
     cssi::WsBuf ws1, ws2;
     cssi::LaunchCfg cfg;
     std::map<int64_t, int> bps_cache;   // resident CTAs per SM by (precision, shape)
+    int cfg_explicit = 0;               // the shape was set or tuned (no automatic adaptation)
     int pair_cap = 64;               // pairs per source slab
     // deferral list of the first pass (one entry per work item at most)
     int32_t* defer = nullptr;
