@@ -205,6 +205,22 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(dist, t: float, device: str) -> float:
+    """The slowest rank's time (every rank gets it); without a process group, t itself.
+    The job's throughput is then (units processed by all ranks) / this time."""
+    if not dist:
+        return t
+    import torch
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_throughput(world: int, units_per_rank: float, t_max: float) -> float:
+    """Whole-job rate of `world` replicas that each processed units_per_rank in at most t_max."""
+    return world * units_per_rank / t_max
+
+
 POT_NAMES = {0: "harmonic (1-d/sigma)^2", 1: "WCA", 2: "Gaussian"}
 INT_NAMES = {0: "NVE velocity Verlet", 1: "overdamped Brownian", 2: "active Brownian"}
 
@@ -258,11 +274,7 @@ class Timer:
             torch.cuda.synchronize()
         if self.dist:
             self.dist.barrier()
-        t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-        if self.dist:
-            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-            self.dist.all_reduce(tt, op=self.dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(self.dist, sum(a.elapsed_time(b) for a, b in ev) / 1e3, "cuda")
         return dict(t=t, steps=steps, kernel_ms=kms, pairs=pairs, props=props, clocks=clk.summary())
 
 
@@ -409,20 +421,20 @@ def run_single(args, cfg, css, ctx, torch, stream, timer, rank, world):
                          statistics.mean(r32["kernel_ms"]) / 1e3, "k_geodesic<float>",
                          traffic=TRAFFIC_BYTES.get(cfg["name"]))
     line = {
-        "metric": METRIC, "value": world * r32["pairs"] / t32, "unit": UNIT, "n_gpus": world, "steps": k32,
+        "metric": METRIC, "value": replica_throughput(world, r32["pairs"], t32), "unit": UNIT, "n_gpus": world, "steps": k32,
         "warmup": args.warmup, "ms_per_step": 1e3 * t32 / k32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(describe(cfg, world), precision="FP32 form", launch=r32["launch"]),
         "md_steps_per_s": world * k32 / t32,
         "pairs_per_step": r32["pairs"] / k32,
-        "fp64": {"value": world * r64["pairs"] / t64, "unit": UNIT, "md_steps_per_s": world * k64 / t64,
+        "fp64": {"value": replica_throughput(world, r64["pairs"], t64), "unit": UNIT, "md_steps_per_s": world * k64 / t64,
                  "ms_per_step": 1e3 * t64 / k64, "kernel_ms": statistics.mean(r64["kernel_ms"]),
                  "clocks": r64["clocks"], "launch": r64["launch"]},
         "fp32_over_fp64": (r32["pairs"] / t32) / (r64["pairs"] / t64),
         "accuracy_vs_oracle": acc,
         "roofline": roof,
         "memory_roofline": mem,
-        "e2e": {"value": world * e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": replica_throughput(world, e2e_pairs, e2e_t), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         # per step: move (1) + bucketing (5) + neighbour/force first and second pass (2) + kick
         # or step counter (1)
@@ -448,11 +460,7 @@ def e2e_time(torch, stream, step, args, dist):
     with torch.cuda.stream(stream):
         ee[1].record(stream)
     torch.cuda.synchronize()
-    t = ee[0].elapsed_time(ee[1]) / 1e3
-    if dist:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(dist, ee[0].elapsed_time(ee[1]) / 1e3, "cuda")
     return t, pairs
 
 
@@ -515,7 +523,7 @@ def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
     ctx.set_launch(**r32b["launch"])
 
     def rate(r):
-        return world * r["pairs"] / r["t"]
+        return replica_throughput(world, r["pairs"], r["t"])
 
     def sub(r, what):
         return {"value": rate(r), "unit": UNIT, "what": what, "md_steps_per_s": world * r["steps"] / r["t"],
@@ -609,7 +617,7 @@ def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
         "accuracy_vs_oracle": acc,
         "roofline": roof,
         "memory_roofline": mem,
-        "e2e": {"value": world * e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": n * (4 + 24 + 24),
+        "e2e": {"value": replica_throughput(world, e2e_pairs, e2e_t), "unit": UNIT, "h2d_bytes_per_step": n * (4 + 24 + 24),
                 "d2h_bytes_per_step": n * (4 + 24 + 24 + 24)},
         "gpu_launches": launches_per_step * k32,
         "clocks": r32b["clocks"],
