@@ -958,8 +958,10 @@ static void vertex_turn(const om_mesh* m, int64_t* fp, int cw, double* px, doubl
     }
 }
 
-int om_shift(const om_mesh* m, int32_t* face, double* bary, const double* disp3,
-             int ncarry, double* carry3) {
+/* the walk of om_shift; with rec != NULL it also writes the world position of every
+ * edge or vertex it crosses (at most cap points; *nrec counts all of them) */
+static int shift_rec(const om_mesh* m, int32_t* face, double* bary, const double* disp3,
+                     int ncarry, double* carry3, double* rec, int cap, int* nrec) {
     if (ncarry > OM_MAXCARRY) return -1;
     int64_t f = *face;
     double px, py, dx, dy, cx[OM_MAXCARRY], cy[OM_MAXCARRY];
@@ -992,6 +994,14 @@ int om_shift(const om_mesh* m, int32_t* face, double* bary, const double* disp3,
         if (lh[(k + 1) % 3] < tolb) vcorner = k;
         else if (lh[k] < tolb) vcorner = (k + 1) % 3;
         ++crossings;
+        if (rec) {
+            if (*nrec < cap) {
+                double w[3];
+                face_to_world_vec(m, f, hx, hy, w);
+                for (int c = 0; c < 3; ++c) rec[3 * *nrec + c] = m->frame[9 * f + c] + w[c];
+            }
+            ++*nrec;
+        }
         if (vcorner >= 0) {
             vertex_turn(m, &f, vcorner, &px, &py, &rx, &ry, ncarry, cx, cy);
             dx = rx; dy = ry; entry = -1;
@@ -1036,6 +1046,30 @@ int om_shift(const om_mesh* m, int32_t* face, double* bary, const double* disp3,
     *face = (int32_t)f;
     for (int i = 0; i < ncarry; ++i) face_to_world_vec(m, f, cx[i], cy[i], carry3 + 3 * i);
     return crossings;
+}
+
+int om_shift(const om_mesh* m, int32_t* face, double* bary, const double* disp3,
+             int ncarry, double* carry3) {
+    return shift_rec(m, face, bary, disp3, ncarry, carry3, NULL, 0, NULL);
+}
+
+/* The straightest geodesic from (face, bary) along the world tangent disp3 (its length is
+ * the path length), as a polyline: the start point, every edge or vertex crossing, the end
+ * point (world positions, at most cap points; *npts = all points).  face/bary become the
+ * end point.  A pair's shortest path is this walk along its initial tangent for its length
+ * whenever the path bends at no vertex (Sec. 2.2: shortest paths are straight in the
+ * unfolding of the faces they cross). */
+int om_trace(const om_mesh* m, int32_t* face, double* bary, const double* disp3, int cap, double* pts,
+             int* npts) {
+    if (cap > 0) om_world_position(m, *face, bary, pts);
+    int n = 1, nrec = 0;
+    const int rc = shift_rec(m, face, bary, disp3, 0, NULL, cap > 1 ? pts + 3 : pts, cap > 1 ? cap - 1 : 0, &nrec);
+    if (rc < 0) return rc;
+    n += nrec;
+    if (n < cap) om_world_position(m, *face, bary, pts + 3 * n);
+    ++n;
+    *npts = n;
+    return 0;
 }
 
 /* ------------------------------------------------------------------ Philox4x32-10 (Salmon et al.) */

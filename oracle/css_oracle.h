@@ -102,6 +102,10 @@ int om_forces_subset(const om_mesh* m, int64_t n, const int32_t* face, const dou
  * edge crossings (>= 0) or <0 on error. */
 int om_shift(const om_mesh* m, int32_t* face, double* bary, const double* disp3,
              int ncarry, double* carry3);
+/* The straightest walk of om_shift as a polyline (start, each crossing, end; world
+ * positions, at most cap points, *npts = all of them); face/bary become the end point. */
+int om_trace(const om_mesh* m, int32_t* face, double* bary, const double* disp3, int cap, double* pts,
+             int* npts);
 
 /* nsteps of the chosen dynamics.  vel used by NVE, orient by ABP, force in/out (the
  * force at the current positions must be valid on entry for NVE).  noise: NULL, or

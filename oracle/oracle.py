@@ -49,6 +49,8 @@ def lib():
         L.om_integrate.argtypes = [P, C.c_int64, P, P, P, P, P, P, P, C.c_double, C.c_int64,
                                    C.c_uint64, C.c_int64, P, P, C.c_int]
         L.om_integrate.restype = C.c_int
+        L.om_trace.argtypes = [P, P, P, P, C.c_int, P, P]
+        L.om_trace.restype = C.c_int
         L.om_fire.argtypes = [P, C.c_int64, P, P, P, P, P, P, C.c_double, C.c_int64, P, P, C.c_int]
         L.om_fire.restype = C.c_int
         L.om_philox4x32_10.argtypes = [P, P, P]
@@ -272,6 +274,19 @@ class OracleMesh:
             raise ValueError(f"oracle integrate failed ({rc})")
         return dict(face=face, bary=bary, vel=vel, orient=orient, force=force, epot=e.value)
 
+
+    def trace(self, face: int, bary, disp3, cap: int = 4096):
+        """Polyline (world points: start, crossings, end) of the straightest walk from
+        (face, bary) along disp3, and its end point (face, bary)."""
+        f = C.c_int32(int(face))
+        b = _f64(bary).copy()
+        d = _f64(disp3)
+        pts = np.zeros((cap, 3))
+        n = C.c_int(0)
+        rc = lib().om_trace(self.h, C.byref(f), _p(b), _p(d), int(cap), _p(pts), C.byref(n))
+        if rc != 0:
+            raise ValueError(f"oracle trace failed ({rc})")
+        return pts[:min(n.value, cap)].copy(), n.value, f.value, b
 
     def fire(self, face, bary, vel, force, pot: dict, integ: dict, r_c: float, nsteps: int, state=None,
              nthreads: int = 0):

@@ -277,3 +277,72 @@ def test_descent_check_accepts_shortest_directions_only():
             assert abs(chk(i, int(j[q]), d[q], t[q])) < 1e-8
             bad = t[q] * math.cos(2e-3) + np.cross(n, t[q]) * math.sin(2e-3)
             assert chk(i, int(j[q]), d[q], bad) > 1e-6
+
+
+# ------------------------------------------------------------------ path polylines
+def _locate_xy(m, x, y):
+    """(face, bary) of the point (x, y, 0) of a flat mesh."""
+    P = synth.meshes.unwrapped_face_vertices(m)
+    for f in range(m.nf):
+        A = np.array([[P[f][1][0] - P[f][0][0], P[f][2][0] - P[f][0][0]],
+                      [P[f][1][1] - P[f][0][1], P[f][2][1] - P[f][0][1]]])
+        l1, l2 = np.linalg.solve(A, [x - P[f][0][0], y - P[f][0][1]])
+        b = np.array([1 - l1 - l2, l1, l2])
+        if b.min() > 1e-9:
+            return np.array([f], np.int32), b[None, :]
+    raise ValueError((x, y))
+
+
+def test_trace_on_a_plane_is_the_straight_segment():
+    """On a flat grid the traced path is the straight segment: every recorded point lies on
+    it, in order, and the crossings of the axis-parallel grid lines sit where the segment
+    meets them."""
+    m = synth.grid_plane(11, 11, 0, 1, 0, 1)
+    om = O.OracleMesh(m)
+    face, bary = _locate_xy(m, 0.213, 0.247)
+    x0 = om.world(face, bary)[0]
+    d = np.array([0.51, 0.37, 0.0])
+    pts, n, f1, b1 = om.trace(int(face[0]), bary[0], d)
+    assert n == len(pts) >= 3
+    np.testing.assert_allclose(pts[0], x0, atol=1e-14)
+    np.testing.assert_allclose(pts[-1], x0 + d, atol=1e-12)
+    u = d / np.linalg.norm(d)
+    s = (pts - x0) @ u
+    assert np.all(np.diff(s) >= -1e-14)                             # in order along the segment
+    np.testing.assert_allclose(np.linalg.norm((pts - x0) - np.outer(s, u), axis=1), 0, atol=1e-12)
+    assert np.linalg.norm(np.diff(pts, axis=0), axis=1).sum() == pytest.approx(np.linalg.norm(d), rel=1e-12)
+    # every crossing of a vertical grid line x = k/10 inside the segment is a recorded point
+    for k in range(11):
+        xk = k / 10
+        if min(x0[0], x0[0] + d[0]) < xk < max(x0[0], x0[0] + d[0]):
+            t = (xk - x0[0]) / d[0]
+            assert np.min(np.linalg.norm(pts - (x0 + t * d), axis=1)) < 1e-12
+
+
+def test_trace_on_a_tube_is_the_unrolled_line():
+    """Around an open tube the path is a helix, straight in the unrolled strip: its points
+    have arc length (unrolled) proportional to height, and the total unrolled length is the
+    requested one."""
+    R, H = 1.0, 2.0
+    m = synth.cylinder_tube(24, 8, R, H)
+    om = O.OracleMesh(m)
+    face, bary = synth.place_uniform(m, 1, 9)
+    x0 = om.world(face, bary)[0]
+    # a tangent direction at x0: mix of the axial and the circumferential direction
+    fr = om.face_frame(int(face[0]))
+    n3 = np.cross(fr[1], fr[2])
+    n3 /= np.linalg.norm(n3)
+    ax = np.array([0.0, 0.0, 1.0]) - np.dot([0.0, 0.0, 1.0], n3) * n3
+    ax /= np.linalg.norm(ax)
+    circ = np.cross(n3, ax)
+    d = 1.5 * (0.6 * circ + 0.8 * ax) / np.linalg.norm(0.6 * circ + 0.8 * ax)
+    if x0[2] + d[2] > H - 0.05 or x0[2] + d[2] < 0.05:
+        d[2] = -d[2]
+        d = 1.5 * (0.6 * circ - 0.8 * ax) / np.linalg.norm(0.6 * circ - 0.8 * ax)
+    pts, n, f1, b1 = om.trace(int(face[0]), bary[0], d)
+    seg = np.linalg.norm(np.diff(pts, axis=0), axis=1)
+    # consecutive points share a flat face, so the polyline is the path itself
+    assert seg.sum() == pytest.approx(1.5, rel=1e-12)
+    dz = np.diff(pts[:, 2])
+    # straight in the unrolled strip: equal height gain per unit of unrolled length
+    assert np.allclose(dz / np.maximum(seg, 1e-300), dz[0] / seg[0], atol=1e-9) or np.all(np.abs(dz) < 1e-15)
