@@ -179,6 +179,25 @@ int css_integrate_step(css_parts* parts, const css_potential* pot, const css_int
                        double r_c, int precision, int64_t n_steps, const double* noise,
                        double* e_pot);
 
+/* css_trace_geodesics: the path of a pair as a polyline.  Path k is the straightest
+ * geodesic (the face walk of css_integrate_step) from particle src[k] along the world
+ * tangent tangent[3k..3k+2] (unit) for length[k]; with the tangent and distance of a pair
+ * returned by css_geodesic_neighbors it is that pair's shortest path whenever the path
+ * bends at no vertex (Sec. 2.2: shortest paths are straight in the unfolding of the faces
+ * they cross) -- the end point then coincides with the neighbour, which callers can check
+ * with end_face / end_bary.  Paths that bend at saddle, flat or boundary vertices are not
+ * followed around the bend (the walk goes straight on).
+ *   points   n_paths x max_points x 3 world positions: the start, every edge or vertex
+ *            crossing, the end; unused entries are zero; max_points >= 2;
+ *   n_points all points of each path (more than max_points when truncated);
+ *   end_face, end_bary  the walk's end point.
+ * Inputs and outputs may be host or device pointers.  Allocates temporaries and
+ * synchronises.  CSS_ERR_INVALID_ARG for a source index out of range or a non-finite or
+ * negative length or tangent. */
+int css_trace_geodesics(css_parts* parts, int64_t n_paths, const int32_t* src, const double* tangent,
+                        const double* length, int32_t max_points, double* points, int32_t* n_points,
+                        int32_t* end_face, double* end_bary);
+
 /* ---------------------------------------------------------------- batched form
  * Many independent particle sets (each on its own mesh) advanced together: the
  * neighbour/force work of all sets runs in one persistent launch per step whose

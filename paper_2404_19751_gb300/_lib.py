@@ -27,7 +27,8 @@ SYMBOLS = ("css_create", "css_destroy", "css_last_error", "css_last_counters", "
            "css_mesh_upload", "css_mesh_free", "css_mesh_counts", "css_particles_set",
            "css_particles_get", "css_particles_free", "css_geodesic_neighbors", "css_compute_forces",
            "css_integrate_step", "css_batch_create", "css_batch_step", "css_batch_free",
-           "css_last_kernel_ms", "css_fma_peak", "css_particles_update", "css_get_launch", "css_autotune")
+           "css_last_kernel_ms", "css_fma_peak", "css_particles_update", "css_get_launch", "css_autotune",
+           "css_trace_geodesics")
 
 
 class CssError(RuntimeError):
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
         "css_set_launch": [P, P],
         "css_get_launch": [P, P],
         "css_autotune": [P, P, I32, P, D, C.c_int, I32, I64, P, C.POINTER(D)],
+        "css_trace_geodesics": [P, I64, P, P, P, I32, P, P, P, P],
         "css_mesh_upload": [P, P, I64, P, I64, P, C.POINTER(C.c_void_p)],
         "css_mesh_free": [P],
         "css_mesh_counts": [P, P],
@@ -284,6 +286,24 @@ def geodesic_neighbors(parts: Particles, r_c: float, precision: int = FP64, capa
         parts.ctx.check(rc)
         k = int(npairs.value)
         return rs, j[:k], d[:k], t[:k]
+
+
+def trace_geodesics(parts: Particles, src, tangent, length, max_points: int = 256):
+    """Polylines of straightest geodesics (see css_trace_geodesics): returns a list of
+    (points (k x 3), complete) and the end points (face, bary)."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    tan = np.ascontiguousarray(tangent, dtype=np.float64).reshape(-1, 3)
+    ln = np.ascontiguousarray(length, dtype=np.float64)
+    n = src.shape[0]
+    pts = np.zeros((max(n, 1), max_points, 3))
+    npts = np.zeros(max(n, 1), np.int32)
+    ef = np.zeros(max(n, 1), np.int32)
+    eb = np.zeros((max(n, 1), 3))
+    parts.ctx.check(load().css_trace_geodesics(parts.h, n, src.ctypes.data, tan.ctypes.data, ln.ctypes.data,
+                                               int(max_points), pts.ctypes.data, npts.ctypes.data,
+                                               ef.ctypes.data, eb.ctypes.data))
+    paths = [(pts[k, :min(npts[k], max_points)].copy(), bool(npts[k] <= max_points)) for k in range(n)]
+    return paths, ef[:n], eb[:n]
 
 
 def _pot(p) -> Potential:

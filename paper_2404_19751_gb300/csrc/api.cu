@@ -1103,3 +1103,54 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
     if (best_ms) *best_ms = pick_ms;
     return CSS_OK;
 }
+
+// ------------------------------------------------------------------------------ path polylines
+int css_trace_geodesics(css_parts* p, int64_t n_paths, const int32_t* src, const double* tangent,
+                        const double* length, int32_t max_points, double* points, int32_t* n_points,
+                        int32_t* end_face, double* end_bary) {
+    if (!p || n_paths < 0 || max_points < 2 || (n_paths > 0 && (!src || !tangent || !length || !points || !n_points ||
+                                                                 !end_face || !end_bary)))
+        return CSS_ERR_INVALID_ARG;
+    if (n_paths == 0) return CSS_OK;
+    css_ctx* c = p->ctx;
+    cudaStream_t st = c->stream;
+    // the source indices are checked on the host before any kernel reads through them
+    std::vector<int32_t> hs((size_t)n_paths);
+    std::vector<double> hl((size_t)n_paths), ht(3 * (size_t)n_paths);
+    TRY(c, "trace", cudaMemcpy(hs.data(), src, hs.size() * sizeof(int32_t), cudaMemcpyDefault));
+    TRY(c, "trace", cudaMemcpy(hl.data(), length, hl.size() * sizeof(double), cudaMemcpyDefault));
+    TRY(c, "trace", cudaMemcpy(ht.data(), tangent, ht.size() * sizeof(double), cudaMemcpyDefault));
+    for (int64_t k = 0; k < n_paths; ++k) {
+        if (hs[k] < 0 || hs[k] >= p->n || !std::isfinite(hl[k]) || hl[k] < 0.0 || !std::isfinite(ht[3 * k]) ||
+            !std::isfinite(ht[3 * k + 1]) || !std::isfinite(ht[3 * k + 2])) {
+            c->err = "trace_geodesics: path " + std::to_string(k) + " has a bad source index, length or tangent";
+            return CSS_ERR_INVALID_ARG;
+        }
+    }
+    int32_t *ds = nullptr, *dn = nullptr, *df = nullptr;
+    double *dt = nullptr, *dl = nullptr, *dp = nullptr, *db = nullptr;
+    auto cleanup = [&]() { cudaFree(ds); cudaFree(dn); cudaFree(df); cudaFree(dt); cudaFree(dl); cudaFree(dp); cudaFree(db); };
+    const size_t np = (size_t)n_paths, npts = np * (size_t)max_points;
+    cudaError_t e = stage_in(hs.data(), np, &ds, st);
+    if (e == cudaSuccess) e = stage_in(hl.data(), np, &dl, st);
+    if (e == cudaSuccess) e = stage_in(ht.data(), 3 * np, &dt, st);
+    if (e == cudaSuccess) e = cudaMalloc(&dp, 3 * npts * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dn, np * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&df, np * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&db, 3 * np * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(dp, 0, 3 * npts * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dscal + 1, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cssi::launch_trace(p->mesh->view(), n_paths, p->face, p->bary, ds, dt, dl, max_points, dp, dn, df, db,
+                               c->dscal + 1, st);
+    if (e == cudaSuccess) e = copy_out(points, dp, 3 * npts, st);
+    if (e == cudaSuccess) e = copy_out(n_points, dn, np, st);
+    if (e == cudaSuccess) e = copy_out(end_face, df, np, st);
+    if (e == cudaSuccess) e = copy_out(end_bary, db, 3 * np, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->hstat, c->dscal + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(c, "trace_geodesics", e);
+    if (*c->hstat) return status_error(c, *c->hstat);
+    return CSS_OK;
+}

@@ -224,6 +224,10 @@ cudaError_t launch_step_inc(int64_t* dstep, cudaStream_t st);
 cudaError_t launch_fire_move(const css::DMesh& m, int32_t n, int32_t* face, double* bary, double* vel,
                              const double* force, double* fire_state, css_integrator it, int half, int* status,
                              cudaStream_t st);
+// straightest-walk polylines of npaths paths (see css_trace_geodesics)
+cudaError_t launch_trace(const css::DMesh& m, int64_t npaths, const int32_t* pface, const double* pbary,
+                         const int32_t* src, const double* tan, const double* len, int cap, double* pts,
+                         int32_t* npts, int32_t* end_face, double* end_bary, int* status, cudaStream_t st);
 // batched forms over the sets of a batch: item k belongs to set s with offs[s] <= k < offs[s+1]
 // (offs has nsets + 1 entries on the device; total = offs[nsets])
 cudaError_t launch_batch_bucket(const SetView* sv, const int32_t* offs, int nsets, int64_t total, cudaStream_t st);

@@ -176,7 +176,7 @@ __device__ void through_vertex(const DMesh& m, int& f, int cw, double& px, doubl
 
 // walk from (f, p) by d (face-frame components), carrying nc vectors; false on iteration cap
 __device__ bool face_walk(const DMesh& m, int& f, double& px, double& py, double dx, double dy, int nc, double* cx,
-                          double* cy) {
+                          double* cy, double* rec = nullptr, int rec_cap = 0, int* rec_n = nullptr) {
     int entry = -1;
     for (int it = 0; it < WALK_MAX; ++it) {
         const double L01 = m.lay[3 * f], x2 = m.lay[3 * f + 1], y2 = m.lay[3 * f + 2];
@@ -200,6 +200,13 @@ __device__ bool face_walk(const DMesh& m, int& f, double& px, double& py, double
         double rx = (1.0 - tmin) * dx, ry = (1.0 - tmin) * dy;
         double lh[3];
         lh[2] = hy / y2; lh[1] = (hx - lh[2] * x2) / L01; lh[0] = 1.0 - lh[1] - lh[2];
+        if (rec) {   // the crossing point, world position
+            if (*rec_n < rec_cap) {
+                const double* fr = m.frame + 9 * (size_t)f;
+                for (int a = 0; a < 3; ++a) rec[3 * *rec_n + a] = fr[a] + hx * fr[3 + a] + hy * fr[6 + a];
+            }
+            ++*rec_n;
+        }
         int vc = -1;
         if (lh[k1] < 1e-12) vc = k;
         else if (lh[k] < 1e-12) vc = k1;
@@ -374,6 +381,43 @@ __global__ void k_overdamped(DMesh m, int32_t n, int32_t* face, double* bary, do
 }
 
 __global__ void k_step_inc(int64_t* dstep) { *dstep += 1; }
+
+// ------------------------------------------------------------------ path polylines
+// Path p: the straightest walk from particle src[p] along the world tangent tan[p] for
+// length len[p], recorded as world points (start, each crossing, end; at most cap).
+__global__ void k_trace(DMesh m, int64_t npaths, const int32_t* pface, const double* pbary, const int32_t* src,
+                        const double* tan, const double* len, int cap, double* pts, int32_t* npts,
+                        int32_t* end_face, double* end_bary, int* status) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= npaths) return;
+    const int i = src[p];
+    int f = pface[i];
+    double b[3] = {pbary[3 * (size_t)i], pbary[3 * (size_t)i + 1], pbary[3 * (size_t)i + 2]};
+    double* out = pts + 3 * (size_t)p * cap;
+    double px = b[1] * m.lay[3 * f] + b[2] * m.lay[3 * f + 1], py = b[2] * m.lay[3 * f + 2];
+    if (cap > 0) {
+        const double* fr = m.frame + 9 * (size_t)f;
+        for (int a = 0; a < 3; ++a) out[a] = fr[a] + px * fr[3 + a] + py * fr[6 + a];
+    }
+    double d3[3] = {len[p] * tan[3 * p], len[p] * tan[3 * p + 1], len[p] * tan[3 * p + 2]};
+    double dx, dy;
+    to_face(m, f, d3, dx, dy);
+    int n = 0;
+    const bool ok = face_walk(m, f, px, py, dx, dy, 0, nullptr, nullptr, cap > 1 ? out + 3 : out, cap > 1 ? cap - 1 : 0, &n);
+    if (!ok) atomicOr(status, css::ST_WALK_LIMIT);
+    n += 1;
+    if (n < cap) {
+        const double* fr = m.frame + 9 * (size_t)f;
+        for (int a = 0; a < 3; ++a) out[3 * n + a] = fr[a] + px * fr[3 + a] + py * fr[6 + a];
+    }
+    npts[p] = n + 1;
+    const double L01 = m.lay[3 * f], x2 = m.lay[3 * f + 1], y2 = m.lay[3 * f + 2];
+    double l2 = py / y2, l1 = (px - l2 * x2) / L01, l0 = 1.0 - l1 - l2;
+    l0 = l0 < 0.0 ? 0.0 : l0; l1 = l1 < 0.0 ? 0.0 : l1; l2 = l2 < 0.0 ? 0.0 : l2;
+    const double sb = l0 + l1 + l2;
+    end_face[p] = f;
+    end_bary[3 * p] = l0 / sb; end_bary[3 * p + 1] = l1 / sb; end_bary[3 * p + 2] = l2 / sb;
+}
 
 // ------------------------------------------------------------------ FIRE minimiser
 // Device state of one set: [0] step, [1] alpha, [2] consecutive steps with P > 0,
@@ -602,6 +646,15 @@ cudaError_t launch_fire_move(const DMesh& m, int32_t n, int32_t* face, double* b
     } else {
         k_fire_kick<<<nb(3 * (int64_t)n), 256, 0, st>>>(3 * (int64_t)n, vel, force, fire_state, it.mass);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const DMesh& m, int64_t npaths, const int32_t* pface, const double* pbary,
+                         const int32_t* src, const double* tan, const double* len, int cap, double* pts,
+                         int32_t* npts, int32_t* end_face, double* end_bary, int* status, cudaStream_t st) {
+    if (npaths < 1) return cudaSuccess;
+    k_trace<<<nb(npaths, 128), 128, 0, st>>>(m, npaths, pface, pbary, src, tan, len, cap, pts, npts, end_face,
+                                              end_bary, status);
     return cudaGetLastError();
 }
 

@@ -390,3 +390,39 @@ def test_fire_matches_oracle_and_relaxes(ctx):
     p32.free()
     parts.free()
     mesh.free()
+
+
+@pytest.mark.parametrize("name", ["ico5_n1024", "noisy_ico5_n2048"])
+def test_traced_paths_match_oracle_and_reach_neighbours(ctx, name):
+    """Path polylines: for sampled neighbour pairs (the oracle's tangents and distances) the
+    GPU walk along the pair's tangent for its distance gives the oracle's polyline point by
+    point; on the smooth sphere every
+    path ends on its neighbour (no saddle vertex to bend at), on the noisy sphere most do
+    (75 % of this sample; the rest bend at saddle vertices, which a straight walk does not
+    follow)."""
+    m, face, bary, r_c = WORKLOADS[name]()
+    mesh, parts = _setup(ctx, m, face, bary)
+    om = O.OracleMesh(m)
+    rs, j, d, t = om.neighbors(face, bary, r_c)          # the pairs' tangents and lengths
+    rows = np.repeat(np.arange(len(rs) - 1), np.diff(rs))
+    rng = np.random.default_rng(3)
+    pick = rng.choice(len(j), size=min(200, len(j)), replace=False)
+    paths, ef, eb = css.trace_geodesics(parts, rows[pick], t[pick], d[pick], max_points=512)
+    x = om.world(face, bary)
+    reached = 0
+    for k, q in enumerate(pick):
+        i = int(rows[q])
+        pts, n, f1, b1 = om.trace(int(face[i]), bary[i], d[q] * t[q], cap=512)
+        gp, complete = paths[k]
+        assert complete and len(gp) == len(pts)
+        np.testing.assert_allclose(gp, pts, atol=1e-9)
+        assert ef[k] == f1
+        seg = np.linalg.norm(np.diff(gp, axis=0), axis=1).sum()
+        assert seg == pytest.approx(d[q], rel=1e-9)
+        reached += np.linalg.norm(om.world([ef[k]], [eb[k]])[0] - x[int(j[q])]) < 1e-7
+    if name == "ico5_n1024":
+        assert reached == len(pick)
+    else:
+        assert reached >= 0.6 * len(pick)      # 75 % measured: the rest bend at saddles
+    parts.free()
+    mesh.free()
