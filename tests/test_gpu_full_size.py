@@ -89,6 +89,29 @@ def test_full_size_rows_fp32(workload):
     assert len(g[1]) == len(css.geodesic_neighbors(parts, r_c, css.FP64)[1])
 
 
+def test_full_size_rows_in_the_tuned_shapes(workload, ctx):
+    """The shapes the autotuner picks for these workloads in the benchmark (global tables,
+    32768-window pools, the 128-register variant with 8 warps per CTA, and the first pass
+    with shared tables at scale 4) give the same pairs as the default shape, with distances
+    and tangents equal up to FP32 rounding."""
+    cfg, mesh, parts, om, src = workload
+    r_c = cfg["r_c"]
+    before = ctx.get_launch()
+    ref = css.geodesic_neighbors(parts, r_c, css.FP32)
+    for shape in (dict(warps_per_cta=8, ctas_per_sm=0, tile=1, shared_scale=0, window_capacity=32768,
+                       window_capacity2=16384, warps2_per_sm=2, occupancy=2),
+                  dict(warps_per_cta=2, ctas_per_sm=0, tile=1, shared_scale=4, window_capacity=8192,
+                       window_capacity2=16384, warps2_per_sm=2, occupancy=1)):
+        ctx.set_launch(**shape)
+        g = css.geodesic_neighbors(parts, r_c, css.FP32)
+        assert np.array_equal(g[0], ref[0]) and np.array_equal(g[1], ref[1])
+        # the two register-budget variants are compiled separately, so FP32 roundings (FMA
+        # contraction) may differ in the last bits
+        np.testing.assert_allclose(g[2], ref[2], rtol=1e-6, atol=0)
+        np.testing.assert_allclose(g[3], ref[3], atol=1e-5)
+    ctx.set_launch(**before)
+
+
 def test_full_size_forces(workload):
     """Forces of the sampled particles.  WCA on these overpacked workloads spans many
     decades (overlapping pairs), so each row is held to the error its own pairs allow:
