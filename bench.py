@@ -382,19 +382,18 @@ def run_single(args, cfg, css, ctx, torch, stream, timer, rank, world):
     # ---- end to end through the C ABI with host buffers: upload the state from pinned
     # host memory, one step, read the state back, every step
     parts = css.particles_set(ctx, mesh, cfg["face"], cfg["bary"], cfg["vel"], cfg["orient"], seed=1)
+    # a host-driven loop: every step writes the state held in pinned host memory to the
+    # device, steps, and reads the new state (and forces) back into the same buffers
     hf = torch.from_numpy(np.ascontiguousarray(cfg["face"], np.int32)).pin_memory()
     hb = torch.from_numpy(np.ascontiguousarray(cfg["bary"])).pin_memory()
     hv = torch.from_numpy(np.ascontiguousarray(cfg["vel"] if cfg["vel"] is not None else np.zeros((n, 3)))).pin_memory()
-    of = torch.empty(n, dtype=torch.int32).pin_memory()
-    ob = torch.empty((n, 3), dtype=torch.float64).pin_memory()
-    ov = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     oF = torch.empty((n, 3), dtype=torch.float64).pin_memory()
 
     def e2e_step():
         css.particles_update(parts, hf, hb, hv)
         css.integrate_step(parts, pot, integ, rc, css.FP32, 1)
         pc = ctx.last_counters()["pairs"]
-        css.particles_get_into(parts, of, ob, ov, None, oF)
+        css.particles_get_into(parts, hf, hb, hv, None, oF)
         return pc
     e2e_t, e2e_pairs = e2e_time(torch, stream, e2e_step, args, timer.dist)
     parts.free()
@@ -540,8 +539,6 @@ def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
         host.append((torch.from_numpy(np.ascontiguousarray(it["face"], np.int32)).pin_memory(),
                      torch.from_numpy(np.ascontiguousarray(it["bary"])).pin_memory(),
                      torch.from_numpy(np.ascontiguousarray(it["vel"])).pin_memory(),
-                     torch.empty(k, dtype=torch.int32).pin_memory(), torch.empty((k, 3), dtype=torch.float64).pin_memory(),
-                     torch.empty((k, 3), dtype=torch.float64).pin_memory(),
                      torch.empty((k, 3), dtype=torch.float64).pin_memory()))
 
     def e2e_step():
@@ -550,7 +547,7 @@ def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
         css.batch_step(b, pot, integ, rc, css.FP32, 1)
         pc = ctx.last_counters()["pairs"]
         for p, h in zip(sets, host):
-            css.particles_get_into(p, h[3], h[4], h[5], None, h[6])
+            css.particles_get_into(p, h[0], h[1], h[2], None, h[3])
         return pc
     e2e_t, e2e_pairs = e2e_time(torch, stream, e2e_step, args, timer.dist)
     b.free()

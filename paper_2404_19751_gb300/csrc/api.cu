@@ -542,6 +542,35 @@ int css_particles_update(css_parts* p, const int32_t* face, const double* bary, 
     css_ctx* c = p->ctx;
     cudaStream_t st = c->stream;
     auto kind = [](const void* q) { return is_device_ptr(q) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; };
+    if ((face || bary || vel) && (p->force_valid || p->fire_valid)) {
+        // forces (or a FIRE state) are cached for the current state: stage the upload in the
+        // snapshot buffer, compare it bitwise with the current state, then copy it in; an
+        // upload of an unchanged state (a host loop that writes back what it read) keeps them
+        if (face && !is_device_ptr(face))
+            for (int64_t i = 0; i < p->n; ++i)
+                if (face[i] < 0 || face[i] >= p->mesh->nf) { c->err = "particles_update: face index out of range"; return CSS_ERR_INVALID_ARG; }
+        if (!p->snap) TRY(c, "particles_update", cudaMalloc(&p->snap, p->state_bytes()));
+        const int64_t n = p->n;
+        double* sb = (double*)p->snap;                 // same layout as the state block
+        double* sv = sb + 3 * n;
+        int32_t* sf = (int32_t*)(sb + 12 * n);
+        if (face) TRY(c, "particles_update", cudaMemcpyAsync(sf, face, n * sizeof(int32_t), kind(face), st));
+        if (bary) TRY(c, "particles_update", cudaMemcpyAsync(sb, bary, 3 * n * sizeof(double), kind(bary), st));
+        if (vel) TRY(c, "particles_update", cudaMemcpyAsync(sv, vel, 3 * n * sizeof(double), kind(vel), st));
+        TRY(c, "particles_update", cudaMemsetAsync(c->dscal + 1, 0, sizeof(int), st));
+        TRY(c, "particles_update", cssi::launch_state_diff((int32_t)n, face ? sf : nullptr, p->face, bary ? sb : nullptr,
+                                                           p->bary, vel ? sv : nullptr, p->vel, c->dscal + 1, st));
+        if (face) TRY(c, "particles_update", cudaMemcpyAsync(p->face, sf, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        if (bary) TRY(c, "particles_update", cudaMemcpyAsync(p->bary, sb, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (vel) TRY(c, "particles_update", cudaMemcpyAsync(p->vel, sv, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (orient) TRY(c, "particles_update", cudaMemcpyAsync(p->orient, orient, 3 * n * sizeof(double), kind(orient), st));
+        TRY(c, "particles_update", cudaMemcpyAsync(c->hstat, c->dscal + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(c, "particles_update", cudaStreamSynchronize(st));
+        const int changed = *c->hstat;
+        if (changed & 1) p->force_valid = 0;
+        if (changed & 3) p->fire_valid = 0;
+        return CSS_OK;
+    }
     if (face) {
         if (!is_device_ptr(face))
             for (int64_t i = 0; i < p->n; ++i)

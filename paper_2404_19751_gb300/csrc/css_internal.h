@@ -228,6 +228,9 @@ cudaError_t launch_fire_move(const css::DMesh& m, int32_t n, int32_t* face, doub
 cudaError_t launch_trace(const css::DMesh& m, int64_t npaths, const int32_t* pface, const double* pbary,
                          const int32_t* src, const double* tan, const double* len, int cap, double* pts,
                          int32_t* npts, int32_t* end_face, double* end_bary, int* status, cudaStream_t st);
+// bitwise change of an uploaded state against the current one (flag |= 1 positions, 2 velocities)
+cudaError_t launch_state_diff(int32_t n, const int32_t* nf, const int32_t* of, const double* nb, const double* ob,
+                              const double* nv, const double* ov, int* flag, cudaStream_t st);
 // batched forms over the sets of a batch: item k belongs to set s with offs[s] <= k < offs[s+1]
 // (offs has nsets + 1 entries on the device; total = offs[nsets])
 cudaError_t launch_batch_bucket(const SetView* sv, const int32_t* offs, int nsets, int64_t total, cudaStream_t st);

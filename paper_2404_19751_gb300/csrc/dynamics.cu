@@ -382,6 +382,21 @@ __global__ void k_overdamped(DMesh m, int32_t n, int32_t* face, double* bary, do
 
 __global__ void k_step_inc(int64_t* dstep) { *dstep += 1; }
 
+// bitwise comparison of an uploaded state with the current one: bit 1 = positions (face or
+// barycentrics) differ, bit 2 = velocities differ; arrays the caller did not upload are NULL
+__global__ void k_state_diff(int32_t n, const int32_t* nf, const int32_t* of, const double* nb, const double* ob,
+                             const double* nv, const double* ov, int* flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int d = 0;
+    if (nf && nf[i] != of[i]) d |= 1;
+    for (int a = 0; a < 3; ++a) {
+        if (nb && __double_as_longlong(nb[3 * i + a]) != __double_as_longlong(ob[3 * i + a])) d |= 1;
+        if (nv && __double_as_longlong(nv[3 * i + a]) != __double_as_longlong(ov[3 * i + a])) d |= 2;
+    }
+    if (d) atomicOr(flag, d);
+}
+
 // ------------------------------------------------------------------ path polylines
 // Path p: the straightest walk from particle src[p] along the world tangent tan[p] for
 // length len[p], recorded as world points (start, each crossing, end; at most cap).
@@ -655,6 +670,12 @@ cudaError_t launch_trace(const DMesh& m, int64_t npaths, const int32_t* pface, c
     if (npaths < 1) return cudaSuccess;
     k_trace<<<nb(npaths, 128), 128, 0, st>>>(m, npaths, pface, pbary, src, tan, len, cap, pts, npts, end_face,
                                               end_bary, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_diff(int32_t n, const int32_t* new_f, const int32_t* old_f, const double* new_b,
+                              const double* old_b, const double* new_v, const double* old_v, int* flag, cudaStream_t st) {
+    if (n > 0) k_state_diff<<<nb(n), 256, 0, st>>>(n, new_f, old_f, new_b, old_b, new_v, old_v, flag);
     return cudaGetLastError();
 }
 

@@ -426,3 +426,32 @@ def test_traced_paths_match_oracle_and_reach_neighbours(ctx, name):
         assert reached >= 0.6 * len(pick)      # 75 % measured: the rest bend at saddles
     parts.free()
     mesh.free()
+
+
+def test_state_upload_keeps_or_drops_cached_forces_correctly(ctx):
+    """An upload of the unchanged state (a host loop writing back what it read) keeps the
+    forces cached for it, and a changed one drops them: either way the next NVE step equals
+    the step of a fresh set created from the uploaded state."""
+    cfg = synth.make_config("ico5_n1024")
+    m, face, bary, vel = cfg["mesh"], cfg["face"], cfg["bary"], cfg["vel"]
+    pot, integ, r_c = cfg["pot"], cfg["integ"], cfg["r_c"]
+    mesh, a = _setup(ctx, m, face, bary, vel)
+    css.integrate_step(a, pot, integ, r_c, css.FP64, 2)
+    s = css.particles_get(a)
+    for perturb in (False, True):
+        f1, b1, v1 = s["face"].copy(), s["bary"].copy(), s["vel"].copy()
+        if perturb:                      # move particle 3 a little inside its face
+            b1[3] = 0.9 * b1[3] + 0.1 * np.array([1 / 3, 1 / 3, 1 / 3])
+        css.particles_update(a, f1, b1, v1)
+        css.integrate_step(a, pot, integ, r_c, css.FP64, 1)
+        ra = css.particles_get(a)
+        fresh = css.particles_set(ctx, mesh, f1, b1, v1)
+        css.integrate_step(fresh, pot, integ, r_c, css.FP64, 1)
+        rb = css.particles_get(fresh)
+        fresh.free()
+        assert np.array_equal(ra["face"], rb["face"])
+        np.testing.assert_allclose(ra["bary"], rb["bary"], atol=1e-13)
+        np.testing.assert_allclose(ra["vel"], rb["vel"], atol=1e-12)
+        s = ra
+    a.free()
+    mesh.free()
