@@ -114,9 +114,9 @@ struct WarpSm {
 // live either in shared memory -- plain 32-bit keys, cleared for every source, for patches
 // that fit -- or in the warp's global workspace slice with generation-tagged 64-bit keys;
 // the window pool is always in the global slice.
-template <class R>
+template <class R, bool SH>
 struct Ws {
-    bool shared;
+    static constexpr bool shared = SH;   // keyed tables in shared memory (else global, tagged)
     int32_t* sekey;
     int32_t* svkey;
     int32_t* sfkey;
@@ -160,12 +160,12 @@ __host__ __device__ inline size_t ws_layout(int log_eh, int log_vh, int log_fh, 
     return o;
 }
 
-template <class R>
-__device__ inline Ws<R> ws_bind(const cssi::GeoWs& g, int warp) {
+template <class R, bool SH>
+__device__ inline Ws<R, SH> ws_bind(const cssi::GeoWs& g, int warp) {
     size_t off[13];
     ws_layout<R>(g.log_eh, g.log_vh, g.log_fh, g.wcap, g.fcap, g.emcap, off);
     char* b = g.base + (size_t)warp * g.stride;
-    Ws<R> w;
+    Ws<R, SH> w;
     w.ekey = (unsigned long long*)(b + off[0]);
     w.ehead = (int32_t*)(b + off[1]);
     w.vkey = (unsigned long long*)(b + off[2]);
@@ -182,7 +182,6 @@ __device__ inline Ws<R> ws_bind(const cssi::GeoWs& g, int warp) {
     w.log_eh = g.log_eh; w.log_vh = g.log_vh; w.log_fh = g.log_fh;
     w.wcap = g.wcap; w.fcap = g.fcap; w.emcap = g.emcap;
     w.gen = 0;
-    w.shared = false;
     w.sekey = w.svkey = w.sfkey = nullptr;
     return w;
 }
@@ -206,8 +205,8 @@ __host__ __device__ inline size_t sh_bytes_per_warp(int scale) {
                 (size_t)(1 << SH_LOG_FH) * 4 + (size_t)SH_FCAP * 4 + (size_t)SH_EMCAP * 4);
 }
 
-template <class R>
-__device__ inline void ws_bind_shared(Ws<R>& w, unsigned char* base, int scale) {
+template <class R, bool SH>
+__device__ inline void ws_bind_shared(Ws<R, SH>& w, unsigned char* base, int scale) {
     const int ls = sh_log2(scale);
     const int eh = 1 << (SH_LOG_EH + ls), vh = 1 << (SH_LOG_VH + ls), fh = 1 << (SH_LOG_FH + ls);
     unsigned char* p = base;
@@ -223,7 +222,6 @@ __device__ inline void ws_bind_shared(Ws<R>& w, unsigned char* base, int scale) 
     w.vvid = w.svkey;   // the key is the vertex id
     w.log_eh = SH_LOG_EH + ls; w.log_vh = SH_LOG_VH + ls; w.log_fh = SH_LOG_FH + ls;
     w.fcap = SH_FCAP << ls; w.emcap = SH_EMCAP << ls;
-    w.shared = true;
 }
 
 __device__ __forceinline__ int sh_insert(int32_t* keys, int logcap, int32_t key, bool& claimed) {
@@ -255,35 +253,36 @@ __device__ __forceinline__ int sh_find(const int32_t* keys, int logcap, int32_t 
     return -1;
 }
 
-template <class R>
-__device__ __forceinline__ int ws_eins(Ws<R>& ws, int32_t key, bool& claimed) {
+template <class R, bool SH>
+__device__ __forceinline__ int ws_eins(Ws<R, SH>& ws, int32_t key, bool& claimed) {
     return ws.shared ? sh_insert(ws.sekey, ws.log_eh, key, claimed) : css::ht_insert(ws.ekey, ws.log_eh, ws.gen, key, claimed);
 }
-template <class R>
-__device__ __forceinline__ int ws_efind(const Ws<R>& ws, int32_t key) {
+template <class R, bool SH>
+__device__ __forceinline__ int ws_efind(const Ws<R, SH>& ws, int32_t key) {
     return ws.shared ? sh_find(ws.sekey, ws.log_eh, key) : css::ht_find(ws.ekey, ws.log_eh, ws.gen, key);
 }
-template <class R>
-__device__ __forceinline__ int ws_vins(Ws<R>& ws, int32_t key, bool& claimed) {
+template <class R, bool SH>
+__device__ __forceinline__ int ws_vins(Ws<R, SH>& ws, int32_t key, bool& claimed) {
     return ws.shared ? sh_insert(ws.svkey, ws.log_vh, key, claimed) : css::ht_insert(ws.vkey, ws.log_vh, ws.gen, key, claimed);
 }
-template <class R>
-__device__ __forceinline__ int ws_vfind(const Ws<R>& ws, int32_t key) {
+template <class R, bool SH>
+__device__ __forceinline__ int ws_vfind(const Ws<R, SH>& ws, int32_t key) {
     return ws.shared ? sh_find(ws.svkey, ws.log_vh, key) : css::ht_find(ws.vkey, ws.log_vh, ws.gen, key);
 }
-template <class R>
-__device__ __forceinline__ int ws_fins(Ws<R>& ws, int32_t key, bool& claimed) {
+template <class R, bool SH>
+__device__ __forceinline__ int ws_fins(Ws<R, SH>& ws, int32_t key, bool& claimed) {
     return ws.shared ? sh_insert(ws.sfkey, ws.log_fh, key, claimed) : css::ht_insert(ws.fkey, ws.log_fh, ws.gen, key, claimed);
 }
 
 // forget the previous source's shared tables
-template <class R>
-__device__ __forceinline__ void ws_clear_shared(Ws<R>& ws, int lane) {
-    if (!ws.shared) return;
-    for (int k = lane; k < (1 << ws.log_eh); k += 32) ws.sekey[k] = -1;
-    for (int k = lane; k < (1 << ws.log_vh); k += 32) ws.svkey[k] = -1;
-    for (int k = lane; k < (1 << ws.log_fh); k += 32) ws.sfkey[k] = -1;
-    __syncwarp();
+template <class R, bool SH>
+__device__ __forceinline__ void ws_clear_shared(Ws<R, SH>& ws, int lane) {
+    if constexpr (SH) {
+        for (int k = lane; k < (1 << ws.log_eh); k += 32) ws.sekey[k] = -1;
+        for (int k = lane; k < (1 << ws.log_vh); k += 32) ws.svkey[k] = -1;
+        for (int k = lane; k < (1 << ws.log_fh); k += 32) ws.sfkey[k] = -1;
+        __syncwarp();
+    }
 }
 
 // ------------------------------------------------------------------ window geometry
@@ -555,8 +554,8 @@ __device__ __forceinline__ void ivl_add(Ivl<R>& L, R x0, R x1, bool cover = true
     else if (cover) L.b[MAXP - 1] = x1;
 }
 
-template <class R>
-__device__ __forceinline__ void face_add(Ws<R>& ws, WarpSm& sm, int32_t f) {
+template <class R, bool SH>
+__device__ __forceinline__ void face_add(Ws<R, SH>& ws, WarpSm& sm, int32_t f) {
     bool claimed;
     int s = ws_fins<R>(ws, f, claimed);
     if (s < 0) { atomicOr(&sm.err, css::ST_HASH_OVERFLOW); return; }
@@ -576,8 +575,8 @@ __device__ __forceinline__ int win_alloc(WarpSm& sm, int wcap) {
 
 // queue a window that still has to be unfolded (each window is queued at most once, so
 // the queue never holds more entries than the pool)
-template <class R>
-__device__ __forceinline__ void push_pending(Ws<R>& ws, WarpSm& sm, int id, float key) {
+template <class R, bool SH>
+__device__ __forceinline__ void push_pending(Ws<R, SH>& ws, WarpSm& sm, int id, float key) {
     const int p = atomicAdd(&sm.npend, 1);
     ws.pq[p] = id;
     ws.pk[p] = key;
@@ -737,11 +736,11 @@ __device__ __forceinline__ bool same_family(const Win<R>& a, const Win<R>& b) {
 // Insert candidate window c on its edge (list slot es), intersecting it with every window
 // already on the edge from either side: on each overlap both keep only where they carry
 // the smaller distance.  Executed by one lane per edge.
-template <class R>
-__device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win<R> c, double rc);
+template <class R, bool SH>
+__device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int es, Win<R> c, double rc);
 
-template <class R>
-__device__ __forceinline__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, const Win<R>& c0,
+template <class R, bool SH>
+__device__ __forceinline__ void insert_window(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int es, const Win<R>& c0,
                                               double rc) {
     if (ws.ehead[es] >= 0) { insert_window_general<R>(m, ws, sm, es, c0, rc); return; }
     // first window on this edge: nothing to intersect with
@@ -760,8 +759,8 @@ __device__ __forceinline__ void insert_window(const DMesh& m, Ws<R>& ws, WarpSm&
     face_add(ws, sm, c.he / 3);
 }
 
-template <class R>
-__device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R>& ws, WarpSm& sm, int es, Win<R> c, double rc) {
+template <class R, bool SH>
+__device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int es, Win<R> c, double rc) {
     const double Ld = m.he[c.he].L;
     const R Lr = (R)Ld;
     const R tolw = (R)Tol<R>::w * Lr;
@@ -923,8 +922,8 @@ __device__ __forceinline__ int group_rounds(bool has, int key, int lane, int& ra
     return (int)__reduce_max_sync(CSS_FULL, (unsigned)__popc(grp));
 }
 
-template <class R>
-__device__ __noinline__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, const VCand<R>& c, double rc,
+template <class R, bool SH>
+__device__ __noinline__ void vertex_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, bool has, const VCand<R>& c, double rc,
                              int lane) {
     if (!__any_sync(CSS_FULL, has)) return;
     bool claimed = false;
@@ -965,8 +964,8 @@ __device__ __noinline__ void vertex_round(const DMesh& m, Ws<R>& ws, WarpSm& sm,
     }
 }
 
-template <class R>
-__device__ __noinline__ void child_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, bool has, const Win<R>& c, double rc,
+template <class R, bool SH>
+__device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, bool has, const Win<R>& c, double rc,
                                          int lane) {
     if (!__any_sync(CSS_FULL, has)) return;
     bool claimed = false;
@@ -991,8 +990,8 @@ __device__ __noinline__ void child_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, 
 // candidate a window yields is at least that window's key, so vertices with
 // d(v) <= kmin (the smallest queued key) go now and the others wait.  Returns the number
 // of vertices emitted.
-template <class R>
-__device__ __noinline__ int emit_round(const DMesh& m, Ws<R>& ws, WarpSm& sm, double rc, double kmin, int lane) {
+template <class R, bool SH>
+__device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, double rc, double kmin, int lane) {
     __syncwarp();
     const int ne = min(sm.nemit, ws.emcap);
     if (ne == 0) return 0;
@@ -1105,8 +1104,8 @@ __device__ __forceinline__ double pot_u(const css_potential& p, double l) {
 }
 
 // distance + source tangent (source-face layout) of particle j of face fl
-template <class R>
-__device__ __noinline__ double query(const DMesh& m, const Ws<R>& ws, int f0, R qx, R qy, int fl, const double* bj,
+template <class R, bool SH>
+__device__ __noinline__ double query(const DMesh& m, const Ws<R, SH>& ws, int f0, R qx, R qy, int fl, const double* bj,
                                      R& tx, R& ty) {
     R L01, x2, y2, dummy;
     face_corner_f<R>(m, fl, 1, L01, dummy);
@@ -1206,8 +1205,8 @@ __device__ __noinline__ double query(const DMesh& m, const Ws<R>& ws, int f0, R 
 }
 
 // Smallest and largest queued key.
-template <class R>
-__device__ __forceinline__ void pending_range(const Ws<R>& ws, int npend, int lane, float& kmin, float& kmax) {
+template <class R, bool SH>
+__device__ __forceinline__ void pending_range(const Ws<R, SH>& ws, int npend, int lane, float& kmin, float& kmax) {
     kmin = INFINITY;
     kmax = 0.0f;
     for (int i = lane; i < npend; i += 32) {
@@ -1227,8 +1226,8 @@ __device__ __forceinline__ void pending_range(const Ws<R>& ws, int npend, int la
 // those in queue order are taken and the queue is compacted in place.  Processing in
 // (batched) key order keeps the work close to that of a priority queue: windows that a
 // shorter family would trim are mostly never unfolded.
-template <class R>
-__device__ int select_wave(Ws<R>& ws, WarpSm& sm, int npend, float kmin, float kmax, int lane) {
+template <class R, bool SH>
+__device__ int select_wave(Ws<R, SH>& ws, WarpSm& sm, int npend, float kmin, float kmax, int lane) {
     float T = kmax;
     if (npend > 32) {
         float lo = kmin, hi = kmax;
@@ -1276,8 +1275,8 @@ __device__ int select_wave(Ws<R>& ws, WarpSm& sm, int npend, float kmin, float k
     return mine;
 }
 
-template <class R>
-__device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, int lane, int* status,
+template <class R, bool SH>
+__device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, int lane, int* status,
                            unsigned long long* counters, int item, int32_t* defer_list, int* defer_count) {
     const DMesh& m = J.m;
     const double rc = J.rc;
@@ -1471,7 +1470,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R>& ws, WarpSm& sm, 
 // OCC = CTAs of 256 threads per SM the register budget must allow: 1 gives up to 255
 // registers a thread (fewer resident warps, no spills), 2 caps them at 128 (twice the
 // resident warps, some spills); which is faster depends on the workload.
-template <class R, int OCC>
+template <class R, int OCC, bool SH>
 __global__ void __launch_bounds__(256, OCC) k_geodesic(cssi::GeoJob job0, const cssi::GeoJob* jobs, cssi::GeoQueue q,
                                                   cssi::GeoWs g, int* work, int* status,
                                                   unsigned long long* counters) {
@@ -1481,9 +1480,9 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic(cssi::GeoJob job0, const 
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     if (gw >= g.nwarps) return;
     WarpSm& sm = smem[wib];
-    Ws<R> ws = ws_bind<R>(g, gw);
+    Ws<R, SH> ws = ws_bind<R, SH>(g, gw);
     extern __shared__ __align__(16) unsigned char dsm[];
-    if (g.shared) ws_bind_shared<R>(ws, dsm + (size_t)wib * sh_bytes_per_warp<R>(g.shared), g.shared);
+    if constexpr (SH) ws_bind_shared<R, SH>(ws, dsm + (size_t)wib * sh_bytes_per_warp<R>(g.shared), g.shared);
     uint32_t gen = 0;
     if (lane == 0) gen = g.gen[gw];
     gen = __shfl_sync(CSS_FULL, gen, 0);
@@ -1565,33 +1564,36 @@ cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const GeoQu
                             unsigned long long* counters, cudaStream_t st) {
     const dim3 block(32 * warps_per_cta);
     const size_t sm = geodesic_shared_bytes(precision, warps_per_cta, ws.shared);
-    const bool light = ws.occupancy == 2;
+    // one instantiation per (precision, register budget, table placement)
+    const bool light = ws.occupancy == 2, sh = ws.shared != 0;
+#define CSS_LAUNCH(RT, O, S) k_geodesic<RT, O, S><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters)
     if (precision == CSS_FP32) {
-        if (light) k_geodesic<float, 2><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
-        else k_geodesic<float, 1><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
+        if (light) { if (sh) CSS_LAUNCH(float, 2, true); else CSS_LAUNCH(float, 2, false); }
+        else { if (sh) CSS_LAUNCH(float, 1, true); else CSS_LAUNCH(float, 1, false); }
     } else {
-        if (light) k_geodesic<double, 2><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
-        else k_geodesic<double, 1><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters);
+        if (light) { if (sh) CSS_LAUNCH(double, 2, true); else CSS_LAUNCH(double, 2, false); }
+        else { if (sh) CSS_LAUNCH(double, 1, true); else CSS_LAUNCH(double, 1, false); }
     }
+#undef CSS_LAUNCH
     return cudaGetLastError();
 }
 
 // resident CTAs per SM for a launch shape (0: the shape does not fit an SM)
-template <class R, int OCC>
+template <class R, int OCC, bool SH>
 static int blocks_per_sm(int warps_per_cta, size_t dyn) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_geodesic<R, OCC>) != cudaSuccess) { cudaGetLastError(); return 0; }
+    if (cudaFuncGetAttributes(&fa, k_geodesic<R, OCC, SH>) != cudaSuccess) { cudaGetLastError(); return 0; }
     const int room = optin - (int)fa.sharedSizeBytes;   // dynamic shared memory a CTA may take
     if (dyn > (size_t)room) return 0;
-    if (cudaFuncSetAttribute(k_geodesic<R, OCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, room) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_geodesic<R, OCC, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, room) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<R, OCC>, 32 * warps_per_cta, dyn) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic<R, OCC, SH>, 32 * warps_per_cta, dyn) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -1600,9 +1602,13 @@ static int blocks_per_sm(int warps_per_cta, size_t dyn) {
 
 int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared_scale, int occupancy) {
     const size_t dyn = geodesic_shared_bytes(precision, warps_per_cta, shared_scale);
-    if (occupancy == 2)
-        return precision == CSS_FP32 ? blocks_per_sm<float, 2>(warps_per_cta, dyn) : blocks_per_sm<double, 2>(warps_per_cta, dyn);
-    return precision == CSS_FP32 ? blocks_per_sm<float, 1>(warps_per_cta, dyn) : blocks_per_sm<double, 1>(warps_per_cta, dyn);
+    const bool f32 = precision == CSS_FP32, sh = shared_scale != 0;
+    if (occupancy == 2) {
+        if (sh) return f32 ? blocks_per_sm<float, 2, true>(warps_per_cta, dyn) : blocks_per_sm<double, 2, true>(warps_per_cta, dyn);
+        return f32 ? blocks_per_sm<float, 2, false>(warps_per_cta, dyn) : blocks_per_sm<double, 2, false>(warps_per_cta, dyn);
+    }
+    if (sh) return f32 ? blocks_per_sm<float, 1, true>(warps_per_cta, dyn) : blocks_per_sm<double, 1, true>(warps_per_cta, dyn);
+    return f32 ? blocks_per_sm<float, 1, false>(warps_per_cta, dyn) : blocks_per_sm<double, 1, false>(warps_per_cta, dyn);
 }
 
 cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd,
