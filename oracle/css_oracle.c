@@ -227,6 +227,7 @@ void om_world_position(const om_mesh* m, int32_t f, const double* bary, double* 
 /* ------------------------------------------------------------------ windows (Sec. 2.2, Sec. 3.1) */
 typedef struct {
     int32_t he;          /* half-edge it lies on and propagates into */
+    int32_t pv;          /* its pseudo-source vertex, -1 for the source point itself */
     int8_t alive, processed, fixed;
     double b0, b1;       /* interval along the half-edge, 0 <= b0 < b1 <= L */
     double sx, sy;       /* pseudo-source in the half-edge frame, sy <= 0 */
@@ -240,6 +241,11 @@ typedef struct {
     const om_mesh* m;
     double rc;
     double* d; double* tv; int32_t* vtouch; int64_t nvt;
+    /* how each vertex's distance was reached (path extraction): the previous node of the
+       path (a pseudo-source vertex, -1 = the source), a face holding the vertex and its
+       corner there, the unit direction from the vertex towards that node in the face's
+       layout (it may point into another face of the vertex's ring) and the leg's length */
+    int32_t* par; int32_t* pf; int32_t* pc; double* pdir; double* plen;
     int32_t** el; int32_t* ecnt; int32_t* ecap; int32_t* etouch; int64_t net;
     owin* w; int64_t nw, wcap;
     hent* hp; int64_t nh, hcap;
@@ -253,6 +259,11 @@ static ows* ws_create(const om_mesh* m) {
     for (int64_t v = 0; v < m->nv; ++v) s->d[v] = OM_INF;
     s->tv = (double*)calloc(2 * m->nv, sizeof(double));
     s->vtouch = (int32_t*)malloc(sizeof(int32_t) * m->nv);
+    s->par = (int32_t*)malloc(sizeof(int32_t) * m->nv);
+    s->pf = (int32_t*)malloc(sizeof(int32_t) * m->nv);
+    s->pc = (int32_t*)malloc(sizeof(int32_t) * m->nv);
+    s->pdir = (double*)malloc(sizeof(double) * 2 * m->nv);
+    s->plen = (double*)malloc(sizeof(double) * m->nv);
     s->el = (int32_t**)calloc(m->ne, sizeof(int32_t*));
     s->ecnt = (int32_t*)calloc(m->ne, sizeof(int32_t));
     s->ecap = (int32_t*)calloc(m->ne, sizeof(int32_t));
@@ -270,7 +281,8 @@ static void ws_reset(ows* s) {
 
 static void ws_destroy(ows* s) {
     for (int64_t e = 0; e < s->m->ne; ++e) free(s->el[e]);
-    free(s->d); free(s->tv); free(s->vtouch); free(s->el); free(s->ecnt); free(s->ecap);
+    free(s->d); free(s->tv); free(s->vtouch);
+    free(s->par); free(s->pf); free(s->pc); free(s->pdir); free(s->plen); free(s->el); free(s->ecnt); free(s->ecap);
     free(s->etouch); free(s->w); free(s->hp); free(s);
 }
 
@@ -325,12 +337,58 @@ static int win_degenerate_sees(const om_mesh* m, const owin* w) {
     return w->sx >= w->b0 - tol && w->sx <= w->b1 + tol;
 }
 
-static void set_vertex(ows* s, int32_t v, double dist, double tx, double ty) {
-    if (!(dist < s->d[v])) return;
+/* previous node of a path, as recorded for the path extraction */
+typedef struct { int32_t par, f, k; double dx, dy, len; } olink;
+
+static void set_link(ows* s, int32_t v, const olink* l) {
+    s->par[v] = l->par; s->pf[v] = l->f; s->pc[v] = l->k;
+    s->pdir[2 * v] = l->dx; s->pdir[2 * v + 1] = l->dy; s->plen[v] = l->len;
+}
+
+static void set_vertex(ows* s, int32_t v, double dist, double tx, double ty, const olink* l) {
+    if (!(dist < s->d[v])) {
+        /* an equally short path (up to rounding) that comes straight from the source is
+           preferred as the vertex's previous node: distances and tangents do not change */
+        if (dist <= s->d[v] * (1.0 + 1e-13) && l->par < 0 && s->par[v] >= 0) set_link(s, v, l);
+        return;
+    }
     if (s->d[v] == OM_INF) s->vtouch[s->nvt++] = v;
     s->d[v] = dist;
     s->tv[2 * v] = tx; s->tv[2 * v + 1] = ty;
+    set_link(s, v, l);
     if (s->m->pseudo[v] && dist < s->rc) heap_push(s, dist, 1, v);
+}
+
+/* vector (a, b) of the frame of half-edge 3f+k -> face f's layout */
+static void he_vec_to_layout(const om_mesh* m, int64_t f, int k, double a, double b, double* x, double* y) {
+    double ax, ay, bx, by;
+    face_pt(m, f, k, &ax, &ay);
+    face_pt(m, f, k + 1, &bx, &by);
+    const double L = hypot(bx - ax, by - ay);
+    const double dx = (bx - ax) / L, dy = (by - ay) / L;
+    *x = a * dx - b * dy;
+    *y = a * dy + b * dx;
+}
+
+/* the link of a point (X, Y) of window W's half-edge frame straight back to W's
+   pseudo-source.  which = 2: the far corner of the face W enters (the direction lies in
+   that face); 0 / 1: the start / end vertex of W's edge (the direction points into the
+   face on the other side of the edge, and is written in that face); -1: a point inside
+   the face W enters. */
+static void window_link(const om_mesh* m, const owin* W, double X, double Y, int which, olink* l) {
+    const int64_t f = W->he / 3; const int k = W->he % 3;
+    const double a = W->sx - X, b = W->sy - Y, n = hypot(a, b);
+    l->par = W->pv; l->len = n;
+    const double ua = n > 0.0 ? a / n : 1.0, ub = n > 0.0 ? b / n : 0.0;
+    if (which == 0 || which == 1) {
+        const int32_t tw = m->twin[W->he];
+        const int64_t g = tw / 3; const int kg = tw % 3;   /* tw runs from W's end vertex to its start */
+        l->f = (int32_t)g; l->k = which == 0 ? (kg + 1) % 3 : kg;
+        he_vec_to_layout(m, g, kg, -ua, -ub, &l->dx, &l->dy);
+    } else {
+        l->f = (int32_t)f; l->k = which == 2 ? (k + 2) % 3 : -1;
+        he_vec_to_layout(m, f, k, ua, ub, &l->dx, &l->dy);
+    }
 }
 
 static int32_t new_window(ows* s, const owin* w) {
@@ -500,14 +558,24 @@ static void propagate(ows* s, int32_t wid) {
     const int32_t vu = m->F[3 * f + k], vv = m->F[3 * f + (k + 1) % 3], vc = m->F[3 * f + (k + 2) % 3];
     const double tolv = 1e-12 * L;
     double tx, ty;
-    if (W.b0 <= tolv) { win_tangent(&W, 0.0, 0.0, &tx, &ty); set_vertex(s, vu, W.sigma + hypot(W.sx, W.sy), tx, ty); }
-    if (W.b1 >= L - tolv) { win_tangent(&W, L, 0.0, &tx, &ty); set_vertex(s, vv, W.sigma + hypot(L - W.sx, W.sy), tx, ty); }
+    olink lk;
+    if (W.b0 <= tolv) {
+        win_tangent(&W, 0.0, 0.0, &tx, &ty);
+        window_link(m, &W, 0.0, 0.0, 0, &lk);
+        set_vertex(s, vu, W.sigma + hypot(W.sx, W.sy), tx, ty, &lk);
+    }
+    if (W.b1 >= L - tolv) {
+        win_tangent(&W, L, 0.0, &tx, &ty);
+        window_link(m, &W, L, 0.0, 1, &lk);
+        set_vertex(s, vv, W.sigma + hypot(L - W.sx, W.sy), tx, ty, &lk);
+    }
     const int degen = win_degenerate(m, &W);
     if (degen && !win_degenerate_sees(m, &W)) return;
     const double xc = degen ? 0.5 * (W.b0 + W.b1) : W.sx + (cx - W.sx) * (-W.sy) / (cy - W.sy);
     if (degen || (xc >= W.b0 && xc <= W.b1)) {
         win_tangent(&W, cx, cy, &tx, &ty);
-        set_vertex(s, vc, W.sigma + hypot(cx - W.sx, cy - W.sy), tx, ty);
+        window_link(m, &W, cx, cy, 2, &lk);
+        set_vertex(s, vc, W.sigma + hypot(cx - W.sx, cy - W.sy), tx, ty, &lk);
     }
     const int32_t tl = m->twin[3 * f + (k + 2) % 3];   /* across edge c-u */
     const int32_t tr = m->twin[3 * f + (k + 1) % 3];   /* across edge v-c */
@@ -565,7 +633,7 @@ static void emit_vertex(ows* s, int32_t v) {
         memset(&c, 0, sizeof(c));
         c.he = tw; c.b0 = 0.0; c.b1 = m->hl[tw];
         c.sx = L - m->hcx[hop]; c.sy = -m->hcy[hop];
-        c.sigma = s->d[v]; c.fixed = 1;
+        c.sigma = s->d[v]; c.fixed = 1; c.pv = v;
         c.ta = s->tv[2 * v]; c.tb = s->tv[2 * v + 1];
         insert_window(s, c);
     }
@@ -583,7 +651,8 @@ static void run_source(ows* s, int32_t f0, const double* b) {
         face_pt(m, f0, k, &px, &py);
         double dd = hypot(px - qx, py - qy);
         double tx = dd > 0.0 ? (px - qx) / dd : 1.0, ty = dd > 0.0 ? (py - qy) / dd : 0.0;
-        set_vertex(s, m->F[3 * f0 + k], dd, tx, ty);
+        const olink lk = {-1, f0, k, -tx, -ty, dd};
+        set_vertex(s, m->F[3 * f0 + k], dd, tx, ty, &lk);
     }
     for (int k = 0; k < 3; ++k) {
         const int32_t h = 3 * f0 + k, tw = m->twin[h];
@@ -597,7 +666,7 @@ static void run_source(ows* s, int32_t f0, const double* b) {
         memset(&c, 0, sizeof(c));
         c.he = tw; c.b0 = 0.0; c.b1 = m->hl[tw];
         c.sx = L - hx; c.sy = -hy; if (c.sy > 0.0) c.sy = 0.0;
-        c.sigma = 0.0; c.fixed = 0;
+        c.sigma = 0.0; c.fixed = 0; c.pv = -1;
         c.ta = -dx; c.tb = dy;
         insert_window(s, c);
     }
@@ -635,16 +704,18 @@ static double cand_gap(const ocand* c, double best, double tx, double ty) {
  * the direct segment (same face), windows entering the face whose cone contains the
  * point, and paths through the face's vertices (Sec. 3.1: query the cached structure). */
 static double query_point_c(ows* s, int32_t f0, double qx, double qy, int32_t f, const double* b,
-                            double* tx, double* ty, ocand* cands) {
+                            double* tx, double* ty, ocand* cands, olink* lk) {
     const om_mesh* m = s->m;
     s->st.queries++;
     double px, py;
     bary_to_face(m, f, b, &px, &py);
     double best = OM_INF; *tx = 0.0; *ty = 0.0;
+    olink lb = {-1, f, -1, 1.0, 0.0, 0.0};
     if (f == f0) {
         best = hypot(px - qx, py - qy);
         if (best > 0.0) { *tx = (px - qx) / best; *ty = (py - qy) / best; }
         cand_add(cands, best, *tx, *ty);
+        lb.dx = best > 0.0 ? -*tx : 1.0; lb.dy = best > 0.0 ? -*ty : 0.0; lb.len = best;
     }
     for (int k = 0; k < 3; ++k) {
         const int32_t h = 3 * f + k, e = m->edge[h];
@@ -665,7 +736,11 @@ static double query_point_c(ows* s, int32_t f0, double qx, double qy, int32_t f,
             double ux, uy;
             win_tangent(w, hx, hy, &ux, &uy);
             cand_add(cands, dd, ux, uy);
-            if (dd < best) { best = dd; *tx = ux; *ty = uy; }
+            if (dd < best) {
+                best = dd; *tx = ux; *ty = uy;
+                window_link(m, w, hx, hy, -1, &lb);
+                lb.f = f;
+            }
         }
     }
     for (int k = 0; k < 3; ++k) {
@@ -675,14 +750,20 @@ static double query_point_c(ows* s, int32_t f0, double qx, double qy, int32_t f,
         face_pt(m, f, k, &vx, &vy);
         const double dd = s->d[v] + hypot(px - vx, py - vy);
         cand_add(cands, dd, s->tv[2 * v], s->tv[2 * v + 1]);
-        if (dd < best) { best = dd; *tx = s->tv[2 * v]; *ty = s->tv[2 * v + 1]; }
+        if (dd < best) {
+            best = dd; *tx = s->tv[2 * v]; *ty = s->tv[2 * v + 1];
+            const double n = hypot(vx - px, vy - py);
+            lb.par = v; lb.f = f; lb.k = -1; lb.len = n;
+            lb.dx = n > 0.0 ? (vx - px) / n : 1.0; lb.dy = n > 0.0 ? (vy - py) / n : 0.0;
+        }
     }
+    if (lk) *lk = lb;
     return best;
 }
 
 static double query_point(ows* s, int32_t f0, double qx, double qy, int32_t f, const double* b,
                           double* tx, double* ty) {
-    return query_point_c(s, f0, qx, qy, f, b, tx, ty, NULL);
+    return query_point_c(s, f0, qx, qy, f, b, tx, ty, NULL, NULL);
 }
 
 static void add_stats(om_stats* a, const om_stats* b) {
@@ -766,7 +847,7 @@ int om_neighbors_gap(const om_mesh* m, int64_t n, const int32_t* face, const dou
                 double tx, ty;
                 ocand cands;
                 cands.n = 0;
-                double d = query_point_c(s, face[i], qx, qy, face[j], bary + 3 * j, &tx, &ty, &cands);
+                double d = query_point_c(s, face[i], qx, qy, face[j], bary + 3 * j, &tx, &ty, &cands, NULL);
                 if (!(d < r_c)) continue;
                 buf[c].j = (int32_t)j; buf[c].d = d;
                 buf[c].gap = cand_gap(&cands, d, tx, ty);
@@ -1070,6 +1151,257 @@ int om_trace(const om_mesh* m, int32_t* face, double* bary, const double* disp3,
     ++n;
     *npts = n;
     return 0;
+}
+
+/* ------------------------------------------------------------------ shortest-path polylines (Sec. 2.2) */
+/* A shortest path on the polyhedral surface is a chain of straight legs that meet at
+ * pseudo-source vertices (boundary, flat or saddle).  The window propagation above records
+ * for every vertex the previous node of its path and, at the query, the last node of the
+ * target's path; the path is rebuilt from the target backwards, leg by leg, each leg a
+ * straight walk from its start node along the recorded direction for the recorded length. */
+
+static double corner_angle(const om_mesh* m, int64_t f, int k) {
+    const int64_t h = 3 * f + k;
+    return atan2(m->hcy[h], m->hcx[h]);
+}
+
+/* The face of the ring of the vertex at corner k of face f whose wedge holds the direction
+ * at angle *phi, counted counter-clockwise from the edge P_k -> P_{k+1} (negative: clockwise
+ * of it; beyond the corner angle: past the edge P_k -> P_{k+2}).  Turns face by face around
+ * the vertex; on return f, k and *phi refer to that face, with *phi clamped into its
+ * wedge.  Returns -1 when the direction leaves the ring through a boundary edge. */
+static int ring_locate(const om_mesh* m, int64_t* f, int* k, double* phi) {
+    const double tol = 1e-12;
+    for (int guard = 0; guard < 256; ++guard) {
+        const double a = corner_angle(m, *f, *k);
+        if (*phi < -tol) {
+            const int32_t tw = m->twin[3 * *f + *k];              /* across P_k -> P_{k+1} */
+            if (tw < 0) return -1;
+            *f = tw / 3; *k = (tw % 3 + 1) % 3;
+            *phi += corner_angle(m, *f, *k);
+        } else if (*phi > a + tol) {
+            const int32_t tw = m->twin[3 * *f + (*k + 2) % 3];    /* across P_{k+2} -> P_k */
+            if (tw < 0) return -1;
+            *phi -= a;
+            *f = tw / 3; *k = tw % 3;
+        } else {
+            if (*phi < 0.0) *phi = 0.0;
+            if (*phi > a) *phi = a;
+            return 0;
+        }
+    }
+    return -1;
+}
+
+/* unit direction at angle phi from the edge P_k -> P_{k+1} of face f */
+static void corner_dir(const om_mesh* m, int64_t f, int k, double phi, double* dx, double* dy) {
+    double ax, ay, bx, by;
+    face_pt(m, f, k, &ax, &ay);
+    face_pt(m, f, k + 1, &bx, &by);
+    const double L = hypot(bx - ax, by - ay);
+    double ex = (bx - ax) / L, ey = (by - ay) / L;
+    rot2(cos(phi), sin(phi), &ex, &ey);
+    *dx = ex; *dy = ey;
+}
+
+/* A leg meets a vertex on its way: it goes on straight, i.e. at angle pi from the reversed
+ * incoming direction, counted counter-clockwise around the ring if the ring holds that
+ * angle on that side, else clockwise (a boundary vertex holds it on one side only). */
+static int vertex_pass(const om_mesh* m, int64_t* f, int* k, double* dx, double* dy) {
+    double ax, ay, bx, by;
+    face_pt(m, *f, *k, &ax, &ay);
+    face_pt(m, *f, *k + 1, &bx, &by);
+    const double L = hypot(bx - ax, by - ay);
+    const double ex = (bx - ax) / L, ey = (by - ay) / L;
+    double beta = atan2(cross2(ex, ey, -*dx, -*dy), dot2(ex, ey, -*dx, -*dy));
+    const double a = corner_angle(m, *f, *k);
+    if (beta < 0.0) beta = 0.0;
+    if (beta > a) beta = a;
+    int64_t g = *f; int kg = *k;
+    double phi = beta + OM_PI;
+    if (ring_locate(m, &g, &kg, &phi) < 0) {
+        g = *f; kg = *k; phi = beta - OM_PI;
+        if (ring_locate(m, &g, &kg, &phi) < 0) return -1;
+    }
+    *f = g; *k = kg;
+    corner_dir(m, g, kg, phi, dx, dy);
+    return 0;
+}
+
+/* Straight walk of one leg: from corner kc of face f (kc >= 0; the unit direction (dx, dy)
+ * of f's layout may point into any face of the vertex's ring) or from the point (px, py) of
+ * f (kc < 0), for length len.  Every edge or vertex crossed before the end is written to
+ * rec (world positions, at most cap, *nrec counts all); the end point is returned as face
+ * *fend and layout point (*ex, *ey).  A crossing within 1e-12 of the leg's end is the end. */
+static int leg_walk(const om_mesh* m, int64_t f, int kc, double px, double py, double dx, double dy, double len,
+                    double* rec, int cap, int* nrec, int64_t* fend, double* ex, double* ey) {
+    int corner = kc;
+    if (corner < 0) {   /* a start point on a corner of its face starts from that vertex */
+        double l[3];
+        bary_of(m, f, px, py, l);
+        for (int c = 0; c < 3; ++c)
+            if (l[c] > 1.0 - 1e-12) corner = c;
+    }
+    if (corner >= 0) {
+        double ax, ay, bx, by;
+        face_pt(m, f, corner, &ax, &ay);
+        face_pt(m, f, corner + 1, &bx, &by);
+        const double L = hypot(bx - ax, by - ay);
+        const double ux = (bx - ax) / L, uy = (by - ay) / L;
+        double phi = atan2(cross2(ux, uy, dx, dy), dot2(ux, uy, dx, dy));
+        if (ring_locate(m, &f, &corner, &phi) < 0) return -3;
+        corner_dir(m, f, corner, phi, &dx, &dy);
+        face_pt(m, f, corner, &px, &py);
+    }
+    double rem = len;
+    int entry = -1;
+    const double tolb = 1e-12;
+    int it;
+    for (it = 0; it < 1000000; ++it) {
+        double l[3], dl[3];
+        bary_of(m, f, px, py, l);
+        const double Dx = dx * rem, Dy = dy * rem;
+        const double L01 = m->lay[3 * f], x2 = m->lay[3 * f + 1], y2 = m->lay[3 * f + 2];
+        dl[2] = Dy / y2; dl[1] = (Dx - dl[2] * x2) / L01; dl[0] = -dl[1] - dl[2];
+        double tmin = OM_INF; int imin = -1;
+        for (int i = 0; i < 3; ++i) {
+            if (corner >= 0 && i != corner) continue;   /* from a corner: only the far edge */
+            if (!(dl[i] < 0.0)) continue;
+            if ((i + 1) % 3 == entry) continue;
+            double t = -l[i] / dl[i];
+            if (t < 0.0) t = 0.0;
+            if (t < tmin) { tmin = t; imin = i; }
+        }
+        if (!(tmin < 1.0 - 1e-12)) { px += Dx; py += Dy; break; }
+        const int k = (imin + 1) % 3;
+        const double hx = px + tmin * Dx, hy = py + tmin * Dy;
+        rem *= (1.0 - tmin);
+        double lh[3];
+        bary_of(m, f, hx, hy, lh);
+        int vcorner = -1;
+        if (lh[(k + 1) % 3] < tolb) vcorner = k;
+        else if (lh[k] < tolb) vcorner = (k + 1) % 3;
+        if (rec && *nrec < cap) {
+            double w[3];
+            if (vcorner >= 0) { double vx, vy; face_pt(m, f, vcorner, &vx, &vy); face_to_world_vec(m, f, vx, vy, w); }
+            else face_to_world_vec(m, f, hx, hy, w);
+            for (int c = 0; c < 3; ++c) rec[3 * *nrec + c] = m->frame[9 * f + c] + w[c];
+        }
+        if (rec) ++*nrec;
+        if (vcorner >= 0) {
+            int kk = vcorner;
+            if (vertex_pass(m, &f, &kk, &dx, &dy) < 0) return -4;
+            corner = kk;
+            face_pt(m, f, corner, &px, &py);
+            entry = -1;
+            continue;
+        }
+        const int32_t h = (int32_t)(3 * f + k), tw = m->twin[h];
+        if (tw < 0) return -5;    /* a shortest path never crosses the boundary */
+        double ax, ay, bx, by;
+        face_pt(m, f, k, &ax, &ay); face_pt(m, f, k + 1, &bx, &by);
+        const double L = hypot(bx - ax, by - ay);
+        const double ux = (bx - ax) / L, uy = (by - ay) / L;
+        const int64_t g = tw / 3; const int k2 = tw % 3;
+        double qax, qay, qbx, qby;
+        face_pt(m, g, k2 + 1, &qax, &qay); face_pt(m, g, k2, &qbx, &qby);
+        const double Lg = hypot(qbx - qax, qby - qay);
+        const double vx = (qbx - qax) / Lg, vy = (qby - qay) / Lg;
+        const double co = dot2(ux, uy, vx, vy), si = cross2(ux, uy, vx, vy);
+        double ox = hx - ax, oy = hy - ay;
+        rot2(co, si, &ox, &oy);
+        px = qax + ox; py = qay + oy;
+        rot2(co, si, &dx, &dy);
+        f = g; entry = k2; corner = -1;
+    }
+    if (it >= 1000000) return -2;
+    *fend = f; *ex = px; *ey = py;
+    return 0;
+}
+
+static void layout_world(const om_mesh* m, int64_t f, double x, double y, double* out3) {
+    double w[3];
+    face_to_world_vec(m, f, x, y, w);
+    for (int c = 0; c < 3; ++c) out3[c] = m->frame[9 * f + c] + w[c];
+}
+
+static void wrap_world(const om_mesh* m, double* p) {
+    if (m->periodic)
+        for (int a = 0; a < 2; ++a) p[a] -= m->per[a] * floor(p[a] / m->per[a]);
+}
+
+#define OM_MAXLEGS 64
+
+int om_geodesic_paths(const om_mesh* m, int64_t n, const int32_t* face, const double* bary, double r_c,
+                      int64_t np, const int32_t* src, const int32_t* dst, int cap, double* pts, int32_t* npts,
+                      int32_t* nlegs, double* dist, double* gap) {
+    ows* s = ws_create(m);
+    s->rc = r_c;
+    int32_t cur = -1;
+    double* buf = (double*)malloc(sizeof(double) * 3 * (size_t)(cap > 0 ? cap : 1));
+    int rc_all = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        const int32_t i = src[p], j = dst[p];
+        npts[p] = 0; nlegs[p] = 0; dist[p] = OM_INF; gap[p] = 0.0;
+        if (i < 0 || i >= n || j < 0 || j >= n || i == j) { rc_all = -1; continue; }
+        if (i != cur) { run_source(s, face[i], bary + 3 * (int64_t)i); cur = i; }
+        double qx, qy, tx, ty;
+        bary_to_face(m, face[i], bary + 3 * (int64_t)i, &qx, &qy);
+        olink lk;
+        const double d = query_point_c(s, face[i], qx, qy, face[j], bary + 3 * (int64_t)j, &tx, &ty, NULL, &lk);
+        if (!(d < r_c)) continue;
+        dist[p] = d;
+        /* walk back from the target: its leg, then each node's leg until the source */
+        int nb = 0, legs = 0;
+        double e[3];
+        om_world_position(m, face[j], bary + 3 * (int64_t)j, e);
+        if (nb < cap) memcpy(buf + 3 * nb, e, sizeof(e));
+        ++nb;
+        double sx, sy;
+        bary_to_face(m, face[j], bary + 3 * (int64_t)j, &sx, &sy);
+        int64_t f = face[j]; int kc = -1;
+        double g = 0.0;
+        for (;;) {
+            if (legs >= OM_MAXLEGS) { rc_all = -6; break; }
+            int nrec = 0;
+            int64_t fe; double ex, ey;
+            const int w = leg_walk(m, f, kc, sx, sy, lk.dx, lk.dy, lk.len, buf + 3 * (nb < cap ? nb : 0),
+                                   nb < cap ? cap - nb : 0, &nrec, &fe, &ex, &ey);
+            if (w < 0) { rc_all = w; break; }
+            for (int r = 0; r < nrec && nb + r < cap; ++r) wrap_world(m, buf + 3 * (nb + r));
+            nb += nrec;
+            ++legs;
+            /* where the leg should have ended: the next node */
+            double node[3], end[3];
+            layout_world(m, fe, ex, ey, end);
+            if (lk.par < 0) om_world_position(m, face[i], bary + 3 * (int64_t)i, node);
+            else {
+                const int32_t v = lk.par;
+                double vx, vy;
+                face_pt(m, s->pf[v], s->pc[v], &vx, &vy);
+                layout_world(m, s->pf[v], vx, vy, node);
+            }
+            double dd[3] = {end[0] - node[0], end[1] - node[1], end[2] - node[2]};
+            min_image(m, dd);
+            const double gl = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+            if (gl > g) g = gl;
+            wrap_world(m, node);
+            if (nb < cap) memcpy(buf + 3 * nb, node, sizeof(node));
+            ++nb;
+            if (lk.par < 0) break;
+            const int32_t v = lk.par;
+            f = s->pf[v]; kc = s->pc[v];
+            lk.par = s->par[v]; lk.dx = s->pdir[2 * v]; lk.dy = s->pdir[2 * v + 1]; lk.len = s->plen[v];
+        }
+        /* source first */
+        const int kept = nb < cap ? nb : cap;
+        for (int r = 0; r < kept; ++r)
+            for (int c = 0; c < 3; ++c) pts[3 * ((int64_t)p * cap + r) + c] = buf[3 * (kept - 1 - r) + c];
+        npts[p] = nb; nlegs[p] = legs; gap[p] = g;
+    }
+    free(buf);
+    ws_destroy(s);
+    return rc_all;
 }
 
 /* ------------------------------------------------------------------ Philox4x32-10 (Salmon et al.) */

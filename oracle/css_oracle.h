@@ -107,6 +107,17 @@ int om_shift(const om_mesh* m, int32_t* face, double* bary, const double* disp3,
 int om_trace(const om_mesh* m, int32_t* face, double* bary, const double* disp3, int cap, double* pts,
              int* npts);
 
+/* Shortest paths of np pairs (src[p] -> dst[p]) as polylines (Sec. 2.2: straight legs in
+ * the unfolding that meet at pseudo-source vertices), rebuilt from the links the window
+ * propagation records: the source point, every edge crossing and bend vertex, the target
+ * (world positions, wrapped into the period on periodic meshes; at most cap points per
+ * pair in pts[p*cap*3 ...], npts[p] = all of them, 0 when l >= r_c).  nlegs[p] = straight
+ * legs, dist[p] = l, gap[p] = the largest distance between a leg walk's end and the node
+ * it must reach.  Pairs sorted by src reuse one propagation. */
+int om_geodesic_paths(const om_mesh* m, int64_t n, const int32_t* face, const double* bary, double r_c,
+                      int64_t np, const int32_t* src, const int32_t* dst, int cap, double* pts, int32_t* npts,
+                      int32_t* nlegs, double* dist, double* gap);
+
 /* nsteps of the chosen dynamics.  vel used by NVE, orient by ABP, force in/out (the
  * force at the current positions must be valid on entry for NVE).  noise: NULL, or
  * nsteps*n*2 standard normals used instead of the Philox stream. */

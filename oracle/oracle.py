@@ -51,6 +51,9 @@ def lib():
         L.om_integrate.restype = C.c_int
         L.om_trace.argtypes = [P, P, P, P, C.c_int, P, P]
         L.om_trace.restype = C.c_int
+        L.om_geodesic_paths.argtypes = [P, C.c_int64, P, P, C.c_double, C.c_int64, P, P, C.c_int, P, P, P, P,
+                                        P]
+        L.om_geodesic_paths.restype = C.c_int
         L.om_fire.argtypes = [P, C.c_int64, P, P, P, P, P, P, C.c_double, C.c_int64, P, P, C.c_int]
         L.om_fire.restype = C.c_int
         L.om_philox4x32_10.argtypes = [P, P, P]
@@ -287,6 +290,26 @@ class OracleMesh:
         if rc != 0:
             raise ValueError(f"oracle trace failed ({rc})")
         return pts[:min(n.value, cap)].copy(), n.value, f.value, b
+
+    def geodesic_paths(self, face, bary, r_c: float, src, dst, cap: int = 512):
+        """Shortest-path polylines of the pairs src[p] -> dst[p] (source first).  Returns
+        (list of (npts, 3) arrays, empty when l >= r_c; legs; l; largest leg landing gap)."""
+        face = _i32(face)
+        bary = _f64(bary)
+        src, dst = _i32(src), _i32(dst)
+        np_ = src.shape[0]
+        pts = np.zeros((np_, cap, 3))
+        npts = np.zeros(np_, np.int32)
+        legs = np.zeros(np_, np.int32)
+        dist = np.zeros(np_)
+        gap = np.zeros(np_)
+        rc = lib().om_geodesic_paths(self.h, face.shape[0], _p(face), _p(bary), float(r_c), np_, _p(src), _p(dst),
+                                     int(cap), _p(pts), _p(npts), _p(legs), _p(dist), _p(gap))
+        if rc != 0:
+            raise ValueError(f"oracle path extraction failed ({rc})")
+        if np.any(npts > cap):
+            raise ValueError("polyline longer than cap points")
+        return [pts[p, :npts[p]].copy() for p in range(np_)], legs, dist, gap
 
     def fire(self, face, bary, vel, force, pot: dict, integ: dict, r_c: float, nsteps: int, state=None,
              nthreads: int = 0):

@@ -56,6 +56,21 @@ def grid_plane(nx: int = 21, ny: int = 21, x0=0.0, x1=1.0, y0=0.0, y1=1.0,
     return _mk(verts, faces, name=f"plane{nx}x{ny}")
 
 
+def holed_plane(n: int = 21, hole=(0.4, 0.6, 0.4, 0.6)) -> Mesh:
+    """The open flat unit square of ``grid_plane(n, n)`` with the grid cells inside the
+    rectangle hole = (x0, x1, y0, y1) removed (a square hole whose sides lie on grid
+    lines), unused vertices dropped.  Shortest paths on it wrap around the hole's corners."""
+    g = grid_plane(n, n)
+    x0, x1, y0, y1 = hole
+    c = g.verts[g.faces].mean(axis=1)
+    keep = ~((c[:, 0] > x0) & (c[:, 0] < x1) & (c[:, 1] > y0) & (c[:, 1] < y1))
+    faces = g.faces[keep]
+    used = np.unique(faces)
+    remap = -np.ones(g.nv, np.int64)
+    remap[used] = np.arange(used.size)
+    return _mk(g.verts[used], remap[faces], name=f"holed_plane{n}")
+
+
 def cylinder_tube(n_around: int = 12, n_along: int = 6, radius: float = 1.0,
                   height: float = 2.0) -> Mesh:
     """Open prism tube (n_around-gon cross-section) of the given height, outward normals."""

@@ -346,3 +346,129 @@ def test_trace_on_a_tube_is_the_unrolled_line():
     dz = np.diff(pts[:, 2])
     # straight in the unrolled strip: equal height gain per unit of unrolled length
     assert np.allclose(dz / np.maximum(seg, 1e-300), dz[0] / seg[0], atol=1e-9) or np.all(np.abs(dz) < 1e-15)
+
+
+def _point_to_polyline(p, Q):
+    """distance from point p to the polyline through the points Q"""
+    best = math.inf
+    for a, b in zip(Q[:-1], Q[1:]):
+        ab = b - a
+        t = np.clip(np.dot(p - a, ab) / np.dot(ab, ab), 0.0, 1.0)
+        best = min(best, float(np.linalg.norm(p - (a + t * ab))))
+    return best
+
+
+def _taut_string(S, E, lo, hi):
+    """Shortest path from S to E in the plane around the open square (lo, hi)^2: the
+    shortest path in the visibility graph of S, E and the square's corners (the textbook
+    construction for Euclidean shortest paths among polygonal obstacles).  A segment is
+    visible if no part of positive length lies inside the open square (Liang-Barsky clip)."""
+    corners = [np.array([lo, lo, 0.0]), np.array([lo, hi, 0.0]), np.array([hi, hi, 0.0]), np.array([hi, lo, 0.0])]
+    nodes = [S] + corners + [E]
+
+    def visible(P, Q):
+        t0, t1 = 0.0, 1.0
+        for a in range(2):
+            d = Q[a] - P[a]
+            if abs(d) < 1e-300:
+                if not (lo < P[a] < hi):
+                    return True
+                continue
+            u0, u1 = sorted(((lo - P[a]) / d, (hi - P[a]) / d))
+            t0, t1 = max(t0, u0), min(t1, u1)
+        return t1 - t0 <= 1e-12
+
+    n = len(nodes)
+    dist = [math.inf] * n
+    prev = [-1] * n
+    dist[0] = 0.0
+    done = [False] * n
+    for _ in range(n):
+        u = min((k for k in range(n) if not done[k]), key=lambda k: dist[k])
+        done[u] = True
+        for v in range(n):
+            if not done[v] and visible(nodes[u], nodes[v]):
+                w = dist[u] + float(np.linalg.norm(nodes[v] - nodes[u]))
+                if w < dist[v]:
+                    dist[v], prev[v] = w, u
+    chain, k = [], n - 1
+    while k >= 0:
+        chain.append(nodes[k])
+        k = prev[k]
+    return np.array(chain[::-1]), dist[-1]
+
+
+def test_paths_around_a_square_hole_are_the_taut_strings():
+    """On a flat sheet with a square hole the shortest path is the taut string around the
+    hole (Sec. 2.2: it bends at boundary vertices only).  Checks the distance against the
+    visibility-graph shortest path, every polyline point on that string, its wrapped corners
+    among the points, the polyline length, and that each leg lands on its node."""
+    m = synth.holed_plane(21, (0.4, 0.6, 0.4, 0.6))
+    om = O.OracleMesh(m)
+    ends = [((0.43, 0.31), (0.47, 0.78)),     # two bends, left of the hole
+            ((0.31, 0.52), (0.57, 0.71)),     # one bend at the upper left corner
+            ((0.71, 0.47), (0.37, 0.64)),     # one bend at the upper right corner
+            ((0.72, 0.33), (0.27, 0.69)),     # two bends, along the top side or the bottom side
+            ((0.62, 0.33), (0.66, 0.62))]     # in sight of each other: straight
+    bends = []
+    for s, e in ends:
+        fs, bs = _locate_xy(m, *s)
+        fe, be = _locate_xy(m, *e)
+        face, bary = np.concatenate([fs, fe]), np.concatenate([bs, be])
+        S, E = np.array(s + (0.0,)), np.array(e + (0.0,))
+        Q, L = _taut_string(S, E, 0.4, 0.6)
+        paths, legs, dist, gap = om.geodesic_paths(face, bary, math.inf, [0], [1])
+        assert dist[0] == pytest.approx(L, rel=1e-13, abs=1e-15)
+        P = paths[0]
+        np.testing.assert_allclose(P[0], S, atol=1e-14)
+        np.testing.assert_allclose(P[-1], E, atol=1e-14)
+        assert max(_point_to_polyline(p, Q) for p in P) < 1e-13
+        for c in Q[1:-1]:
+            assert np.min(np.linalg.norm(P - c, axis=1)) < 1e-13
+        assert np.sum(np.linalg.norm(np.diff(P, axis=0), axis=1)) == pytest.approx(L, rel=1e-13)
+        assert legs[0] >= len(Q) - 1 and gap[0] < 1e-13
+        bends.append(len(Q) - 2)
+    assert sorted(set(bends)) == [0, 1, 2]
+
+
+def test_straight_paths_are_the_straightest_walk():
+    """A path with one leg (no bend) is the straightest walk from the source along the
+    pair's tangent for the pair's distance (Sec. 3.2): the same points as the face walk
+    that moves particles, which is a separate routine."""
+    cfg = synth.make_config("ico5_n1024")
+    m, face, bary, r_c = cfg["mesh"], cfg["face"], cfg["bary"], cfg["r_c"]
+    om = O.OracleMesh(m)
+    src = np.array([3, 400, 777])
+    rs, j, d, t = om.neighbors(face, bary, r_c, sources=src)[:4]
+    S = np.repeat(src, np.diff(rs)).astype(np.int32)
+    paths, legs, dist, gap = om.geodesic_paths(face, bary, r_c, S, j)
+    assert np.all(legs == 1) and len(S) > 10
+    np.testing.assert_allclose(dist, d, rtol=0, atol=0)
+    for p in range(len(S)):
+        pts, n, _, _ = om.trace(int(face[S[p]]), bary[S[p]], d[p] * t[p])
+        assert len(pts) == len(paths[p])
+        np.testing.assert_allclose(paths[p], pts, atol=1e-12)
+
+
+def test_bent_paths_on_a_noisy_sphere_land_on_their_nodes():
+    """On a noisy sphere many shortest paths bend at saddle vertices.  Every leg, walked
+    straight from its node along the recorded direction for the recorded length, ends on
+    the next node; the polyline (consecutive points share a face) is as long as the
+    distance, starts at the source and ends at the neighbour."""
+    m = synth.icosphere(4, 1.0, noise=0.04, seed=7)
+    om = O.OracleMesh(m)
+    face, bary = synth.place_uniform(m, 200, 8)
+    r_c = 0.5
+    src = np.arange(0, 200, 20)
+    rs, j, d = om.neighbors(face, bary, r_c, sources=src)[:3]
+    S = np.repeat(src, np.diff(rs)).astype(np.int32)
+    paths, legs, dist, gap = om.geodesic_paths(face, bary, r_c, S, j, cap=4096)
+    np.testing.assert_array_equal(dist, d)
+    assert np.sum(legs >= 2) > 10            # the sample holds bent paths
+    assert np.max(gap) < 1e-12
+    x = om.world(face, bary)
+    for p in range(len(S)):
+        P = paths[p]
+        np.testing.assert_allclose(P[0], x[S[p]], atol=1e-13)
+        np.testing.assert_allclose(P[-1], x[j[p]], atol=1e-13)
+        assert np.sum(np.linalg.norm(np.diff(P, axis=0), axis=1)) == pytest.approx(d[p], rel=1e-12)
