@@ -198,6 +198,33 @@ int css_trace_geodesics(css_parts* parts, int64_t n_paths, const int32_t* src, c
                         const double* length, int32_t max_points, double* points, int32_t* n_points,
                         int32_t* end_face, double* end_bary);
 
+/* css_geodesic_paths (Sec. 2.2): the shortest path of each pair src[k] -> dst[k] as a
+ * polyline, bends included.  A shortest path on the polyhedral surface is a chain of
+ * straight legs (straight in the unfolding of the faces they cross) that meet at
+ * pseudo-source vertices (boundary, flat or saddle vertices, where the window
+ * propagation starts new windows).  This call runs the FP64 neighbour kernel for the
+ * distinct sources with link recording: every vertex's table entry keeps the previous
+ * node of its path (a pseudo-source vertex or the source), the direction towards it and
+ * the leg's length, and every pair gets its chain of legs from the target back to the
+ * source; each leg is then walked straight across the faces it crosses, passing straight
+ * (angle pi on the side that holds it) through any vertex it meets on the way.
+ *   points   n_pairs x max_points x 3 world positions (wrapped into the period on periodic
+ *            meshes): the source particle, every edge or vertex crossing and every bend
+ *            vertex in order, the target particle; unused entries are zero; max_points >= 2;
+ *   n_points all points of each path (more than max_points: truncated, call again with
+ *            more); 0 when l >= r_c;
+ *   n_legs   straight legs of each path (1: no bend), 0 when l >= r_c;
+ *   dist     l (INFINITY when l >= r_c);
+ *   gap      the largest distance between where a leg's walk ends and the node it must
+ *            reach (a check of the result; rounding size).
+ * r_c may be INFINITY.  Inputs and outputs may be host or device pointers.  Allocates
+ * temporaries and synchronises.  CSS_ERR_INVALID_ARG for an index out of range or
+ * src[k] == dst[k]; CSS_ERR_QUEUE_OVERFLOW when the window pool cannot grow enough;
+ * CSS_ERR_ITER_LIMIT when a path has more than 32 legs or a leg walk fails. */
+int css_geodesic_paths(css_parts* parts, double r_c, int64_t n_pairs, const int32_t* src, const int32_t* dst,
+                       int32_t max_points, double* points, int32_t* n_points, int32_t* n_legs, double* dist,
+                       double* gap);
+
 /* ---------------------------------------------------------------- batched form
  * Many independent particle sets (each on its own mesh) advanced together: the
  * neighbour/force work of all sets runs in one persistent launch per step whose

@@ -28,7 +28,7 @@ SYMBOLS = ("css_create", "css_destroy", "css_last_error", "css_last_counters", "
            "css_particles_get", "css_particles_free", "css_geodesic_neighbors", "css_compute_forces",
            "css_integrate_step", "css_batch_create", "css_batch_step", "css_batch_free",
            "css_last_kernel_ms", "css_fma_peak", "css_particles_update", "css_get_launch", "css_autotune",
-           "css_trace_geodesics")
+           "css_trace_geodesics", "css_geodesic_paths")
 
 
 class CssError(RuntimeError):
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
         "css_get_launch": [P, P],
         "css_autotune": [P, P, I32, P, D, C.c_int, I32, I64, P, C.POINTER(D)],
         "css_trace_geodesics": [P, I64, P, P, P, I32, P, P, P, P],
+        "css_geodesic_paths": [P, D, I64, P, P, I32, P, P, P, P, P],
         "css_mesh_upload": [P, P, I64, P, I64, P, C.POINTER(C.c_void_p)],
         "css_mesh_free": [P],
         "css_mesh_counts": [P, P],
@@ -304,6 +305,26 @@ def trace_geodesics(parts: Particles, src, tangent, length, max_points: int = 25
                                                ef.ctypes.data, eb.ctypes.data))
     paths = [(pts[k, :min(npts[k], max_points)].copy(), bool(npts[k] <= max_points)) for k in range(n)]
     return paths, ef[:n], eb[:n]
+
+
+def geodesic_paths(parts: Particles, r_c: float, src, dst, max_points: int = 512):
+    """Shortest-path polylines of the pairs src[k] -> dst[k], bends included (see
+    css_geodesic_paths): returns (list of (k x 3) point arrays, source first, empty when
+    l >= r_c; legs; distances; largest leg landing gap)."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    n = src.shape[0]
+    pts = np.zeros((max(n, 1), max_points, 3))
+    npts = np.zeros(max(n, 1), np.int32)
+    legs = np.zeros(max(n, 1), np.int32)
+    dist = np.zeros(max(n, 1))
+    gap = np.zeros(max(n, 1))
+    parts.ctx.check(load().css_geodesic_paths(parts.h, float(r_c), n, src.ctypes.data, dst.ctypes.data,
+                                              int(max_points), pts.ctypes.data, npts.ctypes.data, legs.ctypes.data,
+                                              dist.ctypes.data, gap.ctypes.data))
+    if np.any(npts[:n] > max_points):
+        raise ValueError("a polyline has more than max_points points")
+    return [pts[k, :npts[k]].copy() for k in range(n)], legs[:n], dist[:n], gap[:n]
 
 
 def _pot(p) -> Potential:

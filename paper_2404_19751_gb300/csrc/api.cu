@@ -1183,3 +1183,241 @@ int css_trace_geodesics(css_parts* p, int64_t n_paths, const int32_t* src, const
     if (*c->hstat) return status_error(c, *c->hstat);
     return CSS_OK;
 }
+
+// ------------------------------------------------------------------ shortest-path polylines
+namespace {
+
+constexpr int PATH_MAX_LEGS = 32;
+
+// device scratch of one path extraction, freed on every exit
+struct PathBufs {
+    std::vector<void*> ptrs;
+    template <class T>
+    cudaError_t alloc(T** p, size_t n) {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(T));
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    ~PathBufs() { for (void* q : ptrs) cudaFree(q); }
+};
+
+// One launch of the path instantiation of the neighbour kernel over the distinct sources
+// (us, on the device as dus): rows in the set's pair slab, legs per (rank in us, row slot).
+int run_path_kernel(css_parts* p, double rc, const std::vector<int32_t>& us, const int32_t* dus, int win_cap,
+                    int32_t* dlnum, int32_t* dlfk, double* dldir, double* dllen, int* status) {
+    css_ctx* c = p->ctx;
+    cudaStream_t st = c->stream;
+    const int nus = (int)us.size();
+    int le, lv, lf, fcap, emcap;
+    const size_t stride = cssi::geo_ws_bytes_per_warp(CSS_FP64, win_cap, &le, &lv, &lf, &fcap, &emcap);
+    const size_t lstride = cssi::geo_link_bytes_per_warp(lv);
+    const int wpc = 8;
+    const int nwarps = std::min(c->sm_count * wpc, ((nus + wpc - 1) / wpc) * wpc);
+    PathBufs B;
+    char *base = nullptr, *lbase = nullptr;
+    uint32_t* gen = nullptr;
+    TRY(c, "paths workspace", B.alloc(&base, (size_t)nwarps * stride));
+    TRY(c, "paths workspace", B.alloc(&lbase, (size_t)nwarps * lstride));
+    TRY(c, "paths workspace", B.alloc(&gen, (size_t)nwarps));
+    TRY(c, "paths workspace", cudaMemsetAsync(base, 0, (size_t)nwarps * stride, st));
+    TRY(c, "paths workspace", cudaMemsetAsync(gen, 0, (size_t)nwarps * sizeof(uint32_t), st));
+    cssi::GeoWs g{};
+    g.shared = 0;
+    g.base = base;
+    g.stride = stride;
+    g.log_eh = le; g.log_vh = lv; g.log_fh = lf;
+    g.wcap = win_cap; g.fcap = fcap; g.emcap = emcap;
+    g.gen = gen;
+    g.nwarps = nwarps;
+    g.occupancy = 1;
+    g.lbase = lbase;
+    g.lstride = lstride;
+    TRY(c, "bucket", cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->mesh->frank, p->fcnt,
+                                         p->fstart, p->fitems, p->scan_tmp, st));
+    GeoJob j = make_job(p, rc, 1, 0, nullptr);
+    j.order = dus;
+    j.lmax = PATH_MAX_LEGS;
+    j.lnum = dlnum; j.lfk = dlfk; j.ldir = dldir; j.llen = dllen;
+    cssi::GeoQueue q{nullptr, nullptr, nus, nullptr, nullptr, nullptr, nullptr, 1};
+    TRY(c, "reset", cudaMemsetAsync(c->dscal, 0, 2 * sizeof(int), st));
+    TRY(c, "reset", cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), st));
+    TRY(c, "paths", cssi::launch_geodesic_links(j, q, g, wpc, nwarps / wpc, c->dscal, c->dscal + 1, c->dcount, st));
+    return read_status(c, status);
+}
+
+}  // namespace
+
+int css_geodesic_paths(css_parts* p, double r_c, int64_t n_pairs, const int32_t* src, const int32_t* dst,
+                       int32_t max_points, double* points, int32_t* n_points, int32_t* n_legs, double* dist,
+                       double* gap) {
+    if (!p || bad_rc(r_c) || n_pairs < 0 || max_points < 2 ||
+        (n_pairs > 0 && (!src || !dst || !points || !n_points || !n_legs || !dist || !gap)))
+        return CSS_ERR_INVALID_ARG;
+    if (n_pairs == 0) return CSS_OK;
+    css_ctx* c = p->ctx;
+    cudaStream_t st = c->stream;
+    const size_t np = (size_t)n_pairs;
+    std::vector<int32_t> hs(np), hd(np);
+    TRY(c, "paths", cudaMemcpy(hs.data(), src, np * sizeof(int32_t), cudaMemcpyDefault));
+    TRY(c, "paths", cudaMemcpy(hd.data(), dst, np * sizeof(int32_t), cudaMemcpyDefault));
+    for (size_t k = 0; k < np; ++k)
+        if (hs[k] < 0 || hs[k] >= p->n || hd[k] < 0 || hd[k] >= p->n || hs[k] == hd[k]) {
+            c->err = "geodesic_paths: pair " + std::to_string(k) + " has a bad or repeated particle index";
+            return CSS_ERR_INVALID_ARG;
+        }
+    std::vector<int32_t> us(hs);
+    std::sort(us.begin(), us.end());
+    us.erase(std::unique(us.begin(), us.end()), us.end());
+    const int nus = (int)us.size();
+    PathBufs B;
+    int32_t* dus = nullptr;
+    TRY(c, "paths", B.alloc(&dus, us.size()));
+    TRY(c, "paths", cudaMemcpyAsync(dus, us.data(), us.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // the kernel, grown until neither the window pool nor the pair rows overflow
+    int win_cap = next_pow2(std::max(c->cfg.win_cap2, 16384));
+    int32_t *dlnum = nullptr, *dlfk = nullptr;
+    double *dldir = nullptr, *dllen = nullptr;
+    int cap = 0;
+    for (int attempt = 0;; ++attempt) {
+        int rc = ensure_pairs(p, c->pair_cap);
+        if (rc) return rc;
+        cap = p->pair_cap_alloc;
+        PathBufs L;
+        const size_t slots = (size_t)nus * cap;
+        TRY(c, "paths", L.alloc(&dlnum, slots));
+        TRY(c, "paths", L.alloc(&dlfk, slots * PATH_MAX_LEGS));
+        TRY(c, "paths", L.alloc(&dldir, 2 * slots * PATH_MAX_LEGS));
+        TRY(c, "paths", L.alloc(&dllen, slots * PATH_MAX_LEGS));
+        int status = 0;
+        rc = run_path_kernel(p, r_c, us, dus, win_cap, dlnum, dlfk, dldir, dllen, &status);
+        if (rc) return rc;
+        if (status == 0) {
+            // keep the leg buffers: hand them to the outer scope
+            B.ptrs.insert(B.ptrs.end(), L.ptrs.begin(), L.ptrs.end());
+            L.ptrs.clear();
+            break;
+        }
+        if (attempt >= MAX_RETRY) return status_error(c, status);
+        if (status & (css::ST_WIN_OVERFLOW | css::ST_HASH_OVERFLOW | css::ST_ITER_LIMIT)) {
+            if (win_cap >= WIN_CAP_MAX) return status_error(c, status);
+            win_cap *= 2;
+        } else if (status & css::ST_PAIR_OVERFLOW) {
+            c->pair_cap *= 2;
+        } else {
+            return status_error(c, status);
+        }
+    }
+    // rows and legs of the distinct sources
+    const size_t slots = (size_t)nus * cap;
+    std::vector<int32_t> pcnt(p->n), pj((size_t)p->n * cap), lnum(slots), lfk(slots * PATH_MAX_LEGS);
+    std::vector<double> pd((size_t)p->n * cap), ldir(2 * slots * PATH_MAX_LEGS), llen(slots * PATH_MAX_LEGS);
+    TRY(c, "paths", cudaMemcpyAsync(pcnt.data(), p->pcnt, pcnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TRY(c, "paths", cudaMemcpyAsync(pj.data(), p->pj, pj.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TRY(c, "paths", cudaMemcpyAsync(pd.data(), p->pd, pd.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY(c, "paths", cudaMemcpyAsync(lnum.data(), dlnum, lnum.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TRY(c, "paths", cudaMemcpyAsync(lfk.data(), dlfk, lfk.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TRY(c, "paths", cudaMemcpyAsync(ldir.data(), dldir, ldir.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY(c, "paths", cudaMemcpyAsync(llen.data(), dllen, llen.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY(c, "paths", cudaStreamSynchronize(st));
+    // the legs of every requested pair, from the target back to the source
+    std::vector<int64_t> first(np + 1, 0);
+    std::vector<int32_t> s_fk, s_pi, n_fk, n_pi;
+    std::vector<double> l_dir, l_len;
+    std::vector<double> hdist(np, INFINITY);
+    for (size_t k = 0; k < np; ++k) {
+        first[k] = (int64_t)s_fk.size();
+        const int i = hs[k], jj = hd[k];
+        const int r = (int)(std::lower_bound(us.begin(), us.end(), i) - us.begin());
+        const int cnt = std::min(pcnt[i], cap);
+        int pos = -1;
+        for (int a = 0; a < cnt; ++a)
+            if (pj[(size_t)i * cap + a] == jj) { pos = a; break; }
+        if (pos < 0) continue;   // not within the cutoff
+        hdist[k] = pd[(size_t)i * cap + pos];
+        const size_t o = (size_t)r * cap + pos;
+        const int nl = lnum[o];
+        if (nl <= 0) {
+            c->err = "geodesic_paths: the path of pair " + std::to_string(k) +
+                     (nl == -1 ? " has more legs than the limit" : " lost a vertex link");
+            return CSS_ERR_ITER_LIMIT;
+        }
+        for (int l = 0; l < nl; ++l) {
+            const size_t a = o * PATH_MAX_LEGS + l;
+            s_fk.push_back(lfk[a]);
+            s_pi.push_back(l == 0 ? jj : -1);
+            l_dir.push_back(ldir[2 * a]);
+            l_dir.push_back(ldir[2 * a + 1]);
+            l_len.push_back(llen[a]);
+            if (l + 1 < nl) { n_fk.push_back(lfk[a + 1]); n_pi.push_back(-1); }
+            else { n_fk.push_back(-1); n_pi.push_back(i); }
+        }
+    }
+    first[np] = (int64_t)s_fk.size();
+    const int64_t nleg = first[np];
+    std::vector<int32_t> nrec(nleg);
+    std::vector<double> rec((size_t)nleg * max_points * 3), sw(3 * (size_t)nleg), nw(3 * (size_t)nleg), lg(nleg);
+    if (nleg > 0) {
+        int32_t *d_sfk, *d_spi, *d_nfk, *d_npi, *d_nrec;
+        double *d_dir, *d_len, *d_rec, *d_sw, *d_nw, *d_gap;
+        TRY(c, "paths", B.alloc(&d_sfk, nleg));
+        TRY(c, "paths", B.alloc(&d_spi, nleg));
+        TRY(c, "paths", B.alloc(&d_nfk, nleg));
+        TRY(c, "paths", B.alloc(&d_npi, nleg));
+        TRY(c, "paths", B.alloc(&d_nrec, nleg));
+        TRY(c, "paths", B.alloc(&d_dir, 2 * nleg));
+        TRY(c, "paths", B.alloc(&d_len, nleg));
+        TRY(c, "paths", B.alloc(&d_rec, rec.size()));
+        TRY(c, "paths", B.alloc(&d_sw, sw.size()));
+        TRY(c, "paths", B.alloc(&d_nw, nw.size()));
+        TRY(c, "paths", B.alloc(&d_gap, lg.size()));
+        TRY(c, "paths", cudaMemcpyAsync(d_sfk, s_fk.data(), nleg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        TRY(c, "paths", cudaMemcpyAsync(d_spi, s_pi.data(), nleg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        TRY(c, "paths", cudaMemcpyAsync(d_nfk, n_fk.data(), nleg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        TRY(c, "paths", cudaMemcpyAsync(d_npi, n_pi.data(), nleg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        TRY(c, "paths", cudaMemcpyAsync(d_dir, l_dir.data(), 2 * nleg * sizeof(double), cudaMemcpyHostToDevice, st));
+        TRY(c, "paths", cudaMemcpyAsync(d_len, l_len.data(), nleg * sizeof(double), cudaMemcpyHostToDevice, st));
+        TRY(c, "paths", cssi::launch_legs(p->mesh->view(), nleg, p->face, p->bary, d_sfk, d_spi, d_dir, d_len, d_nfk,
+                                          d_npi, max_points, d_rec, d_nrec, d_sw, d_nw, d_gap, st));
+        TRY(c, "paths", cudaMemcpyAsync(nrec.data(), d_nrec, nleg * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TRY(c, "paths", cudaMemcpyAsync(rec.data(), d_rec, rec.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TRY(c, "paths", cudaMemcpyAsync(sw.data(), d_sw, sw.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TRY(c, "paths", cudaMemcpyAsync(nw.data(), d_nw, nw.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TRY(c, "paths", cudaMemcpyAsync(lg.data(), d_gap, lg.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TRY(c, "paths", cudaStreamSynchronize(st));
+    }
+    // polylines from the source: its position, then the legs in reverse order, each reversed
+    std::vector<double> out(np * (size_t)max_points * 3, 0.0);
+    std::vector<int32_t> onp(np, 0), onl(np, 0);
+    std::vector<double> ogap(np, 0.0);
+    for (size_t k = 0; k < np; ++k) {
+        const int64_t a0 = first[k], a1 = first[k + 1];
+        if (a1 == a0) continue;
+        int64_t n = 0;
+        double g = 0.0;
+        auto put = [&](const double* w) {
+            if (n < max_points) for (int a = 0; a < 3; ++a) out[3 * (k * max_points + n) + a] = w[a];
+            ++n;
+        };
+        put(&nw[3 * (a1 - 1)]);
+        for (int64_t l = a1 - 1; l >= a0; --l) {
+            if (nrec[l] < 0) {
+                c->err = "geodesic_paths: walking a leg of pair " + std::to_string(k) + " failed (" +
+                         std::to_string(nrec[l]) + ")";
+                return CSS_ERR_ITER_LIMIT;
+            }
+            for (int r = std::min<int>(nrec[l], max_points) - 1; r >= 0; --r) put(&rec[3 * ((size_t)l * max_points + r)]);
+            if (nrec[l] > max_points) n += nrec[l] - max_points;   // counted, not stored
+            put(&sw[3 * l]);
+            g = std::max(g, lg[l]);
+        }
+        onp[k] = (int32_t)std::min<int64_t>(n, INT32_MAX);
+        onl[k] = (int32_t)(a1 - a0);
+        ogap[k] = g;
+    }
+    TRY(c, "paths", cudaMemcpy(points, out.data(), out.size() * sizeof(double), cudaMemcpyDefault));
+    TRY(c, "paths", cudaMemcpy(n_points, onp.data(), np * sizeof(int32_t), cudaMemcpyDefault));
+    TRY(c, "paths", cudaMemcpy(n_legs, onl.data(), np * sizeof(int32_t), cudaMemcpyDefault));
+    TRY(c, "paths", cudaMemcpy(dist, hdist.data(), np * sizeof(double), cudaMemcpyDefault));
+    TRY(c, "paths", cudaMemcpy(gap, ogap.data(), np * sizeof(double), cudaMemcpyDefault));
+    return CSS_OK;
+}

@@ -148,6 +148,14 @@ struct GeoJob {
     css_potential pot;
     double* force;
     double* epot;
+    // path launches: for the pair in slot o of the row of the item'th source, its legs
+    // (lnum[o], at most lmax) as 4 * face + corner (corner 3: the target point), unit
+    // direction and length at lfk/ldir/llen[o * lmax + leg]; lnum -1: more legs than lmax
+    int32_t lmax = 0;
+    int32_t* lnum = nullptr;
+    int32_t* lfk = nullptr;
+    double* ldir = nullptr;
+    double* llen = nullptr;
 };
 
 // one particle set as the batched move / bucket kernels see it
@@ -186,6 +194,8 @@ struct GeoWs {
     uint32_t* gen;
     int nwarps;
     int occupancy;           // kernel variant: 1 (255 registers a thread) or 2 (128)
+    char* lbase = nullptr;   // path launches: per-warp vertex link arrays (lstride bytes a warp)
+    size_t lstride = 0;
 };
 
 // geodesic.cu
@@ -194,6 +204,11 @@ size_t geo_ws_bytes_per_warp(int precision, int win_cap, int* log_eh, int* log_v
 cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const GeoQueue& q, int precision,
                             const GeoWs& ws, int warps_per_cta, int nctas, int* work_counter,
                             int* status, unsigned long long* counters, cudaStream_t st);
+// the FP64, global-table kernel that also records the legs of every pair's path
+size_t geo_link_bytes_per_warp(int log_vh);
+cudaError_t launch_geodesic_links(const GeoJob& job, const GeoQueue& q, const GeoWs& ws, int warps_per_cta,
+                                  int nctas, int* work_counter, int* status, unsigned long long* counters,
+                                  cudaStream_t st);
 int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared_scale, int occupancy);
 size_t geodesic_shared_bytes(int precision, int warps_per_cta, int shared_scale);
 cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd,
@@ -225,6 +240,11 @@ cudaError_t launch_fire_move(const css::DMesh& m, int32_t n, int32_t* face, doub
                              const double* force, double* fire_state, css_integrator it, int half, int* status,
                              cudaStream_t st);
 // straightest-walk polylines of npaths paths (see css_trace_geodesics)
+// walks the legs of shortest paths (see k_legs in dynamics.cu)
+cudaError_t launch_legs(const css::DMesh& m, int64_t nleg, const int32_t* pface, const double* pbary,
+                        const int32_t* start_fk, const int32_t* start_pi, const double* dir, const double* len,
+                        const int32_t* next_fk, const int32_t* next_pi, int cap, double* rec, int32_t* nrec,
+                        double* start_w, double* next_w, double* gap, cudaStream_t st);
 cudaError_t launch_trace(const css::DMesh& m, int64_t npaths, const int32_t* pface, const double* pbary,
                          const int32_t* src, const double* tan, const double* len, int cap, double* pts,
                          int32_t* npts, int32_t* end_face, double* end_bary, int* status, cudaStream_t st);

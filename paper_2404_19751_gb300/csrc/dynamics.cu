@@ -664,12 +664,250 @@ cudaError_t launch_fire_move(const DMesh& m, int32_t n, int32_t* face, double* b
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ shortest-path legs (Sec. 2.2)
+// A shortest path is a chain of straight legs meeting at pseudo-source vertices; the
+// neighbour kernel's path instantiation records, for every pair, each leg's start node,
+// direction and length.  Here every leg is walked straight across the faces it crosses.
+
+__device__ __forceinline__ double corner_angle(const DMesh& m, int f, int k) {
+    const HeRec& r = m.he[3 * f + k];
+    return atan2(r.cy, r.cx);
+}
+
+// The face of the ring of the vertex at corner k of face f whose wedge holds the direction
+// at angle phi counted counter-clockwise from the edge corner k -> k+1 (negative: clockwise
+// of it; beyond the corner angle: past the edge corner k -> k+2).  On success f, k and phi
+// refer to that face, phi clamped into its wedge; false when the direction leaves the ring
+// through a boundary edge.
+__device__ bool ring_locate(const DMesh& m, int& f, int& k, double& phi) {
+    const double tol = 1e-12;
+    for (int guard = 0; guard < 256; ++guard) {
+        const double a = corner_angle(m, f, k);
+        if (phi < -tol) {
+            const int tw = m.twin[3 * f + k];                       // across corner k -> k+1
+            if (tw < 0) return false;
+            f = tw / 3;
+            const int kt = tw - 3 * f;
+            k = kt == 2 ? 0 : kt + 1;
+            phi += corner_angle(m, f, k);
+        } else if (phi > a + tol) {
+            const int tw = m.twin[3 * f + (k == 0 ? 2 : k - 1)];    // across corner k+2 -> k
+            if (tw < 0) return false;
+            phi -= a;
+            f = tw / 3;
+            k = tw - 3 * f;
+        } else {
+            phi = phi < 0.0 ? 0.0 : (phi > a ? a : phi);
+            return true;
+        }
+    }
+    return false;
+}
+
+__device__ void corner_dir(const DMesh& m, int f, int k, double phi, double& dx, double& dy) {
+    double ax, ay, bx, by;
+    corner(m, f, k, ax, ay);
+    corner(m, f, k + 1, bx, by);
+    const double L = sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+    dx = (bx - ax) / L;
+    dy = (by - ay) / L;
+    rot(cos(phi), sin(phi), dx, dy);
+}
+
+// A leg meets a vertex on its way and goes on straight: at angle pi from the reversed
+// incoming direction, counter-clockwise around the ring if it holds that angle on that
+// side, else clockwise (a boundary vertex holds it on one side only).
+__device__ bool vertex_pass(const DMesh& m, int& f, int& k, double& dx, double& dy) {
+    double ax, ay, bx, by;
+    corner(m, f, k, ax, ay);
+    corner(m, f, k + 1, bx, by);
+    const double L = sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+    const double ex = (bx - ax) / L, ey = (by - ay) / L;
+    double beta = atan2(ex * (-dy) - ey * (-dx), ex * (-dx) + ey * (-dy));
+    const double a = corner_angle(m, f, k);
+    beta = beta < 0.0 ? 0.0 : (beta > a ? a : beta);
+    int g = f, kg = k;
+    double phi = beta + WPI;
+    if (!ring_locate(m, g, kg, phi)) {
+        g = f; kg = k; phi = beta - WPI;
+        if (!ring_locate(m, g, kg, phi)) return false;
+    }
+    f = g;
+    k = kg;
+    corner_dir(m, g, kg, phi, dx, dy);
+    return true;
+}
+
+__device__ __forceinline__ void layout_world(const DMesh& m, int f, double x, double y, double* w) {
+    const double* fr = m.frame + 9 * (size_t)f;
+    for (int a = 0; a < 3; ++a) w[a] = fr[a] + x * fr[3 + a] + y * fr[6 + a];
+}
+
+__device__ __forceinline__ void wrap_world(const DMesh& m, double* w) {
+    if (m.periodic)
+        for (int a = 0; a < 2; ++a) w[a] -= m.per[a] * floor(w[a] / m.per[a]);
+}
+
+// One leg: from corner kc of face f (kc < 3; the unit direction (dx, dy) of f's layout may
+// point into any face of the vertex's ring) or from the point (px, py) of f (kc == 3), for
+// length len.  Writes the world position (wrapped into the period) of every edge or vertex
+// crossed before the end to rec (at most cap; *nrec counts all) and returns the end point
+// (face f, layout point px, py).  A crossing within 1e-12 of the leg's end is the end.
+// Returns 0, or a negative code (ring left through the boundary, boundary crossed, no end).
+__device__ int leg_walk(const DMesh& m, int& f, int kc, double& px, double& py, double dx, double dy, double len,
+                        double* rec, int cap, int& nrec) {
+    int cn = kc < 3 ? kc : -1;
+    if (cn < 0) {   // a start point on a corner of its face starts from that vertex
+        const double L01 = m.lay[3 * f], x2 = m.lay[3 * f + 1], y2 = m.lay[3 * f + 2];
+        const double l2 = py / y2, l1 = (px - l2 * x2) / L01, l0 = 1.0 - l1 - l2;
+        if (l0 > 1.0 - 1e-12) cn = 0;
+        if (l1 > 1.0 - 1e-12) cn = 1;
+        if (l2 > 1.0 - 1e-12) cn = 2;
+    }
+    if (cn >= 0) {
+        double ax, ay, bx, by;
+        corner(m, f, cn, ax, ay);
+        corner(m, f, cn + 1, bx, by);
+        const double L = sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+        const double ux = (bx - ax) / L, uy = (by - ay) / L;
+        double phi = atan2(ux * dy - uy * dx, ux * dx + uy * dy);
+        if (!ring_locate(m, f, cn, phi)) return -3;
+        corner_dir(m, f, cn, phi, dx, dy);
+        corner(m, f, cn, px, py);
+    }
+    double rem = len;
+    int entry = -1;
+    for (int it = 0; it < WALK_MAX; ++it) {
+        const double L01 = m.lay[3 * f], x2 = m.lay[3 * f + 1], y2 = m.lay[3 * f + 2];
+        const double Dx = dx * rem, Dy = dy * rem;
+        double lam[3], rate[3];
+        lam[2] = py / y2; lam[1] = (px - lam[2] * x2) / L01; lam[0] = 1.0 - lam[1] - lam[2];
+        rate[2] = Dy / y2; rate[1] = (Dx - rate[2] * x2) / L01; rate[0] = -rate[1] - rate[2];
+        double tmin = __longlong_as_double(0x7ff0000000000000ll);
+        int imin = -1;
+        for (int q = 0; q < 3; ++q) {
+            if (cn >= 0 && q != cn) continue;   // from a corner: only the far edge
+            if (!(rate[q] < 0.0)) continue;
+            const int side = q == 2 ? 0 : q + 1;
+            if (side == entry) continue;
+            double t = -lam[q] / rate[q];
+            if (t < 0.0) t = 0.0;
+            if (t < tmin) { tmin = t; imin = q; }
+        }
+        if (!(tmin < 1.0 - 1e-12)) { px += Dx; py += Dy; return 0; }
+        const int k = imin == 2 ? 0 : imin + 1;
+        const int k1 = k == 2 ? 0 : k + 1;
+        const double hx = px + tmin * Dx, hy = py + tmin * Dy;
+        rem *= (1.0 - tmin);
+        double lh[3];
+        lh[2] = hy / y2; lh[1] = (hx - lh[2] * x2) / L01; lh[0] = 1.0 - lh[1] - lh[2];
+        int vc = -1;
+        if (lh[k1] < 1e-12) vc = k;
+        else if (lh[k] < 1e-12) vc = k1;
+        if (rec && nrec < cap) {
+            double w[3];
+            if (vc >= 0) { double vx, vy; corner(m, f, vc, vx, vy); layout_world(m, f, vx, vy, w); }
+            else layout_world(m, f, hx, hy, w);
+            wrap_world(m, w);
+            for (int a = 0; a < 3; ++a) rec[3 * nrec + a] = w[a];
+        }
+        ++nrec;
+        if (vc >= 0) {
+            int kk = vc;
+            if (!vertex_pass(m, f, kk, dx, dy)) return -4;
+            cn = kk;
+            corner(m, f, cn, px, py);
+            entry = -1;
+            continue;
+        }
+        const int h = 3 * f + k;
+        const int tw = m.twin[h];
+        if (tw < 0) return -5;   // a shortest path never crosses the boundary
+        double ax, ay, bx, by;
+        corner(m, f, k, ax, ay);
+        corner(m, f, k1, bx, by);
+        const double L = sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+        const double ux = (bx - ax) / L, uy = (by - ay) / L;
+        const int g = tw / 3, k2 = tw - 3 * g;
+        double qax, qay, qbx, qby;
+        corner(m, g, k2 + 1, qax, qay);
+        corner(m, g, k2, qbx, qby);
+        const double Lg = sqrt((qbx - qax) * (qbx - qax) + (qby - qay) * (qby - qay));
+        const double vx = (qbx - qax) / Lg, vy = (qby - qay) / Lg;
+        const double co = ux * vx + uy * vy, si = ux * vy - uy * vx;
+        double ox = hx - ax, oy = hy - ay;
+        rot(co, si, ox, oy);
+        px = qax + ox; py = qay + oy;
+        rot(co, si, dx, dy);
+        f = g; entry = k2; cn = -1;
+    }
+    return -2;
+}
+
+// world position (wrapped) of a path node: 4 * face + corner, or (fk < 0) particle pi
+__device__ void node_world(const DMesh& m, int fk, int pi, const int32_t* pface, const double* pbary, double* w) {
+    if (fk >= 0) {
+        double x, y;
+        corner(m, fk >> 2, fk & 3, x, y);
+        layout_world(m, fk >> 2, x, y, w);
+    } else {
+        const int f = pface[pi];
+        const double* b = pbary + 3 * (size_t)pi;
+        layout_world(m, f, b[1] * m.lay[3 * f] + b[2] * m.lay[3 * f + 1], b[2] * m.lay[3 * f + 2], w);
+    }
+    wrap_world(m, w);
+}
+
+// Leg l starts at node start_fk[l] (4 * face + corner; corner 3: the point of particle
+// start_pi[l] in that face), goes along dir[l] for len[l], and must end on node next_fk[l]
+// (or, if negative, on particle next_pi[l]).  Writes its start, crossings and that next
+// node (world, wrapped), and gap[l] = distance between its end and the next node.
+__global__ void k_legs(DMesh m, int64_t nleg, const int32_t* pface, const double* pbary, const int32_t* start_fk,
+                       const int32_t* start_pi, const double* dir, const double* len, const int32_t* next_fk,
+                       const int32_t* next_pi, int cap, double* rec, int32_t* nrec, double* start_w,
+                       double* next_w, double* gap) {
+    const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (l >= nleg) return;
+    const int fk = start_fk[l];
+    int f = fk >> 2;
+    const int kc = fk & 3;
+    double px, py;
+    if (kc < 3) corner(m, f, kc, px, py);
+    else {
+        const double* b = pbary + 3 * (size_t)start_pi[l];
+        px = b[1] * m.lay[3 * f] + b[2] * m.lay[3 * f + 1];
+        py = b[2] * m.lay[3 * f + 2];
+    }
+    node_world(m, kc < 3 ? fk : -1, start_pi[l], pface, pbary, start_w + 3 * l);
+    int n = 0;
+    const int rc = leg_walk(m, f, kc, px, py, dir[2 * l], dir[2 * l + 1], len[l], rec + 3 * (size_t)l * cap, cap, n);
+    double e[3], q[3];
+    layout_world(m, f, px, py, e);
+    node_world(m, next_fk[l], next_pi[l], pface, pbary, q);
+    for (int a = 0; a < 3; ++a) next_w[3 * l + a] = q[a];
+    double d[3] = {e[0] - q[0], e[1] - q[1], e[2] - q[2]};
+    if (m.periodic)
+        for (int a = 0; a < 2; ++a) d[a] -= m.per[a] * floor(d[a] / m.per[a] + 0.5);
+    gap[l] = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    nrec[l] = rc < 0 ? rc : n;
+}
+
 cudaError_t launch_trace(const DMesh& m, int64_t npaths, const int32_t* pface, const double* pbary,
                          const int32_t* src, const double* tan, const double* len, int cap, double* pts,
                          int32_t* npts, int32_t* end_face, double* end_bary, int* status, cudaStream_t st) {
     if (npaths < 1) return cudaSuccess;
     k_trace<<<nb(npaths, 128), 128, 0, st>>>(m, npaths, pface, pbary, src, tan, len, cap, pts, npts, end_face,
                                               end_bary, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_legs(const DMesh& m, int64_t nleg, const int32_t* pface, const double* pbary,
+                        const int32_t* start_fk, const int32_t* start_pi, const double* dir, const double* len,
+                        const int32_t* next_fk, const int32_t* next_pi, int cap, double* rec, int32_t* nrec,
+                        double* start_w, double* next_w, double* gap, cudaStream_t st) {
+    if (nleg < 1) return cudaSuccess;
+    k_legs<<<nb(nleg, 128), 128, 0, st>>>(m, nleg, pface, pbary, start_fk, start_pi, dir, len, next_fk, next_pi, cap,
+                                          rec, nrec, start_w, next_w, gap);
     return cudaGetLastError();
 }
 

@@ -59,6 +59,7 @@ struct Win64 {
     double sx, sy, sig;
     double b0, b1, ta, tb;
     int32_t he, next, flags;
+    int32_t pv;        // pseudo-source vertex (-1: the source); set by the path kernel only
 };
 template <class R>
 struct WinT;
@@ -114,9 +115,25 @@ struct WarpSm {
 // live either in shared memory -- plain 32-bit keys, cleared for every source, for patches
 // that fit -- or in the warp's global workspace slice with generation-tagged 64-bit keys;
 // the window pool is always in the global slice.
-template <class R, bool SH>
-struct Ws {
-    static constexpr bool shared = SH;   // keyed tables in shared memory (else global, tagged)
+// Per vertex of the table, how its distance was reached, for the path extraction: the
+// previous node of its path (a pseudo-source vertex, -1 = the source), 4 * face + corner of
+// a face holding the vertex whose layout the direction is written in, the unit direction
+// from the vertex towards that node and the leg's length.  Present only in the path
+// instantiation of the kernel.
+template <bool L>
+struct WsLinks {};
+template <>
+struct WsLinks<true> {
+    int32_t* lpar;
+    int32_t* lfk;
+    double* ldir;
+    double* llen;
+};
+
+template <class R, int SH>
+struct Ws : WsLinks<SH == 2> {
+    static constexpr bool shared = SH == 1;   // keyed tables in shared memory (else global, tagged)
+    static constexpr bool links = SH == 2;    // also records how each vertex was reached (paths)
     int32_t* sekey;
     int32_t* svkey;
     int32_t* sfkey;
@@ -160,7 +177,7 @@ __host__ __device__ inline size_t ws_layout(int log_eh, int log_vh, int log_fh, 
     return o;
 }
 
-template <class R, bool SH>
+template <class R, int SH>
 __device__ inline Ws<R, SH> ws_bind(const cssi::GeoWs& g, int warp) {
     size_t off[13];
     ws_layout<R>(g.log_eh, g.log_vh, g.log_fh, g.wcap, g.fcap, g.emcap, off);
@@ -183,6 +200,14 @@ __device__ inline Ws<R, SH> ws_bind(const cssi::GeoWs& g, int warp) {
     w.wcap = g.wcap; w.fcap = g.fcap; w.emcap = g.emcap;
     w.gen = 0;
     w.sekey = w.svkey = w.sfkey = nullptr;
+    if constexpr (SH == 2) {
+        const size_t VH = (size_t)1 << g.log_vh;
+        char* lb = g.lbase + (size_t)warp * g.lstride;
+        w.lpar = (int32_t*)lb;
+        w.lfk = (int32_t*)(lb + al16(VH * 4));
+        w.ldir = (double*)(lb + 2 * al16(VH * 4));
+        w.llen = w.ldir + 2 * VH;
+    }
     return w;
 }
 
@@ -205,7 +230,7 @@ __host__ __device__ inline size_t sh_bytes_per_warp(int scale) {
                 (size_t)(1 << SH_LOG_FH) * 4 + (size_t)SH_FCAP * 4 + (size_t)SH_EMCAP * 4);
 }
 
-template <class R, bool SH>
+template <class R, int SH>
 __device__ inline void ws_bind_shared(Ws<R, SH>& w, unsigned char* base, int scale) {
     const int ls = sh_log2(scale);
     const int eh = 1 << (SH_LOG_EH + ls), vh = 1 << (SH_LOG_VH + ls), fh = 1 << (SH_LOG_FH + ls);
@@ -253,31 +278,31 @@ __device__ __forceinline__ int sh_find(const int32_t* keys, int logcap, int32_t 
     return -1;
 }
 
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __forceinline__ int ws_eins(Ws<R, SH>& ws, int32_t key, bool& claimed) {
     return ws.shared ? sh_insert(ws.sekey, ws.log_eh, key, claimed) : css::ht_insert(ws.ekey, ws.log_eh, ws.gen, key, claimed);
 }
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __forceinline__ int ws_efind(const Ws<R, SH>& ws, int32_t key) {
     return ws.shared ? sh_find(ws.sekey, ws.log_eh, key) : css::ht_find(ws.ekey, ws.log_eh, ws.gen, key);
 }
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __forceinline__ int ws_vins(Ws<R, SH>& ws, int32_t key, bool& claimed) {
     return ws.shared ? sh_insert(ws.svkey, ws.log_vh, key, claimed) : css::ht_insert(ws.vkey, ws.log_vh, ws.gen, key, claimed);
 }
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __forceinline__ int ws_vfind(const Ws<R, SH>& ws, int32_t key) {
     return ws.shared ? sh_find(ws.svkey, ws.log_vh, key) : css::ht_find(ws.vkey, ws.log_vh, ws.gen, key);
 }
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __forceinline__ int ws_fins(Ws<R, SH>& ws, int32_t key, bool& claimed) {
     return ws.shared ? sh_insert(ws.sfkey, ws.log_fh, key, claimed) : css::ht_insert(ws.fkey, ws.log_fh, ws.gen, key, claimed);
 }
 
 // forget the previous source's shared tables
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __forceinline__ void ws_clear_shared(Ws<R, SH>& ws, int lane) {
-    if constexpr (SH) {
+    if constexpr (SH == 1) {
         for (int k = lane; k < (1 << ws.log_eh); k += 32) ws.sekey[k] = -1;
         for (int k = lane; k < (1 << ws.log_vh); k += 32) ws.svkey[k] = -1;
         for (int k = lane; k < (1 << ws.log_fh); k += 32) ws.sfkey[k] = -1;
@@ -387,18 +412,58 @@ struct Widen<float> {
     static constexpr float mu = 8.0f * 1.1920929e-7f;
 };
 
-template <class R>
-struct VCand {
+// how a candidate reaches its vertex (path kernel only): see WsLinks
+template <bool L>
+struct VLink {};
+template <>
+struct VLink<true> {
+    int32_t par, fk;
+    double dx, dy, len;
+};
+
+template <class R, bool L = false>
+struct VCand : VLink<L> {
     int32_t v;
     int32_t fixed;   // tangent comes from a pseudo-source path
     double d;        // exact FP64 length
     R tx, ty;
 };
 
+// The link of the point (X, Y) of window W's half-edge frame straight back to W's
+// pseudo-source: which = 2 the far corner of the face W enters (the direction lies in that
+// face); 0 / 1 the start / end vertex of W's edge (the direction points into the face on
+// the other side of the edge and is written in that face); -1 a point inside the face W
+// enters (corner slot 3).
+__device__ void win_link(const DMesh& m, const Win64& W, double X, double Y, int which, VLink<true>& l) {
+    const int h = W.he, f = h / 3, k = h - 3 * f;
+    const double a = W.sx - X, b = W.sy - Y, n = sqrt(a * a + b * b);
+    const double ua = n > 0.0 ? a / n : 1.0, ub = n > 0.0 ? b / n : 0.0;
+    l.par = W.pv;
+    l.len = n;
+    int g = f, kg = k, kc = which == 2 ? (k == 0 ? 2 : k - 1) : 3;
+    double va = ua, vb = ub;
+    if ((which == 0 || which == 1) && m.twin[h] >= 0) {
+        const int tw = m.twin[h];   // runs from W's end vertex to its start vertex
+        g = tw / 3;
+        kg = tw - 3 * g;
+        kc = which == 0 ? (kg == 2 ? 0 : kg + 1) : kg;
+        va = -ua;
+        vb = -ub;
+    }
+    double ax, ay, bx, by;
+    css::face_corner(m, g, kg, ax, ay);
+    css::face_corner(m, g, kg + 1, bx, by);
+    const double L = sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+    const double ex = (bx - ax) / L, ey = (by - ay) / L;
+    l.dx = va * ex - vb * ey;
+    l.dy = va * ey + vb * ex;
+    l.fk = 4 * g + kc;
+}
+
 // Unfold window W into the next face: distance candidates for the pseudo-source vertices it
 // reaches (paths through any other vertex can be shortened, Sec. 2.2) and at most two children.
-template <class R>
-__device__ __noinline__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R>* vc, int& nvc,
+template <class R, bool L>
+__device__ __noinline__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R, L>* vc, int& nvc,
                                        Win<R>* ch, int& nch) {
     nvc = 0;
     nch = 0;
@@ -412,14 +477,16 @@ __device__ __noinline__ void propagate(const DMesh& m, const Win<R>& W, double r
     const R tolv = (R)Tol<R>::w * q.L;
     const R sx = fsx(W), sy = fsy(W);
     if (W.b0 <= tolv && m.pseudo[vu]) {
-        VCand<R>& c = vc[nvc++];
+        VCand<R, L>& c = vc[nvc++];
         c.v = vu; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact<R>(W, 0.0, 0.0);
         win_tangent<R>(W, (R)0, (R)0, c.tx, c.ty);
+        if constexpr (L) win_link(m, W, 0.0, 0.0, 0, c);
     }
     if (W.b1 >= q.L - tolv && m.pseudo[vv]) {
-        VCand<R>& c = vc[nvc++];
+        VCand<R, L>& c = vc[nvc++];
         c.v = vv; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact<R>(W, r.L, 0.0);
         win_tangent<R>(W, q.L, (R)0, c.tx, c.ty);
+        if constexpr (L) win_link(m, W, r.L, 0.0, 1, c);
     }
     const bool degen = win_degen<R>(W, q.L);
     if (degen && !win_degen_sees<R>(W, q.L)) return;
@@ -431,9 +498,10 @@ __device__ __noinline__ void propagate(const DMesh& m, const Win<R>& W, double r
         xc = (R)(W.sx + (r.cx - W.sx) * (-W.sy) / (r.cy - W.sy));
     }
     if ((degen || (xc >= W.b0 - tolv && xc <= W.b1 + tolv)) && m.pseudo[vcid]) {
-        VCand<R>& c = vc[nvc++];
+        VCand<R, L>& c = vc[nvc++];
         c.v = vcid; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact<R>(W, r.cx, r.cy);
         win_tangent<R>(W, q.cx, q.cy, c.tx, c.ty);
+        if constexpr (L) win_link(m, W, r.cx, r.cy, 2, c);
     }
     if (r.tl >= 0 && (degen || xc > W.b0)) {
         R mu0 = (R)0, mu1 = (R)1;
@@ -554,7 +622,7 @@ __device__ __forceinline__ void ivl_add(Ivl<R>& L, R x0, R x1, bool cover = true
     else if (cover) L.b[MAXP - 1] = x1;
 }
 
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __forceinline__ void face_add(Ws<R, SH>& ws, WarpSm& sm, int32_t f) {
     bool claimed;
     int s = ws_fins<R>(ws, f, claimed);
@@ -575,7 +643,7 @@ __device__ __forceinline__ int win_alloc(WarpSm& sm, int wcap) {
 
 // queue a window that still has to be unfolded (each window is queued at most once, so
 // the queue never holds more entries than the pool)
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __forceinline__ void push_pending(Ws<R, SH>& ws, WarpSm& sm, int id, float key) {
     const int p = atomicAdd(&sm.npend, 1);
     ws.pq[p] = id;
@@ -736,10 +804,10 @@ __device__ __forceinline__ bool same_family(const Win<R>& a, const Win<R>& b) {
 // Insert candidate window c on its edge (list slot es), intersecting it with every window
 // already on the edge from either side: on each overlap both keep only where they carry
 // the smaller distance.  Executed by one lane per edge.
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int es, Win<R> c, double rc);
 
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __forceinline__ void insert_window(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int es, const Win<R>& c0,
                                               double rc) {
     if (ws.ehead[es] >= 0) { insert_window_general<R>(m, ws, sm, es, c0, rc); return; }
@@ -759,7 +827,7 @@ __device__ __forceinline__ void insert_window(const DMesh& m, Ws<R, SH>& ws, War
     face_add(ws, sm, c.he / 3);
 }
 
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int es, Win<R> c, double rc) {
     const double Ld = m.he[c.he].L;
     const R Lr = (R)Ld;
@@ -922,9 +990,9 @@ __device__ __forceinline__ int group_rounds(bool has, int key, int lane, int& ra
     return (int)__reduce_max_sync(CSS_FULL, (unsigned)__popc(grp));
 }
 
-template <class R, bool SH>
-__device__ __noinline__ void vertex_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, bool has, const VCand<R>& c, double rc,
-                             int lane) {
+template <class R, int SH>
+__device__ __noinline__ void vertex_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, bool has,
+                                          const VCand<R, SH == 2>& c, double rc, int lane) {
     if (!__any_sync(CSS_FULL, has)) return;
     bool claimed = false;
     int slot = -1;
@@ -952,6 +1020,13 @@ __device__ __noinline__ void vertex_round(const DMesh& m, Ws<R, SH>& ws, WarpSm&
                 ws.vtan[2 * slot] = c.tx;
                 ws.vtan[2 * slot + 1] = c.ty;
                 ws.vflag[slot] = c.fixed ? (vf | 2) : (vf & ~2);
+                if constexpr (SH == 2) {
+                    ws.lpar[slot] = c.par;
+                    ws.lfk[slot] = c.fk;
+                    ws.ldir[2 * slot] = c.dx;
+                    ws.ldir[2 * slot + 1] = c.dy;
+                    ws.llen[slot] = c.len;
+                }
                 if (d < vd && d < rc && !(ws.vflag[slot] & 1)) {
                     ws.vflag[slot] |= 1;
                     const int p = atomicAdd(&sm.nemit, 1);
@@ -964,7 +1039,7 @@ __device__ __noinline__ void vertex_round(const DMesh& m, Ws<R, SH>& ws, WarpSm&
     }
 }
 
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, bool has, const Win<R>& c, double rc,
                                          int lane) {
     if (!__any_sync(CSS_FULL, has)) return;
@@ -990,7 +1065,7 @@ __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& 
 // candidate a window yields is at least that window's key, so vertices with
 // d(v) <= kmin (the smallest queued key) go now and the others wait.  Returns the number
 // of vertices emitted.
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, double rc, double kmin, int lane) {
     __syncwarp();
     const int ne = min(sm.nemit, ws.emcap);
@@ -1049,6 +1124,8 @@ __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm
             const double o_dv = __shfl_sync(CSS_FULL, dv, owner);
             const R o_tx = __shfl_sync(CSS_FULL, tx, owner);
             const R o_ty = __shfl_sync(CSS_FULL, ty, owner);
+            int o_vid = 0;
+            if constexpr (SH == 2) o_vid = __shfl_sync(CSS_FULL, vid, owner);
             bool hh = t < total;
             Win<R> c;
             if (hh) {
@@ -1071,6 +1148,7 @@ __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm
                     c.tb = o_ty;
                     c.flags = WIN_FIXED | WIN_ALIVE;
                     c.next = -1;
+                    if constexpr (SH == 2) c.pv = o_vid;
                 }
             }
             child_round<R>(m, ws, sm, hh, c, rc, lane);
@@ -1104,9 +1182,9 @@ __device__ __forceinline__ double pot_u(const css_potential& p, double l) {
 }
 
 // distance + source tangent (source-face layout) of particle j of face fl
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __noinline__ double query(const DMesh& m, const Ws<R, SH>& ws, int f0, R qx, R qy, int fl, const double* bj,
-                                     R& tx, R& ty) {
+                                     R& tx, R& ty, VLink<SH == 2>* ql) {
     R L01, x2, y2, dummy;
     face_corner_f<R>(m, fl, 1, L01, dummy);
     face_corner_f<R>(m, fl, 2, x2, y2);
@@ -1119,6 +1197,7 @@ __device__ __noinline__ double query(const DMesh& m, const Ws<R, SH>& ws, int f0
     // exact FP64 lengths (near-degenerate predicate); best_exact holds the best's FP64 length
     double best_exact = best;
     tx = (R)0; ty = (R)0;
+    if constexpr (SH == 2) { ql->par = -1; ql->fk = 4 * fl + 3; ql->dx = 1.0; ql->dy = 0.0; ql->len = 0.0; }
     if (fl == f0) {
         const R dx = px - qx, dy = py - qy;
         const R d = sqrt(dx * dx + dy * dy);
@@ -1126,6 +1205,11 @@ __device__ __noinline__ double query(const DMesh& m, const Ws<R, SH>& ws, int f0
         best_exact = best;
         best_fixed = false;
         if (d > (R)0) { tx = dx / d; ty = dy / d; }
+        if constexpr (SH == 2) {   // straight back to the source
+            ql->dx = d > (R)0 ? -(double)tx : 1.0;
+            ql->dy = d > (R)0 ? -(double)ty : 0.0;
+            ql->len = (double)d;
+        }
     }
     for (int k = 0; k < 3; ++k) {
         const int h = 3 * fl + k;
@@ -1188,6 +1272,10 @@ __device__ __noinline__ double query(const DMesh& m, const Ws<R, SH>& ws, int f0
                 }
                 best_fixed = !direct;
                 win_tangent<R>(w, hx, hy, tx, ty);
+                if constexpr (SH == 2) {
+                    win_link(m, w, hx, hy, -1, *ql);
+                    ql->fk = 4 * fl + 3;
+                }
             }
         }
     }
@@ -1199,13 +1287,23 @@ __device__ __noinline__ double query(const DMesh& m, const Ws<R, SH>& ws, int f0
         R vx, vy;
         face_corner_f<R>(m, fl, k, vx, vy);
         const double d = ws.vdist[slot] + (double)sqrt((px - vx) * (px - vx) + (py - vy) * (py - vy));
-        if (d < best - tie * d) { best = d; best_exact = d; best_fixed = true; tx = ws.vtan[2 * slot]; ty = ws.vtan[2 * slot + 1]; }
+        if (d < best - tie * d) {
+            best = d; best_exact = d; best_fixed = true; tx = ws.vtan[2 * slot]; ty = ws.vtan[2 * slot + 1];
+            if constexpr (SH == 2) {   // straight to the vertex, then along its path
+                const double ex = (double)(vx - px), ey = (double)(vy - py), n = sqrt(ex * ex + ey * ey);
+                ql->par = v;
+                ql->fk = 4 * fl + 3;
+                ql->dx = n > 0.0 ? ex / n : 1.0;
+                ql->dy = n > 0.0 ? ey / n : 0.0;
+                ql->len = n;
+            }
+        }
     }
     return best;
 }
 
 // Smallest and largest queued key.
-template <class R, bool SH>
+template <class R, int SH>
 __device__ __forceinline__ void pending_range(const Ws<R, SH>& ws, int npend, int lane, float& kmin, float& kmax) {
     kmin = INFINITY;
     kmax = 0.0f;
@@ -1226,7 +1324,7 @@ __device__ __forceinline__ void pending_range(const Ws<R, SH>& ws, int npend, in
 // those in queue order are taken and the queue is compacted in place.  Processing in
 // (batched) key order keeps the work close to that of a priority queue: windows that a
 // shorter family would trim are mostly never unfolded.
-template <class R, bool SH>
+template <class R, int SH>
 __device__ int select_wave(Ws<R, SH>& ws, WarpSm& sm, int npend, float kmin, float kmax, int lane) {
     float T = kmax;
     if (npend > 32) {
@@ -1275,7 +1373,7 @@ __device__ int select_wave(Ws<R, SH>& ws, WarpSm& sm, int npend, float kmin, flo
     return mine;
 }
 
-template <class R, bool SH>
+template <class R, int SH>
 __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, int lane, int* status,
                            unsigned long long* counters, int item, int32_t* defer_list, int* defer_count) {
     const DMesh& m = J.m;
@@ -1289,7 +1387,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
     __syncwarp();
     if (lane == 0) face_add(ws, sm, f0);
     {   // the source's own pseudo-source corners
-        VCand<R> c;
+        VCand<R, SH == 2> c;
         bool has = false;
         if (lane < 3) {
             c.v = m.fv[3 * f0 + lane];
@@ -1301,6 +1399,13 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
             c.d = d;
             c.tx = (R)(d > 0.0 ? dx / d : 1.0);
             c.ty = (R)(d > 0.0 ? dy / d : 0.0);
+            if constexpr (SH == 2) {   // straight back to the source
+                c.par = -1;
+                c.fk = 4 * f0 + lane;
+                c.dx = d > 0.0 ? -dx / d : -1.0;
+                c.dy = d > 0.0 ? -dy / d : 0.0;
+                c.len = d;
+            }
         }
         vertex_round<R>(m, ws, sm, has, c, rc, lane);
     }
@@ -1330,6 +1435,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
                 c.tb = (R)dy;
                 c.flags = WIN_ALIVE;
                 c.next = -1;
+                if constexpr (SH == 2) c.pv = -1;
             }
         }
         child_round<R>(m, ws, sm, has, c, rc, lane);
@@ -1355,10 +1461,10 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
             act = (w.flags & WIN_ALIVE) && !(w.flags & WIN_DONE) && (double)win_key<R>(w) < rc;
             if (act) ws.win[idx].flags = w.flags | WIN_DONE;
         }
-        VCand<R> vc[3];
+        VCand<R, SH == 2> vc[3];
         Win<R> ch[2];
         int nvc = 0, nch = 0;
-        if (act) propagate<R>(m, w, rc, vc, nvc, ch, nch);
+        if (act) propagate<R, SH == 2>(m, w, rc, vc, nvc, ch, nch);
         n_prop += __popc(__ballot_sync(CSS_FULL, act));
         __syncwarp();
         // one call site per round kind keeps the kernel's instruction footprint small
@@ -1415,14 +1521,43 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
             double d = 0.0;
             R tx = (R)0, ty = (R)0;
             int j = -1;
+            VLink<SH == 2> ql;
             if (t < total) {
                 j = J.fitems[o_st + (t - o_ex)];
                 if (j != i) {
-                    d = query<R>(m, ws, f0, qx, qy, o_fl, J.bary + 3 * (size_t)j, tx, ty);
+                    d = query<R>(m, ws, f0, qx, qy, o_fl, J.bary + 3 * (size_t)j, tx, ty, &ql);
                     ispair = d < rc;
                 }
             }
             const unsigned pm = __ballot_sync(CSS_FULL, ispair);
+            if constexpr (SH == 2) {
+                // the pair's legs, from the target back to the source: its own link, then the
+                // link of each vertex on the way (still in this source's table)
+                const int pos = npair + __popc(pm & css::lanemask_lt());
+                if (ispair && pos < J.pair_cap) {
+                    const size_t o = (size_t)item * J.pair_cap + pos;
+                    int nl = 0;
+                    VLink<true> l = ql;
+                    for (;;) {
+                        if (nl >= J.lmax) { nl = -1; break; }
+                        const size_t a = o * J.lmax + nl;
+                        J.lfk[a] = l.fk;
+                        J.ldir[2 * a] = l.dx;
+                        J.ldir[2 * a + 1] = l.dy;
+                        J.llen[a] = l.len;
+                        ++nl;
+                        if (l.par < 0) break;
+                        const int slot = ws_vfind<R>(ws, l.par);
+                        if (slot < 0) { nl = -2; break; }
+                        l.par = ws.lpar[slot];
+                        l.fk = ws.lfk[slot];
+                        l.dx = ws.ldir[2 * slot];
+                        l.dy = ws.ldir[2 * slot + 1];
+                        l.len = ws.llen[slot];
+                    }
+                    J.lnum[o] = nl;
+                }
+            }
             if (wp && ispair) {
                 const int pos = npair + __popc(pm & css::lanemask_lt());
                 if (pos < J.pair_cap) {
@@ -1470,7 +1605,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
 // OCC = CTAs of 256 threads per SM the register budget must allow: 1 gives up to 255
 // registers a thread (fewer resident warps, no spills), 2 caps them at 128 (twice the
 // resident warps, some spills); which is faster depends on the workload.
-template <class R, int OCC, bool SH>
+template <class R, int OCC, int SH>
 __global__ void __launch_bounds__(256, OCC) k_geodesic(cssi::GeoJob job0, const cssi::GeoJob* jobs, cssi::GeoQueue q,
                                                   cssi::GeoWs g, int* work, int* status,
                                                   unsigned long long* counters) {
@@ -1482,7 +1617,7 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic(cssi::GeoJob job0, const 
     WarpSm& sm = smem[wib];
     Ws<R, SH> ws = ws_bind<R, SH>(g, gw);
     extern __shared__ __align__(16) unsigned char dsm[];
-    if constexpr (SH) ws_bind_shared<R, SH>(ws, dsm + (size_t)wib * sh_bytes_per_warp<R>(g.shared), g.shared);
+    if constexpr (SH == 1) ws_bind_shared<R, SH>(ws, dsm + (size_t)wib * sh_bytes_per_warp<R>(g.shared), g.shared);
     uint32_t gen = 0;
     if (lane == 0) gen = g.gen[gw];
     gen = __shfl_sync(CSS_FULL, gen, 0);
@@ -1578,8 +1713,20 @@ cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const GeoQu
     return cudaGetLastError();
 }
 
+size_t geo_link_bytes_per_warp(int log_vh) {
+    const size_t VH = (size_t)1 << log_vh;
+    return 2 * al16(VH * 4) + al16(VH * 24);
+}
+
+cudaError_t launch_geodesic_links(const GeoJob& job, const GeoQueue& q, const GeoWs& ws, int warps_per_cta,
+                                  int nctas, int* work_counter, int* status, unsigned long long* counters,
+                                  cudaStream_t st) {
+    k_geodesic<double, 1, 2><<<nctas, 32 * warps_per_cta, 0, st>>>(job, nullptr, q, ws, work_counter, status, counters);
+    return cudaGetLastError();
+}
+
 // resident CTAs per SM for a launch shape (0: the shape does not fit an SM)
-template <class R, int OCC, bool SH>
+template <class R, int OCC, int SH>
 static int blocks_per_sm(int warps_per_cta, size_t dyn) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);

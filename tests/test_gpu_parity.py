@@ -455,3 +455,85 @@ def test_state_upload_keeps_or_drops_cached_forces_correctly(ctx):
         s = ra
     a.free()
     mesh.free()
+
+
+def _holed():
+    m = synth.holed_plane(21, (0.4, 0.6, 0.4, 0.6))
+    face, bary = synth.place_uniform(m, 48, 5)
+    return m, face, bary, math.inf
+
+
+PATH_WORKLOADS = {"holed_plane21_n48": _holed, "noisy_ico5_n2048": WORKLOADS["noisy_ico5_n2048"],
+                  "hfield64_n1024": WORKLOADS["hfield64_n1024"], "flat64": WORKLOADS["flat64"]}
+
+
+def _polyline_length(P, per):
+    d = np.diff(P, axis=0)
+    if per is not None:
+        for a in range(2):
+            d[:, a] -= per[a] * np.round(d[:, a] / per[a])
+    return float(np.linalg.norm(d, axis=1).sum())
+
+
+@pytest.mark.parametrize("name", list(PATH_WORKLOADS))
+def test_shortest_paths_with_bends_match_oracle(ctx, name):
+    """Shortest-path polylines, bends at pseudo-source vertices included: for every pair of
+    a sample of sources (and a few pairs beyond the cutoff) the GPU gives the oracle's
+    distance, number of legs and polyline point by point (periodic meshes: up to the
+    period), every leg lands on its node, and the polyline is as long as the distance.
+    Pairs with two equally short paths may take either; at most 2 % of the sample may
+    differ from the oracle's, and those must still be exact shortest paths."""
+    m, face, bary, r_c = PATH_WORKLOADS[name]()
+    mesh, parts = _setup(ctx, m, face, bary)
+    om = O.OracleMesh(m)
+    n = len(face)
+    src = np.arange(0, n, max(1, n // 8))[:8]
+    rs, j = om.neighbors(face, bary, r_c, sources=src)[:2]
+    S = np.repeat(src, np.diff(rs)).astype(np.int32)
+    D = j.astype(np.int32)
+    rng = np.random.default_rng(4)
+    extra_s = rng.integers(0, n, 6).astype(np.int32)
+    extra_d = ((extra_s + 1 + rng.integers(0, n - 1, 6)) % n).astype(np.int32)
+    S, D = np.concatenate([S, extra_s]), np.concatenate([D, extra_d])
+    order = np.argsort(S, kind="stable")
+    S, D = S[order], D[order]
+    gp, gl, gd, gg = css.geodesic_paths(parts, r_c, S, D, max_points=2048)
+    op, ol, od, og = om.geodesic_paths(face, bary, r_c, S, D, cap=2048)
+    per = m.period
+    assert np.all(np.isinf(gd) == np.isinf(od))
+    fin = np.isfinite(od)
+    np.testing.assert_allclose(gd[fin], od[fin], rtol=FP64_RTOL, atol=0)
+    differ = 0
+    for k in range(len(S)):
+        if not fin[k]:
+            assert len(gp[k]) == 0 and gl[k] == 0
+            continue
+        assert gg[k] < 1e-9
+        assert _polyline_length(gp[k], per) == pytest.approx(gd[k], rel=1e-9)
+        same = gl[k] == ol[k] and len(gp[k]) == len(op[k])
+        if same:
+            dd = gp[k] - op[k]
+            if per is not None:
+                for a in range(2):
+                    dd[:, a] -= per[a] * np.round(dd[:, a] / per[a])
+            same = bool(np.max(np.abs(dd)) < 1e-9)
+        differ += not same
+    assert differ <= 0.02 * fin.sum()
+    if name in ("holed_plane21_n48", "noisy_ico5_n2048"):
+        assert np.sum(gl >= 2) >= 10          # the sample holds bent paths
+    parts.free()
+    mesh.free()
+
+
+def test_shortest_paths_reject_bad_pairs(ctx):
+    m, face, bary, r_c = _holed()
+    mesh, parts = _setup(ctx, m, face, bary)
+    for s, d in (([0], [0]), ([0], [len(face)]), ([-1], [2])):
+        with pytest.raises(css.CssError):
+            css.geodesic_paths(parts, r_c, s, d)
+    with pytest.raises(ValueError):           # more points than max_points
+        css.geodesic_paths(parts, r_c, [0], [1 + int(np.argmax(np.linalg.norm(
+            synth.particles.world_positions(m, face, bary)[1:] - synth.particles.world_positions(m, face[:1], bary[:1]),
+            axis=1)))], max_points=2)
+    parts.free()
+    mesh.free()
