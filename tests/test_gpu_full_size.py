@@ -194,3 +194,37 @@ def test_tori64_batched_step():
         for mesh in meshes:
             mesh.free()
     ctx.close()
+
+
+def test_full_size_shortest_paths(workload):
+    """Shortest-path polylines (bends included) of every neighbour of three sampled sources
+    at full size: the oracle's distance and points (periodic: up to the period), legs
+    landing on their nodes, polyline length equal to the distance."""
+    cfg, mesh, parts, om, src = workload
+    face, bary, r_c = cfg["face"], cfg["bary"], cfg["r_c"]
+    s3 = np.sort(src[:3])
+    rs, j = om.neighbors(face, bary, r_c, sources=s3)[:2]
+    S = np.repeat(s3, np.diff(rs)).astype(np.int32)
+    gp, gl, gd, gg = css.geodesic_paths(parts, r_c, S, j, max_points=4096)
+    op, ol, od, og = om.geodesic_paths(face, bary, r_c, S, j, cap=4096)
+    np.testing.assert_allclose(gd, od, rtol=FP64_RTOL, atol=0)
+    per = cfg["mesh"].period
+    differ = 0
+    for k in range(len(S)):
+        assert gg[k] < 1e-9
+        dd = np.diff(gp[k], axis=0)
+        if per is not None:
+            for a in range(2):
+                dd[:, a] -= per[a] * np.round(dd[:, a] / per[a])
+        assert np.linalg.norm(dd, axis=1).sum() == pytest.approx(gd[k], rel=1e-9)
+        # the points decide: a vertex on a straight stretch may end a leg on one side and be
+        # passed through mid-leg on the other (equally short chains), which gives the same points
+        same = len(gp[k]) == len(op[k])
+        if same:
+            e = gp[k] - op[k]
+            if per is not None:
+                for a in range(2):
+                    e[:, a] -= per[a] * np.round(e[:, a] / per[a])
+            same = bool(np.max(np.abs(e)) < 1e-9)
+        differ += not same
+    assert differ <= max(1, 0.02 * len(S))

@@ -479,8 +479,8 @@ def _polyline_length(P, per):
 def test_shortest_paths_with_bends_match_oracle(ctx, name):
     """Shortest-path polylines, bends at pseudo-source vertices included: for every pair of
     a sample of sources (and a few pairs beyond the cutoff) the GPU gives the oracle's
-    distance, number of legs and polyline point by point (periodic meshes: up to the
-    period), every leg lands on its node, and the polyline is as long as the distance.
+    distance and polyline point by point (periodic meshes: up to the period), every leg
+    lands on its node, and the polyline is as long as the distance.
     Pairs with two equally short paths may take either; at most 2 % of the sample may
     differ from the oracle's, and those must still be exact shortest paths."""
     m, face, bary, r_c = PATH_WORKLOADS[name]()
@@ -510,7 +510,9 @@ def test_shortest_paths_with_bends_match_oracle(ctx, name):
             continue
         assert gg[k] < 1e-9
         assert _polyline_length(gp[k], per) == pytest.approx(gd[k], rel=1e-9)
-        same = gl[k] == ol[k] and len(gp[k]) == len(op[k])
+        # the points decide: a vertex on a straight stretch may end a leg on one side and be
+        # passed through mid-leg on the other (equally short chains), which gives the same points
+        same = len(gp[k]) == len(op[k])
         if same:
             dd = gp[k] - op[k]
             if per is not None:
