@@ -435,9 +435,9 @@ def run_single(args, cfg, css, ctx, torch, stream, timer, rank, world):
         "memory_roofline": mem,
         "e2e": {"value": replica_throughput(world, e2e_pairs, e2e_t), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        # per step: move (1) + bucketing (5) + neighbour/force first and second pass (2) + kick
-        # or step counter (1)
-        "gpu_launches": 9 * k32,
+        # per step: move (1) + bucketing (6: count, scan, scatter, rank) + neighbour/force first
+        # and second pass (2) + kick or step counter (1)
+        "gpu_launches": 10 * k32,
         "clocks": r32["clocks"],
     }
     if cb:
@@ -594,9 +594,9 @@ def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
     k32 = r32b["steps"]
     roof, mem = roofline(css, ctx, pk, props_per_src, n, r32b["pairs"] / k32,
                          statistics.mean(r32b["kernel_ms"]) / 1e3, "k_geodesic<float> (batched launch)")
-    # per step, for all meshes at once: move (1) + bucketing (3) + two passes (2) + kick or
-    # step counter (1)
-    launches_per_step = 7
+    # per step, for all meshes at once: move (1) + bucketing (4: count, scan, scatter, rank) +
+    # two passes (2) + kick or step counter (1)
+    launches_per_step = 8
     line = {
         "metric": METRIC, "value": rate(r32b), "unit": UNIT, "n_gpus": world, "steps": k32,
         "warmup": args.warmup, "ms_per_step": 1e3 * r32b["t"] / k32, "higher_is_better": True, "scaling": "weak",

@@ -137,6 +137,11 @@ int css_particles_get(css_parts* parts, int32_t* face, double* bary, double* vel
  * simulation from host memory. */
 int css_particles_update(css_parts* parts, const int32_t* face, const double* bary,
                          const double* vel, const double* orient);
+/* Set the step counter (the Philox counter of the Brownian and active noise; what
+ * css_particles_get returns as step).  With css_particles_set / css_particles_update of a
+ * saved state and the same seed it resumes a stochastic run bit for bit.
+ * CSS_ERR_INVALID_ARG for a negative step. */
+int css_particles_set_step(css_parts* parts, int64_t step);
 int css_particles_free(css_parts* parts);
 
 /* ---------------------------------------------------------------- hot path

@@ -28,7 +28,7 @@ SYMBOLS = ("css_create", "css_destroy", "css_last_error", "css_last_counters", "
            "css_particles_get", "css_particles_free", "css_geodesic_neighbors", "css_compute_forces",
            "css_integrate_step", "css_batch_create", "css_batch_step", "css_batch_free",
            "css_last_kernel_ms", "css_fma_peak", "css_particles_update", "css_get_launch", "css_autotune",
-           "css_trace_geodesics", "css_geodesic_paths")
+           "css_trace_geodesics", "css_geodesic_paths", "css_particles_set_step")
 
 
 class CssError(RuntimeError):
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "css_autotune": [P, P, I32, P, D, C.c_int, I32, I64, P, C.POINTER(D)],
         "css_trace_geodesics": [P, I64, P, P, P, I32, P, P, P, P],
         "css_geodesic_paths": [P, D, I64, P, P, I32, P, P, P, P, P],
+        "css_particles_set_step": [P, I64],
         "css_mesh_upload": [P, P, I64, P, I64, P, C.POINTER(C.c_void_p)],
         "css_mesh_free": [P],
         "css_mesh_counts": [P, P],
@@ -258,6 +259,11 @@ def particles_get(parts: Particles):
 def particles_update(parts: Particles, face=None, bary=None, vel=None, orient=None):
     f, b, v, o = _i32(face), _f64(bary), _f64(vel), _f64(orient)
     parts.ctx.check(load().css_particles_update(parts.h, _ptr(f), _ptr(b), _ptr(v), _ptr(o)))
+
+
+def particles_set_step(parts: Particles, step: int):
+    """Set the step counter (noise stream position), e.g. when resuming from a checkpoint."""
+    parts.ctx.check(load().css_particles_set_step(parts.h, int(step)))
 
 
 def particles_get_into(parts: Particles, face=None, bary=None, vel=None, orient=None, force=None):

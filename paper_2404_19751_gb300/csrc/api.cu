@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "css_internal.h"
 
 using cssi::GeoJob;
@@ -216,7 +218,7 @@ int enqueue_passes(css_ctx* c, const GeoJob& j0, const GeoJob* djobs, const int3
 int enqueue_geo(css_parts* p, double rc, int prec, int want_pairs, int want_forces, const css_potential* pot,
                 const GeoPlan& P) {
     css_ctx* c = p->ctx;
-    TRY(c, "bucket", cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->mesh->frank, p->fcnt, p->fstart, p->fitems,
+    TRY(c, "bucket", cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->mesh->frank, p->fcnt, p->fstart, p->fitems, p->ftmp,
                                          p->scan_tmp, c->stream));
     GeoJob j = make_job(p, rc, want_pairs, want_forces, pot);
     return enqueue_passes(c, j, nullptr, nullptr, nullptr, (int32_t)p->n, prec, P);
@@ -299,6 +301,15 @@ bool finite_all(const double* h, size_t n) {
     return true;
 }
 
+}  // namespace
+
+namespace {
+// one NVTX range per public call that launches work (visible to profilers and tracers;
+// free when no tool is attached)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 }  // namespace
 
 // =====================================================================================
@@ -427,6 +438,7 @@ int css_get_launch(const css_ctx* c, css_launch* l) {
 
 int css_mesh_upload(css_ctx* c, const double* verts, int64_t nv, const int32_t* faces, int64_t nf, const double* period,
                     css_mesh** out) {
+    Range range_("css_mesh_upload");
     if (!c || !out || !verts || !faces || nv < 3 || nf < 1 || nv > INT32_MAX / 2 || nf > INT32_MAX / 6)
         return CSS_ERR_INVALID_ARG;
     if (period && !(period[0] > 0.0 && period[1] > 0.0)) return CSS_ERR_INVALID_ARG;
@@ -464,6 +476,7 @@ int css_mesh_counts(const css_mesh* m, int64_t out[4]) {
 
 int css_particles_set(css_ctx* c, css_mesh* m, int64_t n, const int32_t* face, const double* bary, const double* vel,
                       const double* orient, uint64_t seed, css_parts** out) {
+    Range range_("css_particles_set");
     if (!c || !m || !out || !face || !bary || n < 1 || n > INT32_MAX / 64) return CSS_ERR_INVALID_ARG;
     *out = nullptr;
     // validation on the host (a copy when the input is on the device)
@@ -504,6 +517,7 @@ int css_particles_set(css_ctx* c, css_mesh* m, int64_t n, const int32_t* face, c
     if (e == cudaSuccess) e = cudaMalloc(&p->fcnt, (nf + 1) * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->fstart, (nf + 1) * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->fitems, n * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p->ftmp, n * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->scan_tmp, cssi::scan_tmp_ints(nf + 1) * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->pcnt, n * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->dstep, sizeof(int64_t));
@@ -538,6 +552,7 @@ int css_particles_get(css_parts* p, int32_t* face, double* bary, double* vel, do
 
 int css_particles_update(css_parts* p, const int32_t* face, const double* bary, const double* vel,
                          const double* orient) {
+    Range range_("css_particles_update");
     if (!p) return CSS_ERR_INVALID_ARG;
     css_ctx* c = p->ctx;
     cudaStream_t st = c->stream;
@@ -585,11 +600,20 @@ int css_particles_update(css_parts* p, const int32_t* face, const double* bary, 
     return CSS_OK;
 }
 
+int css_particles_set_step(css_parts* p, int64_t step) {
+    if (!p || step < 0) return CSS_ERR_INVALID_ARG;
+    css_ctx* c = p->ctx;
+    p->step = step;
+    TRY(c, "set_step", cudaMemcpyAsync(p->dstep, &p->step, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    TRY(c, "set_step", cudaStreamSynchronize(c->stream));
+    return CSS_OK;
+}
+
 int css_particles_free(css_parts* p) {
     if (!p) return CSS_ERR_INVALID_ARG;
     if (p->graph) cudaGraphExecDestroy(p->graph);
     cudaFree(p->state); cudaFree(p->snap);
-    cudaFree(p->fcnt); cudaFree(p->fstart); cudaFree(p->fitems); cudaFree(p->scan_tmp); cudaFree(p->order);
+    cudaFree(p->fcnt); cudaFree(p->fstart); cudaFree(p->fitems); cudaFree(p->ftmp); cudaFree(p->scan_tmp); cudaFree(p->order);
     cudaFree(p->pcnt); cudaFree(p->pj); cudaFree(p->pd); cudaFree(p->pt); cudaFree(p->dstep); cudaFree(p->dfire);
     delete p;
     return CSS_OK;
@@ -598,6 +622,7 @@ int css_particles_free(css_parts* p) {
 
 int css_geodesic_neighbors(css_parts* p, double r_c, int precision, int64_t capacity, int64_t* n_pairs,
                            int64_t* row_start, int32_t* nbr_j, double* dist, double* tangent) {
+    Range range_("css_geodesic_neighbors");
     if (!p || !n_pairs || bad_prec(precision) || bad_rc(r_c) || capacity < 0) return CSS_ERR_INVALID_ARG;
     css_ctx* c = p->ctx;
     int rc = run_geo(p, r_c, precision, 1, 0, nullptr);
@@ -639,6 +664,7 @@ int css_geodesic_neighbors(css_parts* p, double r_c, int precision, int64_t capa
 }
 
 int css_compute_forces(css_parts* p, const css_potential* pot, double r_c, int precision, double* forces, double* e_pot) {
+    Range range_("css_compute_forces");
     if (!p || !pot || bad_prec(precision) || bad_rc(r_c) || pot->kind < 0 || pot->kind > 2) return CSS_ERR_INVALID_ARG;
     css_ctx* c = p->ctx;
     int rc = run_geo(p, r_c, precision, 0, 1, pot);
@@ -730,6 +756,7 @@ int capture(css_ctx* c, Fn fn, cudaGraphExec_t* exec) {
 
 int css_integrate_step(css_parts* p, const css_potential* pot, const css_integrator* it, double r_c, int precision,
                        int64_t n_steps, const double* noise, double* e_pot) {
+    Range range_("css_integrate_step");
     if (!p || !pot || !it || bad_prec(precision) || bad_rc(r_c) || n_steps < 0 || it->kind < 0 || it->kind > 4 ||
         !(it->dt > 0.0) || !(it->mass > 0.0) || !(it->lambda > 0.0) || !(it->max_disp > 0.0))
         return CSS_ERR_INVALID_ARG;
@@ -857,7 +884,7 @@ int css_batch_create(css_ctx* c, css_parts* const* parts, int32_t n_sets, css_ba
         cssi::SetView v{};
         v.m = p->mesh->view();
         v.face = p->face; v.bary = p->bary; v.vel = p->vel; v.orient = p->orient; v.force = p->force;
-        v.fcnt = p->fcnt; v.fstart = p->fstart; v.fitems = p->fitems; v.dstep = p->dstep; v.seed = p->seed;
+        v.fcnt = p->fcnt; v.fstart = p->fstart; v.fitems = p->fitems; v.ftmp = p->ftmp; v.dstep = p->dstep; v.seed = p->seed;
         hv.push_back(v);
         hoff.push_back(hoff.back() + (int32_t)p->n);
     }
@@ -899,6 +926,7 @@ int batch_enqueue_forces(css_batch* b, const css_potential* pot, double rc, int 
 
 int css_batch_step(css_batch* b, const css_potential* pot, const css_integrator* it, double r_c, int precision,
                    int64_t n_steps) {
+    Range range_("css_batch_step");
     if (!b || !pot || !it || bad_prec(precision) || bad_rc(r_c) || n_steps < 0 || it->kind < 0 || it->kind > 3 ||
         !(it->dt > 0.0) || !(it->mass > 0.0) || !(it->lambda > 0.0) || !(it->max_disp > 0.0))
         return CSS_ERR_INVALID_ARG;
@@ -1010,6 +1038,7 @@ int tune_run(css_ctx* c, const GeoJob* djobs, const GeoJob& j0, const int32_t* j
 
 int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_potential* pot, double r_c,
                  int precision, int32_t reps, int64_t sample, css_launch* best, double* best_ms) {
+    Range range_("css_autotune");
     if (!c || !sets || n_sets < 1 || !pot || bad_prec(precision) || bad_rc(r_c) || reps < 1 || sample < 0)
         return CSS_ERR_INVALID_ARG;
     int64_t total = 0;
@@ -1038,7 +1067,7 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
     if (e == cudaSuccess) e = stage_in(hs.data(), hs.size(), &ds, st);
     for (int k = 0; k < n_sets && e == cudaSuccess; ++k) {
         css_parts* p = sets[k];
-        e = cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->mesh->frank, p->fcnt, p->fstart, p->fitems,
+        e = cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->mesh->frank, p->fcnt, p->fstart, p->fitems, p->ftmp,
                                 p->scan_tmp, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1137,6 +1166,7 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
 int css_trace_geodesics(css_parts* p, int64_t n_paths, const int32_t* src, const double* tangent,
                         const double* length, int32_t max_points, double* points, int32_t* n_points,
                         int32_t* end_face, double* end_bary) {
+    Range range_("css_trace_geodesics");
     if (!p || n_paths < 0 || max_points < 2 || (n_paths > 0 && (!src || !tangent || !length || !points || !n_points ||
                                                                  !end_face || !end_bary)))
         return CSS_ERR_INVALID_ARG;
@@ -1233,7 +1263,7 @@ int run_path_kernel(css_parts* p, double rc, const std::vector<int32_t>& us, con
     g.lbase = lbase;
     g.lstride = lstride;
     TRY(c, "bucket", cssi::launch_bucket((int32_t)p->n, (int32_t)p->mesh->nf, p->face, p->mesh->frank, p->fcnt,
-                                         p->fstart, p->fitems, p->scan_tmp, st));
+                                         p->fstart, p->fitems, p->ftmp, p->scan_tmp, st));
     GeoJob j = make_job(p, rc, 1, 0, nullptr);
     j.order = dus;
     j.lmax = PATH_MAX_LEGS;
@@ -1250,6 +1280,7 @@ int run_path_kernel(css_parts* p, double rc, const std::vector<int32_t>& us, con
 int css_geodesic_paths(css_parts* p, double r_c, int64_t n_pairs, const int32_t* src, const int32_t* dst,
                        int32_t max_points, double* points, int32_t* n_points, int32_t* n_legs, double* dist,
                        double* gap) {
+    Range range_("css_geodesic_paths");
     if (!p || bad_rc(r_c) || n_pairs < 0 || max_points < 2 ||
         (n_pairs > 0 && (!src || !dst || !points || !n_points || !n_legs || !dist || !gap)))
         return CSS_ERR_INVALID_ARG;

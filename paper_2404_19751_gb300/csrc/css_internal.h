@@ -108,6 +108,7 @@ struct css_parts {
     int32_t* fcnt = nullptr;    // nf (kept at zero between uses)
     int32_t* fstart = nullptr;  // nf + 1
     int32_t* fitems = nullptr;  // n
+    int32_t* ftmp = nullptr;    // n, scratch of the bucket scatter
     int32_t* scan_tmp = nullptr;
     int32_t* order = nullptr;   // source processing order (n)
     int64_t* dstep = nullptr;   // device copy of the step counter (Philox counter word)
@@ -169,6 +170,7 @@ struct SetView {
     int32_t* fcnt;
     int32_t* fstart;
     int32_t* fitems;
+    int32_t* ftmp;
     int64_t* dstep;
     uint64_t seed;
 };
@@ -218,8 +220,10 @@ cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* 
 // dynamics.cu
 // particles bucketed by face rank: fstart (nf + 1) is indexed by frank[face] (NULL: by
 // face), fitems lists the particles in rank order
+// face buckets of n particles: counts, offsets, then the particles of each face in index
+// order (ftmp: n ints of scratch for the unordered scatter)
 cudaError_t launch_bucket(int32_t n, int32_t nf, const int32_t* face, const int32_t* frank, int32_t* fcnt,
-                          int32_t* fstart, int32_t* fitems, int32_t* scan_tmp, cudaStream_t st);
+                          int32_t* fstart, int32_t* fitems, int32_t* ftmp, int32_t* scan_tmp, cudaStream_t st);
 size_t scan_tmp_ints(int64_t count);
 cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t count, int32_t* tmp,
                             cudaStream_t st);

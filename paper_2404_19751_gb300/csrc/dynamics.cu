@@ -112,6 +112,24 @@ __global__ void k_scatter(int32_t n, const int32_t* face, const int32_t* frank, 
     items[start[f] + p] = i;
 }
 
+// Deterministic bucket order: the scatter above fills each face's bucket in the order its
+// atomics happen to run; here particle i moves to its rank among the particles of its
+// face by index.  The bucket order is the order in which a source meets its targets, so it
+// fixes every force sum's order: runs repeat bit for bit.
+__device__ __forceinline__ void rank_in_bucket(int i, int key, const int32_t* start, const int32_t* tmp, int32_t* items) {
+    const int st = start[key], cnt = start[key + 1] - st;
+    int r = 0;
+    for (int q = 0; q < cnt; ++q) r += tmp[st + q] < i;
+    items[st + r] = i;
+}
+
+__global__ void k_rank(int32_t n, const int32_t* face, const int32_t* frank, const int32_t* start, const int32_t* tmp,
+                       int32_t* items) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    rank_in_bucket(i, frank ? frank[face[i]] : face[i], start, tmp, items);
+}
+
 // ------------------------------------------------------------------ face walk
 __device__ __forceinline__ void corner(const DMesh& m, int f, int k, double& x, double& y) {
     css::face_corner(m, f, k, x, y);
@@ -586,7 +604,16 @@ __global__ void k_batch_scatter(const cssi::SetView* sv, const int32_t* offs, in
     const int f = V.face[i];
     const int key = V.m.frank ? V.m.frank[f] : f;
     const int p = atomicSub(V.fcnt + key, 1) - 1;
-    V.fitems[V.fstart[key] + p] = i;
+    V.ftmp[V.fstart[key] + p] = i;
+}
+__global__ void k_batch_rank(const cssi::SetView* sv, const int32_t* offs, int nsets) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= offs[nsets]) return;
+    const int s = set_of(offs, nsets, k);
+    const cssi::SetView& V = sv[s];
+    const int i = k - offs[s];
+    const int f = V.face[i];
+    rank_in_bucket(i, V.m.frank ? V.m.frank[f] : f, V.fstart, V.ftmp, V.fitems);
 }
 
 
@@ -619,11 +646,12 @@ cudaError_t launch_scan_rows(const int32_t* cnt, int64_t* row_start, int32_t n, 
 }
 
 cudaError_t launch_bucket(int32_t n, int32_t nf, const int32_t* face, const int32_t* frank, int32_t* fcnt,
-                          int32_t* fstart, int32_t* fitems, int32_t* scan_tmp, cudaStream_t st) {
+                          int32_t* fstart, int32_t* fitems, int32_t* ftmp, int32_t* scan_tmp, cudaStream_t st) {
     k_count<<<nb(n), 256, 0, st>>>(n, face, frank, fcnt);
     cudaError_t e = launch_scan_i32(fcnt, fstart, (int64_t)nf + 1, scan_tmp, st);
     if (e != cudaSuccess) return e;
-    k_scatter<<<nb(n), 256, 0, st>>>(n, face, frank, fcnt, fstart, fitems);
+    k_scatter<<<nb(n), 256, 0, st>>>(n, face, frank, fcnt, fstart, ftmp);
+    k_rank<<<nb(n), 256, 0, st>>>(n, face, frank, fstart, ftmp, fitems);
     return cudaGetLastError();
 }
 
@@ -922,6 +950,7 @@ cudaError_t launch_batch_bucket(const SetView* sv, const int32_t* offs, int nset
     k_batch_count<<<nb(total), 256, 0, st>>>(sv, offs, nsets);
     k_batch_scan<<<nsets, SCAN_THREADS, 0, st>>>(sv);
     k_batch_scatter<<<nb(total), 256, 0, st>>>(sv, offs, nsets);
+    k_batch_rank<<<nb(total), 256, 0, st>>>(sv, offs, nsets);
     return cudaGetLastError();
 }
 

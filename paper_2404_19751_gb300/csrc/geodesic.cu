@@ -1850,7 +1850,8 @@ int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* f
     if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, 256 + 8 * 8, st);
     if (e == cudaSuccess && e_pot) e = cudaMemsetAsync(e_pot, 0, sizeof(double), st);
     if (e == cudaSuccess)
-        e = cssi::launch_bucket((int32_t)n, (int32_t)mesh->nf, face, mesh->frank, fcnt, fstart, fitems, scan, st);
+        // the pair-count region doubles as the scatter scratch: the kernel below rewrites it
+        e = cssi::launch_bucket((int32_t)n, (int32_t)mesh->nf, face, mesh->frank, fcnt, fstart, fitems, pcnt, scan, st);
     cssi::GeoJob j{};
     j.m = mesh->view();
     j.n = (int32_t)n;

@@ -539,3 +539,47 @@ def test_shortest_paths_reject_bad_pairs(ctx):
             axis=1)))], max_points=2)
     parts.free()
     mesh.free()
+
+
+@pytest.mark.parametrize("kind", [css.INT_BD, css.INT_ABP])
+def test_checkpoint_resume_is_bit_exact(ctx, kind):
+    """Checkpoint / resume: a stochastic run of 10 steps equals 5 steps, a checkpoint of the
+    state and the step counter (the noise counter) into a fresh set with the same seed, and
+    5 more steps, bit for bit.  Without the step counter the resumed run replays the noise
+    of steps 0-4 and differs.  All runs use one launch shape: different shapes sum a row's
+    FP64 forces in a different order, and a last-bit difference can flip a pair's tangent at
+    the cut locus of this over-packed workload."""
+    before = ctx.get_launch()
+    ctx.set_launch(warps_per_cta=4, ctas_per_sm=0, tile=1, shared_scale=0, window_capacity=32768,
+                   window_capacity2=32768, warps2_per_sm=2, occupancy=1)
+    m, face, bary, r_c = WORKLOADS["hfield64_n1024"]()
+    pot = dict(kind=css.POT_WCA, eps=1.0, sigma=r_c / 2 ** (1 / 6), r_cut=r_c)
+    integ = dict(kind=kind, dt=1e-5, kT=1.0, lam=1.0, v0=1.0, Dr=1.0, mass=1.0, max_disp=0.5 * r_c)
+    orient = synth.random_tangent_units(m, face, 3) if kind == css.INT_ABP else None
+    mesh, a = _setup(ctx, m, face, bary, None, orient, seed=9)
+    css.integrate_step(a, pot, integ, r_c, css.FP64, 10)
+    full = css.particles_get(a)
+    b = css.particles_set(ctx, mesh, face, bary, None, orient, seed=9)
+    css.integrate_step(b, pot, integ, r_c, css.FP64, 5)
+    ck = css.particles_get(b)
+    assert ck["step"] == 5
+    results = []
+    for restore in (True, False):
+        c = css.particles_set(ctx, mesh, ck["face"], ck["bary"], ck["vel"], ck["orient"], seed=9)
+        if restore:
+            css.particles_set_step(c, ck["step"])
+        css.integrate_step(c, pot, integ, r_c, css.FP64, 5)
+        results.append(css.particles_get(c))
+        c.free()
+    r, r0 = results
+    assert r["step"] == 10
+    np.testing.assert_array_equal(r["face"], full["face"])
+    np.testing.assert_array_equal(r["bary"], full["bary"])
+    np.testing.assert_array_equal(r["orient"], full["orient"])
+    assert not np.array_equal(r0["bary"], full["bary"])
+    with pytest.raises(css.CssError):
+        css.particles_set_step(a, -1)
+    ctx.set_launch(**before)
+    a.free()
+    b.free()
+    mesh.free()
