@@ -191,7 +191,8 @@ int css_integrate_step(css_parts* parts, const css_potential* pot, const css_int
  * bends at no vertex (Sec. 2.2: shortest paths are straight in the unfolding of the faces
  * they cross) -- the end point then coincides with the neighbour, which callers can check
  * with end_face / end_bary.  Paths that bend at saddle, flat or boundary vertices are not
- * followed around the bend (the walk goes straight on).
+ * followed around the bend (the walk goes straight on); css_geodesic_paths returns those
+ * paths with their bends.
  *   points   n_paths x max_points x 3 world positions: the start, every edge or vertex
  *            crossing, the end; unused entries are zero; max_points >= 2;
  *   n_points all points of each path (more than max_points when truncated);
