@@ -472,3 +472,22 @@ def test_bent_paths_on_a_noisy_sphere_land_on_their_nodes():
         np.testing.assert_allclose(P[0], x[S[p]], atol=1e-13)
         np.testing.assert_allclose(P[-1], x[j[p]], atol=1e-13)
         assert np.sum(np.linalg.norm(np.diff(P, axis=0), axis=1)) == pytest.approx(d[p], rel=1e-12)
+
+
+def test_holed_sheet_distances_are_the_visibility_graph_distances():
+    """All pairs of 24 random points of a flat sheet with a square hole: the window
+    propagation's distances (boundary vertices act as pseudo-sources) equal the
+    visibility-graph shortest paths around the hole to 1e-12, and every pair's polyline
+    lands on its nodes."""
+    m = synth.holed_plane(21, (0.4, 0.6, 0.4, 0.6))
+    om = O.OracleMesh(m)
+    face, bary = synth.place_uniform(m, 24, 17)
+    x = om.world(face, bary)
+    rs, j, d = om.neighbors(face, bary, math.inf)[:3]
+    src = np.repeat(np.arange(len(face)), np.diff(rs))
+    assert len(j) == 24 * 23
+    for k in range(len(j)):
+        _, L = _taut_string(x[src[k]], x[j[k]], 0.4, 0.6)
+        assert d[k] == pytest.approx(L, rel=1e-12, abs=1e-15)
+    paths, legs, dist, gap = om.geodesic_paths(face, bary, math.inf, src.astype(np.int32), j)
+    assert np.max(gap) < 1e-13 and np.sum(legs >= 2) > 20
