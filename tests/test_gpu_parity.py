@@ -42,6 +42,9 @@ WORKLOADS = {
     "ico5_n1024": lambda: (lambda c: (c["mesh"], c["face"], c["bary"], c["r_c"]))(synth.make_config("ico5_n1024")),
     "noisy_ico5_n2048": lambda: _noisy5() + (0.15,),
     "hfield64_n1024": lambda: _hfield_small() + (0.12,),
+    # open sheet with a square hole: paths wrap the hole's reflex corners (boundary pseudo-sources)
+    "holed_plane21_n200": lambda: (lambda m: (m,) + synth.place_uniform(m, 200, 6) + (0.3,))(
+        synth.holed_plane(21, (0.4, 0.6, 0.4, 0.6))),
 }
 
 
