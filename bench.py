@@ -243,6 +243,14 @@ def describe(cfg, world):
             "l2": "256 MiB flush between timed steps", "parallelism": f"replicas x{world}"}
 
 
+def counter_reader(ctx):
+    """Reads what the last library call measured: its neighbour-kernel time and counts."""
+    def read():
+        c = ctx.last_counters()
+        return ctx.last_kernel_ms(), c["pairs"], c["propagated"]
+    return read
+
+
 class Timer:
     """Per-step CUDA events on the library's stream, an L2-flushing write before each
     timed step (outside the events), clocks sampled during the timed region."""
@@ -265,9 +273,12 @@ class Timer:
                 with torch.cuda.stream(self.stream):
                     self.flush.zero_()
                     ev[k][0].record(self.stream)
-                km, pc, pp = step()
+                r = step()
                 with torch.cuda.stream(self.stream):
                     ev[k][1].record(self.stream)
+                # a step may hand back a reader of its counters, so that reading them (bench
+                # bookkeeping, not part of the step) happens after the end event
+                km, pc, pp = r() if callable(r) else r
                 kms.append(km)
                 pairs += pc
                 props += pp
@@ -366,10 +377,11 @@ def run_single(args, cfg, css, ctx, torch, stream, timer, rank, world):
         # the library's autotuner picks the launch shape for this workload (outside the timing)
         shape, _ = ctx.autotune([parts], pot, rc, prec, reps=3, sample=min(n, 16384))
 
+        counters = counter_reader(ctx)
+
         def step():
             css.integrate_step(parts, pot, integ, rc, prec, 1)
-            c = ctx.last_counters()
-            return ctx.last_kernel_ms(), c["pairs"], c["propagated"]
+            return counters
         r = timer.run(step, steps, warmup, True)
         r["launch"] = shape
         parts.free()
@@ -485,10 +497,11 @@ def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
         # the autotuner picks warps, residency, table scale and work tile for the batch
         shape, _ = ctx.autotune(sets, pot, rc, prec, reps=3, sample=32768)
 
+        counters = counter_reader(ctx)
+
         def step():
             css.batch_step(b, pot, integ, rc, prec, 1)
-            c = ctx.last_counters()
-            return ctx.last_kernel_ms(), c["pairs"], c["propagated"]
+            return counters
         r = timer.run(step, steps, warmup, True)
         r["launch"] = shape
         b.free()
