@@ -6,7 +6,7 @@ none of the geodesic, force or face-walk arithmetic; both the CPU oracle and
 the CUDA library consume what it generates.
 """
 from .meshes import (  # noqa: F401
-    grid_plane, holed_plane, cylinder_tube, cube, tetrahedron, octahedron, icosphere,
+    grid_plane, holed_plane, saddle_fan, cylinder_tube, cube, tetrahedron, octahedron, icosphere,
     torus, periodic_heightfield, bbox_diagonal, Mesh,
 )
 from .particles import place_uniform, gaussian_tangent_velocities, random_tangent_units  # noqa: F401

@@ -71,6 +71,45 @@ def holed_plane(n: int = 21, hole=(0.4, 0.6, 0.4, 0.6)) -> Mesh:
     return _mk(g.verts[used], remap[faces], name=f"holed_plane{n}")
 
 
+def saddle_fan(n_sectors: int = 8, subdiv: int = 4) -> Mesh:
+    """Open fan of n_sectors (even) equilateral triangles of unit side around one apex, each
+    split flat into subdiv^2 triangles.  The rim vertices alternate above and below the
+    apex's plane so that consecutive ones are one unit apart: the apex's total angle is
+    n_sectors * pi/3 (8 sectors: 8 pi/3 > 2 pi, a saddle vertex).  meta["rim"] holds the
+    rim directions (unit vectors from the apex)."""
+    assert n_sectors % 2 == 0 and n_sectors >= 6
+    dlon = 2 * np.pi / n_sectors
+    # latitude b with chord 1 between (b, 0) and (-b, dlon): cos 60deg = cos^2 b cos dlon - sin^2 b
+    c2 = 1.5 / (1.0 + np.cos(dlon))
+    b = np.arccos(np.sqrt(c2))
+    rim = np.array([[np.cos(b) * np.cos(k * dlon), np.cos(b) * np.sin(k * dlon), (1 if k % 2 == 0 else -1) * np.sin(b)]
+                    for k in range(n_sectors)])
+    verts, faces, index = [], [], {}
+
+    def vid(s_, i, j):
+        # point apex + (i/subdiv) u_s + (j/subdiv) u_{s+1}, i + j <= subdiv; shared across sectors
+        if i + j == 0:
+            key = ("apex",)
+        elif j == 0:
+            key = ("ray", s_ % n_sectors, i)
+        elif i == 0:
+            key = ("ray", (s_ + 1) % n_sectors, j)
+        else:
+            key = ("in", s_ % n_sectors, i, j)
+        if key not in index:
+            index[key] = len(verts)
+            verts.append((i * rim[s_ % n_sectors] + j * rim[(s_ + 1) % n_sectors]) / subdiv)
+        return index[key]
+
+    for s_ in range(n_sectors):
+        for i in range(subdiv):
+            for j in range(subdiv - i):
+                faces.append((vid(s_, i, j), vid(s_, i + 1, j), vid(s_, i, j + 1)))
+                if i + j + 2 <= subdiv:
+                    faces.append((vid(s_, i + 1, j), vid(s_, i + 1, j + 1), vid(s_, i, j + 1)))
+    return _mk(np.array(verts), faces, name=f"saddle_fan{n_sectors}", rim=rim)
+
+
 def cylinder_tube(n_around: int = 12, n_along: int = 6, radius: float = 1.0,
                   height: float = 2.0) -> Mesh:
     """Open prism tube (n_around-gon cross-section) of the given height, outward normals."""

@@ -45,6 +45,8 @@ WORKLOADS = {
     # open sheet with a square hole: paths wrap the hole's reflex corners (boundary pseudo-sources)
     "holed_plane21_n200": lambda: (lambda m: (m,) + synth.place_uniform(m, 200, 6) + (0.3,))(
         synth.holed_plane(21, (0.4, 0.6, 0.4, 0.6))),
+    # an interior saddle vertex (total angle 8 pi/3): paths between far-apart sectors bend there
+    "saddle_fan8_n40": lambda: (lambda m: (m,) + synth.place_uniform(m, 40, 12) + (math.inf,))(synth.saddle_fan(8, 4)),
 }
 
 
@@ -466,7 +468,8 @@ def _holed():
     return m, face, bary, math.inf
 
 
-PATH_WORKLOADS = {"holed_plane21_n48": _holed, "noisy_ico5_n2048": WORKLOADS["noisy_ico5_n2048"],
+PATH_WORKLOADS = {"holed_plane21_n48": _holed, "saddle_fan8_n40": WORKLOADS["saddle_fan8_n40"],
+                  "noisy_ico5_n2048": WORKLOADS["noisy_ico5_n2048"],
                   "hfield64_n1024": WORKLOADS["hfield64_n1024"], "flat64": WORKLOADS["flat64"]}
 
 
@@ -524,7 +527,7 @@ def test_shortest_paths_with_bends_match_oracle(ctx, name):
             same = bool(np.max(np.abs(dd)) < 1e-9)
         differ += not same
     assert differ <= 0.02 * fin.sum()
-    if name in ("holed_plane21_n48", "noisy_ico5_n2048"):
+    if name in ("holed_plane21_n48", "saddle_fan8_n40", "noisy_ico5_n2048"):
         assert np.sum(gl >= 2) >= 10          # the sample holds bent paths
     parts.free()
     mesh.free()

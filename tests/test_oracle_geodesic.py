@@ -491,3 +491,57 @@ def test_holed_sheet_distances_are_the_visibility_graph_distances():
         assert d[k] == pytest.approx(L, rel=1e-12, abs=1e-15)
     paths, legs, dist, gap = om.geodesic_paths(face, bary, math.inf, src.astype(np.int32), j)
     assert np.max(gap) < 1e-13 and np.sum(legs >= 2) > 20
+
+
+def _fan_point(m, r, phi):
+    """(face, bary) of the point at intrinsic polar coordinates (r, phi) around the apex of
+    a saddle fan (phi counted across the sectors, each sector pi/3 wide)."""
+    rim = m.meta["rim"]
+    k = len(rim)
+    s = int(phi // (math.pi / 3)) % k
+    psi = phi - s * math.pi / 3
+    p = r * (math.sin(math.pi / 3 - psi) * rim[s] + math.sin(psi) * rim[(s + 1) % k]) / math.sin(math.pi / 3)
+    best = None
+    for f, tri in enumerate(m.verts[m.faces]):
+        A = np.stack([tri[1] - tri[0], tri[2] - tri[0]], axis=1)
+        l, res, *_ = np.linalg.lstsq(A, p - tri[0], rcond=None)
+        b = np.array([1 - l.sum(), l[0], l[1]])
+        err = np.linalg.norm(A @ l - (p - tri[0]))
+        if b.min() > -1e-12 and err < 1e-12 and (best is None or b.min() > best[2].min()):
+            best = (f, p, b)
+    return best
+
+
+def test_saddle_vertex_distances_and_bends_are_the_cone_closed_form():
+    """An interior saddle vertex: a fan of 8 equilateral triangles has total angle 8 pi/3 at
+    its apex, a cone whose developed angle exceeds 2 pi.  Two points at intrinsic radii r1,
+    r2 and angular separation D (the smaller of the two ways round) are straight apart,
+    sqrt(r1^2 + r2^2 - 2 r1 r2 cos D), when D < pi; otherwise the shortest path bends at the
+    apex and is r1 + r2 long (Sec. 2.2: shortest paths bend only at saddle or boundary
+    vertices).  Checks the distances of all pairs, one leg or two legs meeting at the apex,
+    and the polyline length."""
+    m = synth.saddle_fan(8, 4)
+    om = O.OracleMesh(m)
+    theta = 8 * math.pi / 3
+    rng = np.random.default_rng(21)
+    pts = [(rng.uniform(0.1, 0.45), rng.uniform(0.0, theta)) for _ in range(14)]
+    loc = [_fan_point(m, r, ph) for r, ph in pts]
+    face = np.array([l[0] for l in loc], np.int32)
+    bary = np.array([l[2] for l in loc])
+    rs, j, d = om.neighbors(face, bary, math.inf)[:3]
+    src = np.repeat(np.arange(len(pts)), np.diff(rs))
+    paths, legs, dist, gap = om.geodesic_paths(face, bary, math.inf, src.astype(np.int32), j)
+    bent = 0
+    for k in range(len(j)):
+        (r1, p1), (r2, p2) = pts[src[k]], pts[j[k]]
+        D = abs(p1 - p2) % theta
+        D = min(D, theta - D)
+        L = r1 + r2 if D >= math.pi else math.sqrt(r1 * r1 + r2 * r2 - 2 * r1 * r2 * math.cos(D))
+        assert d[k] == pytest.approx(L, rel=1e-12)
+        assert np.sum(np.linalg.norm(np.diff(paths[k], axis=0), axis=1)) == pytest.approx(L, rel=1e-12)
+        if D > math.pi + 1e-6:
+            bent += 1
+            assert legs[k] == 2 and np.min(np.linalg.norm(paths[k], axis=1)) < 1e-13   # through the apex
+        elif D < math.pi - 1e-6:
+            assert legs[k] == 1
+    assert bent >= 20 and np.max(gap) < 1e-13
