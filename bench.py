@@ -1,12 +1,16 @@
 #!/usr/bin/env python
 """Benchmark: cutoff geodesic pair evaluations/s and MD steps/s on one GB300.
 
-Workload (default): the icosphere workload -- level-5 icosphere of radius 1
-(20480 faces), 1024 particles uniform on the surface, cutoff r_c = 0.15, harmonic
-repulsion sigma = 0.15, velocity-Verlet NVE at dt = 0.002.  A "step" is one full MD
-step through the C ABI: face bucketing, geodesic neighbours by window propagation,
-forces, the face-walk drift and both kicks.  The headline precision is the FP32 form;
-the FP64 form is measured beside it.
+Workload (default): the large noisy sphere -- level-8 icosphere of radius 10 (1,310,720
+faces) with vertices displaced radially by 0.02 N(0,1), 65536 active Brownian particles
+(v0 = 1, D_r = 0.1), WCA with sigma = 0.2 and r_c = 2^(1/6) sigma, dt = 1e-3.  A "step"
+is one full MD step through the C ABI: face bucketing, geodesic neighbours by window
+propagation, forces, the face walk and the orientation update.  The headline precision is
+the FP32 form (one persistent launch over all sources, the step replayed from a captured
+CUDA graph); the FP64 form is measured beside it on the same workload.  The many-mesh
+workload (64 tori of 2k-60k faces, 128-4096 particles each, NVE) is measured in the same
+run and reported under "batched_tori64": the FP32 batched form (one persistent launch
+over all meshes' sources) against the plain FP64 path (one call per mesh).
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on the
 library's stream, with a 256 MiB L2-flushing write between timed steps (outside the
@@ -15,7 +19,7 @@ events); barrier + synchronize around the timed region, max over ranks.  With
 across GPUs in this build), "scaling": "weak".
 
 --impl reference times the CPU oracle (plain FP64 C, OpenMP over sources) on the
-same workload, each step a full oracle MD step.
+same workload, each step a full oracle MD step of a bounded sample of the particles.
 """
 from __future__ import annotations
 
@@ -38,10 +42,32 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FLOPS_PER_PROPAGATION = 150.0   # one window unfolding + child trimming (FP arithmetic)
 FLOPS_PER_PAIR = 20.0           # one target evaluation
 BYTES_PER_FACE = 64.0           # patch mesh data a source must read per face reached
-# DRAM bytes (read + write) of one first-pass launch of the FP32 neighbour kernel, from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernel on the
-# icosphere workload; other workloads were not captured at full size
-TRAFFIC_BYTES = {"ico5_n1024": 11.947e6 + 2.231e6}
+BYTES_PER_WINDOW = 48.0         # one window record written and read back per propagation
+BYTES_PER_PAIR = 20.0           # one FP32 output row entry (j, distance, tangent)
+BYTES_PER_SOURCE = 24.0         # the source's force
+DEFAULT_WORKLOAD = "noisy_ico8_n65536"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one first-pass launch of the
+# FP32 neighbour kernel from an ncu capture, per workload: bytes, the sources that launch
+# processed (the figure is scaled to a full launch by sources) and a digest of the kernel
+# sources it was taken on; a kernel changed since then reports null
+TRAFFIC = {}
+KERNEL_SOURCES = ("paper_2404_19751_gb300/csrc/geodesic.cu", "paper_2404_19751_gb300/csrc/css_dev.cuh",
+                  "paper_2404_19751_gb300/csrc/css_internal.h")
+
+
+def kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(name: str, n_sources: int):
+    t = TRAFFIC.get(name)
+    if not t or t["kernel"] != kernel_digest():
+        return None
+    return t["bytes"] * n_sources / t["sources"]
 
 
 def parse():
@@ -50,8 +76,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ico5_n1024")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the nested many-mesh measurement of the default workload")
     ap.add_argument("--sweep", choices=["n", "v"], default=None,
                     help="time per MD step against particle count (n) or mesh size (v) on a torus, "
                          "with the fitted power-law exponents (not the benchmark line)")
@@ -289,12 +317,20 @@ class Timer:
         return dict(t=t, steps=steps, kernel_ms=kms, pairs=pairs, props=props, clocks=clk.summary())
 
 
+def csr_to_dict(rs, j, d, t):
+    """{(i, j): (distance, tangent)} of a CSR neighbour result."""
+    out = {}
+    for i in range(len(rs) - 1):
+        for q in range(rs[i], rs[i + 1]):
+            out[(i, int(j[q]))] = (float(d[q]), t[q])
+    return out
+
+
 def accuracy(css, ctx, cases):
     """Max distance error of both forms against the oracle on (mesh handle, synth mesh,
     face, bary, r_c) cases, relative to each mesh's bounding-box diagonal."""
     import synth
     from oracle import oracle as O
-    from tests._common import csr_to_dict
     acc = {}
     for prec, nm in ((css.FP32, "fp32"), (css.FP64, "fp64")):
         worst, only = 0.0, 0
@@ -315,22 +351,29 @@ def accuracy(css, ctx, cases):
 
 
 def roofline(css, ctx, pk, props_per_src, n, pairs_per_launch, kern_s, kernel_name, traffic=None):
+    """ALU roofline of the neighbour kernel (algorithmic FP32 flops per launch over the
+    nominal FP32 peak) and its memory roofline (algorithmic bytes over measured HBM)."""
     fp32_peak_nominal = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     alg_flops = n * props_per_src * FLOPS_PER_PROPAGATION + pairs_per_launch * FLOPS_PER_PAIR
     achieved = alg_flops / kern_s
     faces_per_src = props_per_src / 2.0     # about two windows enter each face reached
-    alg_bytes = n * faces_per_src * BYTES_PER_FACE + pairs_per_launch * 24.0
+    alg_bytes = (n * (faces_per_src * BYTES_PER_FACE + props_per_src * BYTES_PER_WINDOW + BYTES_PER_SOURCE) +
+                 pairs_per_launch * BYTES_PER_PAIR)
     hbm = float(pk.get("hbm_gbs", 6800.0)) * 1e9
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak_nominal / 1e12,
             "unit": "TFLOP/s", "frac": achieved / fp32_peak_nominal, "traffic": traffic,
             "kernel": kernel_name, "kernel_ms": kern_s * 1e3,
-            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (nominal; no measured FP32 peak)",
             "fma_probe_tflops": {"fp32": ctx.fma_peak(css.FP32) / 1e12, "fp64": ctx.fma_peak(css.FP64) / 1e12},
             "algorithmic": {"propagations_per_source": props_per_src,
                             "flops_per_propagation": FLOPS_PER_PROPAGATION,
                             "flops_per_pair": FLOPS_PER_PAIR, "flops_per_launch": alg_flops}}
-    mem = {"achieved_gbs": alg_bytes / kern_s / 1e9, "peak_gbs": hbm / 1e9,
-           "frac": alg_bytes / kern_s / hbm, "bytes_per_launch": alg_bytes}
+    mem = {"achieved_gbs": alg_bytes / kern_s / 1e9, "peak_gbs": hbm / 1e9, "peak_basis": "measured HBM copy",
+           "frac": alg_bytes / kern_s / hbm, "bytes_per_launch": alg_bytes,
+           "bytes_model": f"per source {BYTES_PER_FACE:g} B x faces reached (propagations / 2) + "
+                          f"{BYTES_PER_WINDOW:g} B x windows propagated + {BYTES_PER_SOURCE:g} B force; "
+                          f"{BYTES_PER_PAIR:g} B per pair",
+           "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None}
     return roof, mem
 
 
@@ -360,6 +403,12 @@ def run_ours(args, rank: int, world: int):
         line = run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world)
     else:
         line = run_single(args, cfg, css, ctx, torch, stream, timer, rank, world)
+        if args.workload == DEFAULT_WORKLOAD and not args.no_batched:
+            # the many-mesh batched form, measured in the same run and nested in the line
+            nested = run_batched(args, workload("tori64"), css, ctx, torch, stream, timer, rank, world,
+                                 nested=True)
+            if line is not None and nested is not None:
+                line["batched_tori64"] = nested
     if rank == 0 and line:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -430,7 +479,7 @@ def run_single(args, cfg, css, ctx, torch, stream, timer, rank, world):
         props_per_src = r32["props"] / max(1, k32 * n)
     roof, mem = roofline(css, ctx, pk, props_per_src, n, r32["pairs"] / k32,
                          statistics.mean(r32["kernel_ms"]) / 1e3, "k_geodesic<float>",
-                         traffic=TRAFFIC_BYTES.get(cfg["name"]))
+                         traffic=traffic_per_launch(cfg["name"], n))
     line = {
         "metric": METRIC, "value": replica_throughput(world, r32["pairs"], t32), "unit": UNIT, "n_gpus": world, "steps": k32,
         "warmup": args.warmup, "ms_per_step": 1e3 * t32 / k32, "higher_is_better": True, "scaling": "weak",
@@ -451,6 +500,7 @@ def run_single(args, cfg, css, ctx, torch, stream, timer, rank, world):
         # and second pass (2) + kick or step counter (1)
         "gpu_launches": 10 * k32,
         "clocks": r32["clocks"],
+        "kernel_digest": kernel_digest(),
     }
     if cb:
         line["cpu_baseline"] = cb
@@ -475,10 +525,12 @@ def e2e_time(torch, stream, step, args, dist):
     return t, pairs
 
 
-def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
+def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world, nested=False):
     """Many independent meshes: the FP32 batched form (one persistent launch per step over
     every source of every mesh, inside a captured graph) against the plain FP64 path (one
-    integrate call per mesh), both forms of both shown."""
+    integrate call per mesh), both forms of both shown.  nested: the compact record that
+    the default workload's line carries (FP32 batched vs FP64 plain, accuracy on three
+    meshes, the same timing rules; no CPU baseline or end-to-end loop)."""
     import numpy as np
     items = cfg["items"]
     pot, integ, rc = cfg["pot"], cfg["integ"], cfg["r_c"]
@@ -527,12 +579,10 @@ def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
             p.free()
         return r
 
+    saved_shape = ctx.get_launch()
     r32b = batched(css.FP32, args.steps, args.warmup)
     ks = max(3, args.steps // 2)
     r64p = plain(css.FP64, ks, max(3, args.warmup))
-    r64b = batched(css.FP64, ks, max(3, args.warmup))
-    r32p = plain(css.FP32, ks, max(3, args.warmup))
-    ctx.set_launch(**r32b["launch"])
 
     def rate(r):
         return replica_throughput(world, r["pairs"], r["t"])
@@ -542,6 +592,33 @@ def run_batched(args, cfg, css, ctx, torch, stream, timer, rank, world):
                 "mesh_steps_per_s": world * len(items) * r["steps"] / r["t"],
                 "ms_per_step": 1e3 * r["t"] / r["steps"], "kernel_ms": statistics.mean(r["kernel_ms"]),
                 "clocks": r["clocks"]}
+    if nested:
+        ctx.set_launch(**saved_shape)
+        out = None
+        if rank == 0:
+            order = np.argsort([len(it["face"]) for it in items], kind="stable")
+            pick = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+            try:
+                acc = accuracy(css, ctx, [(meshes[k], items[k]["mesh"], items[k]["face"], items[k]["bary"], rc, None)
+                                          for k in pick])
+                acc["sampled_meshes"] = pick
+            except Exception as e:
+                acc = {"error": str(e)}
+            out = {"workload": cfg["name"], "config": dict(describe(cfg, world),
+                                                           precision="FP32 form, batched (one launch over all meshes)",
+                                                           launch=r32b["launch"]),
+                   **sub(r32b, "FP32 form, batched: one persistent launch per step over all meshes"),
+                   "steps": r32b["steps"], "pairs_per_step": r32b["pairs"] / r32b["steps"],
+                   "particle_steps_per_s": world * n * r32b["steps"] / r32b["t"],
+                   "fp64": sub(r64p, "plain FP64: one integrate call per mesh"),
+                   "fp32_batched_over_fp64": rate(r32b) / rate(r64p), "accuracy_vs_oracle": acc,
+                   "gpu_launches": 8 * r32b["steps"]}
+        for mh in meshes:
+            mh.free()
+        return out
+    r64b = batched(css.FP64, ks, max(3, args.warmup))
+    r32p = plain(css.FP32, ks, max(3, args.warmup))
+    ctx.set_launch(**r32b["launch"])
     # ---- end to end: every mesh's state up from pinned host memory, one batched step, all
     # states back, every step
     sets = make_sets()

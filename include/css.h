@@ -252,14 +252,23 @@ int css_batch_free(css_batch* batch);
  * css_compute_forces, for particles given directly as device arrays, and calls no
  * cudaMalloc, cudaFree or allocating library routine: its scratch is one fixed device
  * array of about 59 MB that every GPU loading this library holds until exit.
- *   mesh     uploaded beforehand with css_mesh_upload (that call allocates);
+ *   mesh     uploaded beforehand with css_mesh_upload (that call allocates); the call runs
+ *            on the device of the mesh's context, whatever device is current, and puts
+ *            the caller's current device back before it returns;
  *   face     device int32[n]; bary device double[n x 3]; forces device double[n x 3];
  *   e_pot    device double[1] or NULL (zeroed, then summed into);
- *   stream   cudaStream_t to run on (NULL: the legacy default stream); the call
- *            synchronises it to read the status.
+ *   stream   cudaStream_t of the mesh's device to run on (NULL: that device's legacy
+ *            default stream); the call first makes it wait for the work queued on the
+ *            context's stream (an update or a step writing face / bary), and synchronises
+ *            it to read the status.
+ * The particle arrays are checked on the device before any kernel indexes with them: a
+ * face outside [0, nf) or a barycentric triple that is not finite, has an entry below
+ * -1e-12 or does not sum to 1 within 1e-9 gives CSS_ERR_INVALID_ARG, as does a stream of
+ * another device.
  * Limits: n <= 262144 particles, at most 1048576 faces, 2048 windows per source and
  * warp; beyond them it returns CSS_ERR_CAPACITY (sizes) or CSS_ERR_QUEUE_OVERFLOW (a
- * source needing more windows), and css_compute_forces should be used instead.
+ * source needing more windows), and css_compute_forces should be used instead; a device
+ * loop cap gives CSS_ERR_ITER_LIMIT.
  * The first call on a device looks up the array's device address (set-up): make it
  * before any stream capture.  Every call shares the array, which keeps the previous
  * call's contents, so calls that overlap on the GPU (other streams, other host threads)

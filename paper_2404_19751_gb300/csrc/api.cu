@@ -343,7 +343,8 @@ int css_create(css_ctx** out, int device, void* stream) {
         css_destroy(c);
         return CSS_ERR_OOM;
     }
-    if (cudaEventCreate(&c->ev_geo0) != cudaSuccess || cudaEventCreate(&c->ev_geo1) != cudaSuccess) {
+    if (cudaEventCreate(&c->ev_geo0) != cudaSuccess || cudaEventCreate(&c->ev_geo1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_order, cudaEventDisableTiming) != cudaSuccess) {
         css_destroy(c);
         return CSS_ERR_CUDA;
     }
@@ -367,6 +368,7 @@ int css_destroy(css_ctx* c) {
     cudaFreeHost(c->hcount);
     if (c->ev_geo0) cudaEventDestroy(c->ev_geo0);
     if (c->ev_geo1) cudaEventDestroy(c->ev_geo1);
+    if (c->ev_order) cudaEventDestroy(c->ev_order);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return CSS_OK;
@@ -778,12 +780,18 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
         p->fire_valid = 1;
         p->fire_it = *it;
     }
+    // host noise is staged in a device buffer that this guard frees on every return path
+    struct NoiseBuf {
+        double* owned = nullptr;
+        ~NoiseBuf() { cudaFree(owned); }
+    } staged;
     double* dnoise = nullptr;
     if (noise) {
         const size_t cnt = (size_t)n_steps * p->n * 2;
         if (is_device_ptr(noise)) dnoise = const_cast<double*>(noise);
         else {
-            TRY(c, "noise", cudaMalloc(&dnoise, cnt * sizeof(double)));
+            TRY(c, "noise", cudaMalloc(&staged.owned, cnt * sizeof(double)));
+            dnoise = staged.owned;
             TRY(c, "noise", cudaMemcpyAsync(dnoise, noise, cnt * sizeof(double), cudaMemcpyHostToDevice, st));
         }
     }
@@ -825,7 +833,6 @@ int css_integrate_step(css_parts* p, const css_potential* pot, const css_integra
         if (!grow_for(c, status, &retries)) { rc = status_error(c, status); break; }
         TRY(c, "restore", snap_restore(p));
     }
-    if (noise && !is_device_ptr(noise)) cudaFree(dnoise);
     if (rc) return rc;
     p->step += n_steps;
     p->force_valid = 1;

@@ -60,6 +60,9 @@ struct css_ctx {
     int64_t last_counters[6] = {0, 0, 0, 0, 0, 0};
     cudaEvent_t ev_geo0 = nullptr, ev_geo1 = nullptr;   // around the neighbour/force kernel
     int ev_valid = 0;
+    // orders work on another stream after what is queued on `stream` (made at creation so
+    // that the allocation-free entry point creates nothing)
+    cudaEvent_t ev_order = nullptr;
 };
 
 struct css_mesh {

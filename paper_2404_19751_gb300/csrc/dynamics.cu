@@ -113,14 +113,45 @@ __global__ void k_scatter(int32_t n, const int32_t* face, const int32_t* frank, 
 }
 
 // Deterministic bucket order: the scatter above fills each face's bucket in the order its
-// atomics happen to run; here particle i moves to its rank among the particles of its
-// face by index.  The bucket order is the order in which a source meets its targets, so it
-// fixes every force sum's order: runs repeat bit for bit.
+// atomics happen to run; here each bucket is put in particle-index order.  The bucket order
+// is the order in which a source meets its targets, so it fixes every force sum's order:
+// runs repeat bit for bit.  A bucket of up to RANK_SCAN particles is ranked by its members
+// in parallel (each counts the smaller indices, at most RANK_SCAN reads); a larger one is
+// sorted by its first member alone with an in-place heap sort, O(b log b), so a crowded
+// face costs no b^2 work.
+constexpr int RANK_SCAN = 32;
+
+__device__ __forceinline__ void heap_sift(int32_t* a, int root, int end) {
+    const int32_t v = a[root];
+    for (;;) {
+        int c = 2 * root + 1;
+        if (c >= end) break;
+        if (c + 1 < end && a[c + 1] > a[c]) ++c;
+        if (a[c] <= v) break;
+        a[root] = a[c];
+        root = c;
+    }
+    a[root] = v;
+}
+
 __device__ __forceinline__ void rank_in_bucket(int i, int key, const int32_t* start, const int32_t* tmp, int32_t* items) {
     const int st = start[key], cnt = start[key + 1] - st;
-    int r = 0;
-    for (int q = 0; q < cnt; ++q) r += tmp[st + q] < i;
-    items[st + r] = i;
+    if (cnt <= RANK_SCAN) {
+        int r = 0;
+        for (int q = 0; q < cnt; ++q) r += tmp[st + q] < i;
+        items[st + r] = i;
+        return;
+    }
+    if (tmp[st] != i) return;   // the bucket's first member sorts it
+    int32_t* a = items + st;
+    for (int q = 0; q < cnt; ++q) a[q] = tmp[st + q];
+    for (int r = cnt / 2 - 1; r >= 0; --r) heap_sift(a, r, cnt);
+    for (int e = cnt - 1; e > 0; --e) {
+        const int32_t t = a[0];
+        a[0] = a[e];
+        a[e] = t;
+        heap_sift(a, 0, e);
+    }
 }
 
 __global__ void k_rank(int32_t n, const int32_t* face, const int32_t* frank, const int32_t* start, const int32_t* tmp,

@@ -1804,6 +1804,58 @@ struct NaDevice {
 };
 NaDevice g_na[64];
 
+// The caller's particle arrays are checked on the device before any kernel indexes with
+// them: a face index outside [0, nf), or a barycentric triple that is not finite, has an
+// entry below -1e-12 or does not sum to 1 within 1e-9 (the rule css_particles_set applies
+// on the host), sets ST_BAD_INPUT and nothing else runs.
+__global__ void k_na_validate(int32_t n, int32_t nf, const int32_t* face, const double* bary, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t f = face[i];
+    const double a = bary[3 * (size_t)i], b = bary[3 * (size_t)i + 1], c = bary[3 * (size_t)i + 2];
+    const bool ok = f >= 0 && f < nf && isfinite(a) && isfinite(b) && isfinite(c) && a >= -1e-12 && b >= -1e-12 &&
+                    c >= -1e-12 && fabs(a + b + c - 1.0) <= 1e-9;
+    if (!ok) atomicOr(status, css::ST_BAD_INPUT);
+}
+
+// the current device for the lifetime of the guard, then the caller's again
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t set(int dev) {
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e != cudaSuccess) { prev = -1; return e; }
+        if (prev == dev) { prev = -1; return cudaSuccess; }
+        e = cudaSetDevice(dev);
+        if (e != cudaSuccess) prev = -1;
+        return e;
+    }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+// status bits of the kernel -> C ABI code and message
+int na_status_error(css_ctx* c, int status) {
+    if (status & css::ST_BAD_INPUT) {
+        c->err = "compute_forces_noalloc: a face index is out of range or a barycentric triple is not finite, "
+                 "non-negative and summing to 1";
+        return CSS_ERR_INVALID_ARG;
+    }
+    if (status & (css::ST_WIN_OVERFLOW | css::ST_HASH_OVERFLOW)) {
+        c->err = "compute_forces_noalloc: a source needs more than the fixed window workspace (" +
+                 std::to_string(NA_WIN_CAP) + " windows per warp); use css_compute_forces";
+        return CSS_ERR_QUEUE_OVERFLOW;
+    }
+    if (status & (css::ST_ITER_LIMIT | css::ST_WALK_LIMIT)) {
+        c->err = "compute_forces_noalloc: a device loop reached its iteration cap";
+        return CSS_ERR_ITER_LIMIT;
+    }
+    if (status & css::ST_PIECES) {
+        c->err = "compute_forces_noalloc: window trimming produced too many pieces";
+        return CSS_ERR_QUEUE_OVERFLOW;
+    }
+    c->err = "compute_forces_noalloc: device status " + std::to_string(status);
+    return CSS_ERR_CUDA;
+}
+
 }  // namespace
 
 int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* face, const double* bary,
@@ -1818,12 +1870,26 @@ int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* f
                  std::to_string(NA_MAX_FACES) + " faces fit its fixed scratch";
         return CSS_ERR_CAPACITY;
     }
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CSS_ERR_CUDA;
-    NaDevice& D = g_na[dev];
+    // everything runs on the device of the mesh's context, whatever device is current
+    const int dev = c->device;
+    if (dev < 0 || dev >= 64) return CSS_ERR_INVALID_ARG;
+    DeviceGuard guard;
+    cudaError_t e = guard.set(dev);
+    if (e != cudaSuccess) { c->err = std::string("compute_forces_noalloc: ") + cudaGetErrorString(e); return CSS_ERR_CUDA; }
     cudaStream_t st = (cudaStream_t)stream;
+    if (st) {   // a stream of another device would put these launches beside the wrong memory
+        int sdev = -1;
+        e = cudaStreamGetDevice(st, &sdev);
+        if (e != cudaSuccess) { cudaGetLastError(); c->err = "compute_forces_noalloc: stream not usable"; return CSS_ERR_INVALID_ARG; }
+        if (sdev != dev) {
+            c->err = "compute_forces_noalloc: the stream belongs to device " + std::to_string(sdev) +
+                     ", the mesh to device " + std::to_string(dev);
+            return CSS_ERR_INVALID_ARG;
+        }
+    }
+    NaDevice& D = g_na[dev];
     if (!D.base) {   // first call on this device: host code needs the array's device address
-        cudaError_t e = cudaGetSymbolAddress((void**)&D.base, g_noalloc_scratch);
+        e = cudaGetSymbolAddress((void**)&D.base, g_noalloc_scratch);
         if (e != cudaSuccess) { D.base = nullptr; c->err = std::string("noalloc set-up: ") + cudaGetErrorString(e); return CSS_ERR_CUDA; }
     }
     cssi::GeoWs g{};
@@ -1840,15 +1906,28 @@ int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* f
     int32_t* pcnt = (int32_t*)(D.base + NA_OFF_PCNT);
     int* scal = (int*)(D.base + NA_OFF_SCAL);
     unsigned long long* cnt = (unsigned long long*)(D.base + NA_OFF_COUNT);
-    cudaError_t e = cudaSuccess;
-    if (D.layout != precision) {
+    // work already queued on the context's stream (an update or a step writing the arrays
+    // read here) comes first; the event was made with the context, so nothing is allocated
+    e = cudaEventRecord(c->ev_order, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_order, 0);
+    if (e == cudaSuccess && D.layout != precision) {
         // the array keeps the previous call's bytes; a new workspace layout starts from zero so
         // no stale bytes look like hash entries, and the face counts start from zero
         e = cudaMemsetAsync(D.base, 0, NA_OFF_FSTART, st);
         if (e == cudaSuccess) D.layout = precision;
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, 256 + 8 * 8, st);
-    if (e == cudaSuccess && e_pot) e = cudaMemsetAsync(e_pot, 0, sizeof(double), st);
+    int status = 0;
+    // the inputs are checked before any kernel indexes with them
+    if (e == cudaSuccess) {
+        k_na_validate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((int32_t)n, (int32_t)mesh->nf, face, bary, scal + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, scal + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { c->err = std::string("compute_forces_noalloc: ") + cudaGetErrorString(e); return CSS_ERR_CUDA; }
+    if (status) return na_status_error(c, status);
+    if (e_pot) e = cudaMemsetAsync(e_pot, 0, sizeof(double), st);
     if (e == cudaSuccess)
         // the pair-count region doubles as the scatter scratch: the kernel below rewrites it
         e = cssi::launch_bucket((int32_t)n, (int32_t)mesh->nf, face, mesh->frank, fcnt, fstart, fitems, pcnt, scan, st);
@@ -1871,14 +1950,9 @@ int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* f
         e = cssi::launch_geodesic(j, nullptr, q, precision, g, NA_WARPS_PER_CTA, g.nwarps / NA_WARPS_PER_CTA, scal,
                                   scal + 1, cnt, st);
     }
-    int status = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, scal + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { c->err = std::string("compute_forces_noalloc: ") + cudaGetErrorString(e); return CSS_ERR_CUDA; }
-    if (status) {
-        c->err = "compute_forces_noalloc: a source needs more than the fixed window workspace (" +
-                 std::to_string(NA_WIN_CAP) + " windows per warp); use css_compute_forces";
-        return CSS_ERR_QUEUE_OVERFLOW;
-    }
+    if (status) return na_status_error(c, status);
     return CSS_OK;
 }

@@ -35,7 +35,20 @@ def test_roofline_arithmetic():
     assert math.isclose(roof["peak"], peak / 1e12)
     assert math.isclose(roof["frac"], flops / 1e-3 / peak)
     assert roof["traffic"] == 1.5e7 and roof["bound"] == "alu"
-    bytes_ = 1000 * 150.0 * bench.BYTES_PER_FACE + 6000.0 * 24.0
+    # per source: faces reached (half the propagations) x 64 B + 48 B per propagated window
+    # + its 24 B force; 20 B per pair
+    bytes_ = 1000 * (150.0 * 64.0 + 300.0 * 48.0 + 24.0) + 6000.0 * 20.0
     assert math.isclose(mem["bytes_per_launch"], bytes_)
     assert math.isclose(mem["frac"], bytes_ / 1e-3 / 6000.0e9)
+    assert math.isclose(mem["traffic_over_algorithmic"], 1.5e7 / bytes_)
     json.dumps({"roofline": roof, "memory_roofline": mem}, allow_nan=False)
+
+
+def test_traffic_is_dropped_when_the_kernel_changed(monkeypatch):
+    """A stored DRAM figure is scaled to the launch's sources, and reported only while the
+    kernel sources still have the digest it was captured on."""
+    monkeypatch.setattr(bench, "TRAFFIC", {"w": {"bytes": 8.0e8, "sources": 8192, "kernel": bench.kernel_digest()}})
+    assert math.isclose(bench.traffic_per_launch("w", 65536), 6.4e9)
+    assert bench.traffic_per_launch("other", 10) is None
+    monkeypatch.setattr(bench, "TRAFFIC", {"w": {"bytes": 8.0e8, "sources": 8192, "kernel": "0" * 16}})
+    assert bench.traffic_per_launch("w", 65536) is None

@@ -6,7 +6,7 @@ import pytest
 
 import synth
 from oracle import oracle as O
-from tests._common import FP32_REL_DIAM, FP64_RTOL, compare_pairs, descent_checker
+from tests._common import FP32_REL_DIAM, FP64_RTOL, compare_pairs, descent_checker, force_row_bounds
 
 css = pytest.importorskip("paper_2404_19751_gb300")
 pytestmark = pytest.mark.gpu
@@ -138,6 +138,17 @@ def test_sources_on_vertices_and_edges(ctx):
     compare_pairs(g, r, 0.6, FP64_RTOL, 2.0)
     off = lambda c: (c[0][10:] - c[0][10], c[1][c[0][10]:], c[2][c[0][10]:], c[3][c[0][10]:])
     compare_pairs(off(g), off(r), 0.6, FP64_RTOL, 1e-6)
+    # the FP32 form on the same degenerate sources: every distance within its bar, and the
+    # tangents of the sources off the vertices (edge sources included) as in the FP32 test
+    om = O.OracleMesh(m)
+    tol = FP32_REL_DIAM * synth.bbox_diagonal(m)
+    g32 = css.geodesic_neighbors(parts, 0.6, css.FP32)
+    rg = om.neighbors_gap(face, bary, 0.6)
+    compare_pairs(g32, rg, 0.6, tol, 2.0, rel=False, band=tol)
+    off5 = lambda c: off(c[:4]) + ((c[4][c[0][10]:],) if len(c) > 4 else ())
+    walk = descent_checker(om, face, bary, 0.6)   # rows of the slice start at source 10
+    compare_pairs(off5(g32), off5(rg), 0.6, tol, 1e-5, rel=False, band=tol, tie=tol,
+                  walker=lambda i, j, d, t: walk(i + 10, j, d, t), land_tol=1e-7)
     parts.free()
     mesh.free()
 
@@ -201,8 +212,40 @@ def test_forces_match_oracle(ctx, name):
     assert np.max(np.abs(F - F0)) <= FP64_RTOL * scale
     assert E == pytest.approx(E0, rel=1e-10)
     F32, E32 = css.compute_forces(parts, pot, r_c, css.FP32)
-    # FP32 form: distances within 1e-5 of the diameter; forces follow through U'
-    assert np.max(np.abs(F32 - F0)) <= 2e-3 * scale
+    # FP32 form: each row within what its own pairs allow -- U' varied over the FP32 distance
+    # tolerance plus a 1e-5 turn of each tangent (a full turn at a cut-locus tie)
+    tol = FP32_REL_DIAM * synth.bbox_diagonal(m)
+    rows = O.OracleMesh(m).neighbors_gap(face, bary, r_c)
+    bound = force_row_bounds(rows, pot, lambda l: O.pair_dudl(pot, l), tol, 1e-5, tie=tol)
+    assert np.all(np.linalg.norm(F32 - F0, axis=1) <= bound)
+    parts.free()
+    mesh.free()
+
+
+def test_crowded_face_buckets(ctx):
+    """Faces holding many particles (a bucket of 90, one of 40, beyond the bounded rank
+    scan) give the oracle's neighbours and forces, and two evaluations repeat bit for bit
+    (each bucket is in particle-index order whatever order the scatter wrote it in)."""
+    m = synth.icosphere(2, 1.0, noise=0.02, seed=4)
+    face, bary = synth.place_uniform(m, 240, 9)
+    rng = np.random.default_rng(17)
+    face[:90] = 3
+    face[90:130] = 11
+    bary[:130] = rng.dirichlet([1.5, 1.5, 1.5], 130)
+    perm = rng.permutation(len(face))   # crowded particles spread over the index range
+    face, bary = face[perm].copy(), bary[perm].copy()
+    r_c = 0.45
+    pot = dict(kind=css.POT_HARMONIC, eps=1.0, sigma=r_c, r_cut=r_c)
+    mesh, parts = _setup(ctx, m, face, bary)
+    om = O.OracleMesh(m)
+    g = css.geodesic_neighbors(parts, r_c, css.FP64)
+    compare_pairs(g, om.neighbors_gap(face, bary, r_c), r_c, FP64_RTOL, 1e-7)
+    F0, E0 = om.forces(face, bary, r_c, pot)
+    F1, E1 = css.compute_forces(parts, pot, r_c, css.FP64)
+    F2, E2 = css.compute_forces(parts, pot, r_c, css.FP64)
+    assert np.max(np.abs(F1 - F0)) <= FP64_RTOL * np.max(np.abs(F0))
+    np.testing.assert_array_equal(F1, F2)
+    assert E1 == E2
     parts.free()
     mesh.free()
 

@@ -35,6 +35,34 @@ def test_normals_moments():
     assert O.normal_pair(7, 1, 3) != O.normal_pair(7, 1, 4)
 
 
+def _ks_stat(x, cdf):
+    """Kolmogorov-Smirnov statistic of the sample x against the distribution function cdf."""
+    x = np.sort(np.asarray(x))
+    n = len(x)
+    F = cdf(x)
+    return max(np.max(np.arange(1, n + 1) / n - F), np.max(F - np.arange(n) / n))
+
+
+def test_normals_are_independent_standard_pairs():
+    """The two normals of one Philox draw are an independent standard pair (Box-Muller):
+    each is N(0, 1), they are uncorrelated, z0^2 + z1^2 is exponential with mean 2 and the
+    angle atan2(z1, z0) is uniform.  A mix-up of cos and sin (z1 equal to z0, or to -z0), a
+    wrong radius or a missing 2 pi each fail one of these at the 0.1 % KS level."""
+    n = 20000
+    z = np.array([O.normal_pair(11, i, 5) for i in range(n)])
+    z0, z1 = z[:, 0], z[:, 1]
+    crit = 1.95 / math.sqrt(n)   # KS critical value at the 0.1 % level
+    phi = np.vectorize(lambda t: 0.5 * (1.0 + math.erf(t / math.sqrt(2.0))))
+    assert _ks_stat(z0, phi) < crit
+    assert _ks_stat(z1, phi) < crit
+    assert abs(np.corrcoef(z0, z1)[0, 1]) < 4.0 / math.sqrt(n)
+    assert _ks_stat(z0 ** 2 + z1 ** 2, lambda r: 1.0 - np.exp(-0.5 * r)) < crit
+    assert _ks_stat(np.arctan2(z1, z0), lambda a: (a + math.pi) / (2.0 * math.pi)) < crit
+    # consecutive steps of one particle are independent draws too
+    w = np.array([O.normal_pair(11, 3, s)[0] for s in range(n)])
+    assert abs(np.corrcoef(w[:-1], w[1:])[0, 1]) < 4.0 / math.sqrt(n)
+
+
 def test_flat_plane_is_euclidean():
     """Open flat convex mesh: geodesic = straight segment, tangent = unit chord (Sec. 2.1)."""
     cfg = synth.make_config("flat64")

@@ -74,3 +74,46 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert "particles" in css.load().css_last_error(ctx.h).decode()
     mesh.free()
     ctx.close()
+
+
+def test_noalloc_checks_particle_arrays_on_the_device():
+    """A face index equal to nf, or a barycentric triple that does not sum to 1, is caught by
+    the device check that runs before any kernel indexes with the caller's arrays; the call
+    returns CSS_ERR_INVALID_ARG and a correct call right after still matches css_compute_forces."""
+    fn = _noalloc_fn()
+    ctx = css.create(0)
+    m = synth.icosphere(3, 1.0, noise=0.01, seed=2)
+    face, bary = synth.place_uniform(m, 200, 5)
+    r_c = 0.3
+    mesh = css.mesh_upload(ctx, m.verts, m.faces)
+    parts = css.particles_set(ctx, mesh, face, bary)
+    pot = css.Potential(css.POT_HARMONIC, 1.0, r_c, r_c, 1.0)
+    n = len(face)
+    stream = torch.cuda.current_stream()
+    F = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    good_f = np.ascontiguousarray(face, np.int32)
+    good_b = np.ascontiguousarray(bary)
+    bad_face = good_f.copy()
+    bad_face[n // 2] = m.nf                      # one past the last face
+    bad_bary = good_b.copy()
+    bad_bary[7] = [0.5, 0.5, 0.5]                # sums to 1.5
+    nan_bary = good_b.copy()
+    nan_bary[3, 1] = float("nan")
+    for f_h, b_h in ((bad_face, good_b), (good_f, bad_bary), (good_f, nan_bary)):
+        dface = torch.from_numpy(f_h).cuda()
+        dbary = torch.from_numpy(b_h).cuda()
+        rc = fn(mesh.h, n, dface.data_ptr(), dbary.data_ptr(), C.byref(pot), r_c, css.FP64, F.data_ptr(), None,
+                stream.cuda_stream)
+        assert rc == -1, rc
+        assert "face index" in css.load().css_last_error(ctx.h).decode()
+    dface = torch.from_numpy(good_f).cuda()
+    dbary = torch.from_numpy(good_b).cuda()
+    F_ref, _ = css.compute_forces(parts, pot, r_c, css.FP64)
+    rc = fn(mesh.h, n, dface.data_ptr(), dbary.data_ptr(), C.byref(pot), r_c, css.FP64, F.data_ptr(), None,
+            stream.cuda_stream)
+    assert rc == 0, css.load().css_last_error(ctx.h)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(F.cpu().numpy() - F_ref)) <= FP64_RTOL * np.max(np.abs(F_ref))
+    parts.free()
+    mesh.free()
+    ctx.close()
