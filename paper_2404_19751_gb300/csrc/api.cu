@@ -77,14 +77,17 @@ struct GeoPlan {
 
 // size (and zero on a layout change, so old bytes never look like valid hash tags) one
 // pass's workspace
-int ensure_buf(css_ctx* c, cssi::WsBuf& b, int precision, int win_cap, int shared, int nwarps, GeoWs* out) {
+int ensure_buf(css_ctx* c, cssi::WsBuf& b, int precision, int win_cap, int tab_cap, int shared, int nwarps,
+               GeoWs* out) {
     GeoWs g{};
     g.shared = shared;
-    g.stride = cssi::geo_ws_bytes_per_warp(precision, win_cap, &g.log_eh, &g.log_vh, &g.log_fh, &g.fcap, &g.emcap);
+    g.stride = cssi::geo_ws_bytes_per_warp(precision, win_cap, shared ? 0 : tab_cap, &g.log_eh, &g.log_vh, &g.log_fh,
+                                           &g.fcap, &g.emcap);
     g.wcap = win_cap;
     g.nwarps = nwarps;
     const size_t need = g.stride * (size_t)nwarps;
-    const int64_t key = ((int64_t)precision * 1000003 + (int64_t)win_cap * 31 + nwarps) * 16 + shared;
+    const int64_t key = (((int64_t)precision * 1000003 + (int64_t)win_cap * 31 + nwarps) * 16 + shared) * 2097152 +
+                        (shared ? 0 : tab_cap);
     const bool relayout = (need > b.bytes) || (b.warps < nwarps) || (b.key != key);
     if (need > b.bytes) {
         cudaFree(b.ws);
@@ -127,12 +130,12 @@ int ensure_plan(css_ctx* c, int precision, int64_t nitems, GeoPlan* P) {
     if (L.ctas_per_sm > 0) bps = std::min(bps, L.ctas_per_sm);
     P->wpc1 = L.warps_per_cta;
     P->nctas1 = c->sm_count * bps;
-    int rc = ensure_buf(c, c->ws1, precision, L.win_cap, L.shared_scale, P->nctas1 * P->wpc1, &P->g1);
+    int rc = ensure_buf(c, c->ws1, precision, L.win_cap, L.tab_cap, L.shared_scale, P->nctas1 * P->wpc1, &P->g1);
     if (rc) return rc;
     P->g1.occupancy = L.occupancy;
     P->wpc2 = L.warps2_per_sm;
     P->nctas2 = c->sm_count;
-    rc = ensure_buf(c, c->ws2, precision, L.win_cap2, 0, P->nctas2 * P->wpc2, &P->g2);
+    rc = ensure_buf(c, c->ws2, precision, L.win_cap2, 0, 0, P->nctas2 * P->wpc2, &P->g2);
     if (rc) return rc;
     P->g2.occupancy = 1;
     if (c->defer_cap < nitems) {
@@ -403,7 +406,8 @@ static bool launch_ok(const css_launch* l) {
            l->tile >= 1 && l->tile <= 64 && (s == 0 || s == 1 || s == 2 || s == 4 || s == 8) &&
            l->window_capacity >= 64 && l->window_capacity <= (1 << 20) && l->window_capacity2 >= 64 &&
            l->window_capacity2 <= (1 << 20) && l->warps2_per_sm >= 1 && l->warps2_per_sm <= 8 &&
-           (l->occupancy == 1 || l->occupancy == 2);
+           (l->occupancy == 1 || l->occupancy == 2) &&
+           (l->table_capacity == 0 || (l->table_capacity >= 64 && l->table_capacity <= (1 << 20)));
 }
 
 int css_set_launch(css_ctx* c, const css_launch* l) {
@@ -421,6 +425,7 @@ int css_set_launch(css_ctx* c, const css_launch* l) {
     c->cfg.win_cap2 = next_pow2(l->window_capacity2);
     c->cfg.warps2_per_sm = l->warps2_per_sm;
     c->cfg.occupancy = l->occupancy;
+    c->cfg.tab_cap = l->table_capacity ? next_pow2(l->table_capacity) : 0;
     c->cfg_explicit = 1;
     return CSS_OK;
 }
@@ -435,6 +440,7 @@ int css_get_launch(const css_ctx* c, css_launch* l) {
     l->window_capacity2 = c->cfg.win_cap2;
     l->warps2_per_sm = c->cfg.warps2_per_sm;
     l->occupancy = c->cfg.occupancy;
+    l->table_capacity = c->cfg.tab_cap;
     return CSS_OK;
 }
 
@@ -1082,6 +1088,7 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
     const int32_t nitems = (int32_t)hj.size();
     const cssi::LaunchCfg base = c->cfg;
     constexpr int POOL_UNIT = 2048;   // first-pass windows per warp at table scale 1
+    constexpr int TAB_UNIT = 4096;    // global-table slots tried besides tables tied to the pool
     cssi::LaunchCfg pick = base;
     double pick_ms = INFINITY;
     auto measure = [&](const cssi::LaunchCfg& L, double* out) -> int {
@@ -1110,6 +1117,7 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
                 L.occupancy = 1;
                 L.shared_scale = s;
                 L.win_cap = POOL_UNIT * (s ? s : 4);   // the pool grows with the patch the tables hold
+                L.tab_cap = 0;
                 L.warps_per_cta = wpc;
                 L.ctas_per_sm = cps;
                 L.tile = 1;
@@ -1117,6 +1125,13 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
                 rc = measure(L, &t);
                 if (rc) break;
                 if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
+                if (s == 0) {   // global tables sized for a patch of about TAB_UNIT / 2 faces
+                    cssi::LaunchCfg Lt = L;
+                    Lt.tab_cap = TAB_UNIT;
+                    rc = measure(Lt, &t);
+                    if (rc) break;
+                    if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
+                }
                 // sources deferred for want of pool run twice: try a pool four times larger
                 if (c->last_counters[4] * 100 > nitems && L.win_cap * 4 <= (1 << 20)) {
                     L.win_cap *= 4;
@@ -1139,16 +1154,21 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
             if (variant == 1 && T.win_cap <= pick.win_cap && pick.shared_scale == 0) continue;
         } else if (pick.shared_scale == 0) continue;
         for (int wpc : {4, 8}) {
-            cssi::LaunchCfg L = T;
-            L.occupancy = 2;
-            L.warps_per_cta = wpc;
-            L.ctas_per_sm = 0;
-            L.tile = 1;
-            if (cssi::geodesic_blocks_per_sm(precision, wpc, L.shared_scale, 2) < 1) continue;
-            double t = 0.0;
-            rc = measure(L, &t);
+            for (int tab : {0, TAB_UNIT}) {
+                if (tab && T.shared_scale) continue;
+                cssi::LaunchCfg L = T;
+                L.occupancy = 2;
+                L.warps_per_cta = wpc;
+                L.ctas_per_sm = 0;
+                L.tile = 1;
+                L.tab_cap = T.shared_scale ? 0 : tab;
+                if (cssi::geodesic_blocks_per_sm(precision, wpc, L.shared_scale, 2) < 1) continue;
+                double t = 0.0;
+                rc = measure(L, &t);
+                if (rc) break;
+                if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
+            }
             if (rc) break;
-            if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
         }
     }
     for (int tile : {2, 4, 8}) {
@@ -1246,7 +1266,7 @@ int run_path_kernel(css_parts* p, double rc, const std::vector<int32_t>& us, con
     cudaStream_t st = c->stream;
     const int nus = (int)us.size();
     int le, lv, lf, fcap, emcap;
-    const size_t stride = cssi::geo_ws_bytes_per_warp(CSS_FP64, win_cap, &le, &lv, &lf, &fcap, &emcap);
+    const size_t stride = cssi::geo_ws_bytes_per_warp(CSS_FP64, win_cap, 0, &le, &lv, &lf, &fcap, &emcap);
     const size_t lstride = cssi::geo_link_bytes_per_warp(lv);
     const int wpc = 8;
     const int nwarps = std::min(c->sm_count * wpc, ((nus + wpc - 1) / wpc) * wpc);

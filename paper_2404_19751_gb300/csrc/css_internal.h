@@ -24,6 +24,7 @@ struct LaunchCfg {
     int win_cap2 = 16384;
     int warps2_per_sm = 2;   // second pass: warps per SM (one CTA each)
     int occupancy = 1;       // register budget of the first pass: 1 (255 regs) or 2 (128 regs)
+    int tab_cap = 0;         // first pass with global tables: table slots (0: tied to win_cap)
 };
 // a second-pass workspace (global tables)
 struct WsBuf {
@@ -204,7 +205,7 @@ struct GeoWs {
 };
 
 // geodesic.cu
-size_t geo_ws_bytes_per_warp(int precision, int win_cap, int* log_eh, int* log_vh, int* log_fh,
+size_t geo_ws_bytes_per_warp(int precision, int win_cap, int tab_cap, int* log_eh, int* log_vh, int* log_fh,
                              int* fcap, int* emcap);
 cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const GeoQueue& q, int precision,
                             const GeoWs& ws, int warps_per_cta, int nctas, int* work_counter,

@@ -463,7 +463,7 @@ __device__ void win_link(const DMesh& m, const Win64& W, double X, double Y, int
 // Unfold window W into the next face: distance candidates for the pseudo-source vertices it
 // reaches (paths through any other vertex can be shortened, Sec. 2.2) and at most two children.
 template <class R, bool L>
-__device__ __noinline__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R, L>* vc, int& nvc,
+__device__ __forceinline__ void propagate(const DMesh& m, const Win<R>& W, double rc, VCand<R, L>* vc, int& nvc,
                                        Win<R>* ch, int& nch) {
     nvc = 0;
     nch = 0;
@@ -1605,19 +1605,28 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
 // OCC = CTAs of 256 threads per SM the register budget must allow: 1 gives up to 255
 // registers a thread (fewer resident warps, no spills), 2 caps them at 128 (twice the
 // resident warps, some spills); which is faster depends on the workload.
+// The warp's workspace descriptor (warp-uniform pointers and sizes) lives in shared memory:
+// the out-of-line rounds take it by reference, and a descriptor in registers would be
+// copied to each thread's local memory for that.  The job parameter is a grid constant for
+// the same reason (its address is taken without a local copy).
 template <class R, int OCC, int SH>
-__global__ void __launch_bounds__(256, OCC) k_geodesic(cssi::GeoJob job0, const cssi::GeoJob* jobs, cssi::GeoQueue q,
-                                                  cssi::GeoWs g, int* work, int* status,
+__global__ void __launch_bounds__(256, OCC) k_geodesic(const __grid_constant__ cssi::GeoJob job0, const cssi::GeoJob* jobs,
+                                                  cssi::GeoQueue q, cssi::GeoWs g, int* work, int* status,
                                                   unsigned long long* counters) {
     __shared__ WarpSm smem[MAX_WARPS_CTA];
+    __shared__ Ws<R, SH> wsm[MAX_WARPS_CTA];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     if (gw >= g.nwarps) return;
     WarpSm& sm = smem[wib];
-    Ws<R, SH> ws = ws_bind<R, SH>(g, gw);
+    Ws<R, SH>& ws = wsm[wib];
     extern __shared__ __align__(16) unsigned char dsm[];
-    if constexpr (SH == 1) ws_bind_shared<R, SH>(ws, dsm + (size_t)wib * sh_bytes_per_warp<R>(g.shared), g.shared);
+    if (lane == 0) {
+        ws = ws_bind<R, SH>(g, gw);
+        if constexpr (SH == 1) ws_bind_shared<R, SH>(ws, dsm + (size_t)wib * sh_bytes_per_warp<R>(g.shared), g.shared);
+    }
+    __syncwarp();
     uint32_t gen = 0;
     if (lane == 0) gen = g.gen[gw];
     gen = __shfl_sync(CSS_FULL, gen, 0);
@@ -1638,7 +1647,9 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic(cssi::GeoJob job0, const 
             const int src = J.order ? J.order[pos] : pos;
             ++gen;
             if (gen == 0) gen = 1;   // 0 marks never-used entries
-            ws.gen = gen;
+            __syncwarp();
+            if (lane == 0) ws.gen = gen;
+            __syncwarp();
             run_source<R>(J, src, ws, sm, lane, status, counters, item, q.defer_list, q.defer_count);
         }
     }
@@ -1672,14 +1683,18 @@ __global__ void k_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, con
 
 namespace cssi {
 
-size_t geo_ws_bytes_per_warp(int precision, int win_cap, int* log_eh, int* log_vh, int* log_fh, int* fcap,
-                             int* emcap) {
-    // hash tables sized from the window capacity: roughly one edge per 2 windows,
-    // one vertex per 4, one face per 2; load factor <= 1/2
+size_t geo_ws_bytes_per_warp(int precision, int win_cap, int tab_cap, int* log_eh, int* log_vh, int* log_fh,
+                             int* fcap, int* emcap) {
+    // hash tables sized from tab_cap (0: from the window capacity): tab_cap edge slots, half
+    // as many vertex slots, tab_cap face slots (a patch of tab_cap / 2 faces at load 1/2).
+    // Tables much larger than the patches a pass sees spread each source's entries over
+    // many cache lines; a source that overflows them is deferred like one that overflows
+    // the pool.
+    const int t = tab_cap > 0 ? tab_cap : win_cap;
     int le = 6, lv = 6, lf = 6;
-    while ((1 << le) < win_cap) ++le;
-    while ((1 << lv) < win_cap / 2) ++lv;
-    while ((1 << lf) < win_cap) ++lf;
+    while ((1 << le) < t) ++le;
+    while ((1 << lv) < t / 2) ++lv;
+    while ((1 << lf) < t) ++lf;
     *log_eh = le; *log_vh = lv; *log_fh = lf;
     *fcap = 1 << (lf - 1);
     *emcap = 1 << lv;
@@ -1893,7 +1908,7 @@ int css_compute_forces_noalloc(const css_mesh* mesh, int64_t n, const int32_t* f
         if (e != cudaSuccess) { D.base = nullptr; c->err = std::string("noalloc set-up: ") + cudaGetErrorString(e); return CSS_ERR_CUDA; }
     }
     cssi::GeoWs g{};
-    g.stride = cssi::geo_ws_bytes_per_warp(precision, NA_WIN_CAP, &g.log_eh, &g.log_vh, &g.log_fh, &g.fcap, &g.emcap);
+    g.stride = cssi::geo_ws_bytes_per_warp(precision, NA_WIN_CAP, 0, &g.log_eh, &g.log_vh, &g.log_fh, &g.fcap, &g.emcap);
     g.wcap = NA_WIN_CAP;
     g.nwarps = (int)std::min<size_t>(NA_MAX_WARPS, NA_WS_BYTES / g.stride);
     g.nwarps -= g.nwarps % NA_WARPS_PER_CTA;

@@ -17,7 +17,7 @@ css = pytest.importorskip("paper_2404_19751_gb300")
 pytestmark = pytest.mark.gpu
 
 BASE = dict(warps_per_cta=4, ctas_per_sm=0, tile=1, shared_scale=1, window_capacity=2048,
-            window_capacity2=16384, warps2_per_sm=2, occupancy=1)
+            window_capacity2=16384, warps2_per_sm=2, occupancy=1, table_capacity=0)
 
 SHAPES = [
     dict(),
@@ -30,6 +30,8 @@ SHAPES = [
     dict(shared_scale=1, window_capacity=256, warps2_per_sm=1),
     dict(occupancy=2, warps_per_cta=8),
     dict(occupancy=2, shared_scale=0, window_capacity=8192, tile=2),
+    dict(shared_scale=0, window_capacity=8192, table_capacity=256),    # small tables: some deferred
+    dict(occupancy=2, shared_scale=0, window_capacity=32768, table_capacity=2048, warps_per_cta=8),
 ]
 
 
@@ -70,6 +72,7 @@ def test_results_do_not_depend_on_launch_shape(case):
             assert np.array_equal(g[0], ref[1][0]) and np.array_equal(g[1], ref[1][1])
             assert np.array_equal(g[2], ref[1][2])
     assert deferred[0] == 0 and deferred[6] > len(face) // 2   # the tiny pool defers most sources
+    assert deferred[10] > 0                                    # so do tables of 256 edge slots
     parts.free()
     mesh.free()
     ctx.close()
@@ -79,7 +82,7 @@ def test_launch_shape_validation():
     ctx = css.create(0)
     for bad in (dict(warps_per_cta=0), dict(warps_per_cta=9), dict(shared_scale=3), dict(tile=0),
                 dict(window_capacity=10), dict(warps2_per_sm=0), dict(shared_scale=8, warps_per_cta=8),
-                dict(occupancy=3)):
+                dict(occupancy=3), dict(table_capacity=10), dict(table_capacity=1 << 21)):
         with pytest.raises(css.CssError):
             ctx.set_launch(**dict(BASE, **bad))
     assert ctx.get_launch() == dict(BASE)    # a rejected shape leaves the old one

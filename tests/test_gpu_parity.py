@@ -244,8 +244,8 @@ def test_crowded_face_buckets(ctx):
     F1, E1 = css.compute_forces(parts, pot, r_c, css.FP64)
     F2, E2 = css.compute_forces(parts, pot, r_c, css.FP64)
     assert np.max(np.abs(F1 - F0)) <= FP64_RTOL * np.max(np.abs(F0))
-    np.testing.assert_array_equal(F1, F2)
-    assert E1 == E2
+    np.testing.assert_array_equal(F1, F2)   # each row summed in bucket order
+    assert E1 == pytest.approx(E2, rel=1e-12)   # sources add their energies atomically, in any order
     parts.free()
     mesh.free()
 
