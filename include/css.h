@@ -231,6 +231,33 @@ int css_geodesic_paths(css_parts* parts, double r_c, int64_t n_pairs, const int3
                        int32_t max_points, double* points, int32_t* n_points, int32_t* n_legs, double* dist,
                        double* gap);
 
+/* css_vhm_neighbors: approximate geodesic distances and initial tangents for every ordered
+ * pair (i, j), i != j, with the approximate distance below r_c (INFINITY: all pairs), in the
+ * layout of css_geodesic_neighbors.  This is the approximate alternative the paper names
+ * beside exact window propagation (Sec. 2.2: the vector heat method, O(h) error on a mesh of
+ * spacing h; Sec. 5).  Per source particle q, FP64, on the whole mesh:
+ *   (M + t L) u = u0       one backward-Euler heat step (L cotan Laplacian, M lumped mass,
+ *                          t = t_factor * h^2, h the mean edge length, u0 = q's barycentrics
+ *                          on its face's corners);
+ *   (M + t Lc) Y = Y0      the same step for tangent vectors (Lc the connection Laplacian over
+ *                          vertex frames whose corner angles are scaled to close up; Y0 = the
+ *                          source face's x-axis): H = Y / |Y| is that axis transported;
+ *   L phi = -div(-grad u / |grad u|)   (right-hand side made mean-free), phi(q) = 0;
+ * then l_ij = phi(x_j) (linear interpolation) and t_ij = the source face's x-axis turned by the
+ * angle of grad phi against H at x_j.  The heat steps are solved by Jacobi sweeps (damped
+ * where obtuse triangles make cotan weights negative) until no entry changes by more than
+ * 1e-14 of the terms it is summed from (entries below 1e-290, i.e. farther than about
+ * 660 sqrt(t) from the source, have no relative accuracy left), the Poisson step by
+ * conjugate gradients to 1e-14 of the preconditioned residual.  t_factor > 0 (1: t = h^2).
+ * Allocates a workspace and synchronises.  css_last_counters then holds: sources, the
+ * largest heat-sweep count of a batch, conjugate-gradient iterations (summed over batches),
+ * pairs, batches, sources per batch.
+ * Errors: CSS_ERR_INVALID_ARG (t_factor <= 0 or not finite, r_c NaN or <= 0),
+ * CSS_ERR_CAPACITY (as css_geodesic_neighbors), CSS_ERR_NONMANIFOLD (a vertex whose faces are
+ * not one disk or half-disk), CSS_ERR_ITER_LIMIT (a solve did not converge in 50000 steps). */
+int css_vhm_neighbors(css_parts* parts, double r_c, double t_factor, int64_t capacity, int64_t* n_pairs,
+                      int64_t* row_start, int32_t* nbr_j, double* dist, double* tangent);
+
 /* ---------------------------------------------------------------- batched form
  * Many independent particle sets (each on its own mesh) advanced together: the
  * neighbour/force work of all sets runs in one persistent launch per step whose

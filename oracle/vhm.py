@@ -27,13 +27,16 @@ edge lengths; minimum-image edges on periodic meshes), in FP64 with direct spars
   3. vector heat, one backward-Euler step: (M + t Lc) Y = Y0, Y0 = b_k times the unit
      x-axis of f0's layout carried into corner k's frame; H = Y / |Y| (the transported
      reference direction);
-  4. X_f = -grad u / |grad u| per face (unit, pointing away from the source);
+  4. X_f = -grad u / |grad u| per face (unit, pointing away from the source; 0 where the
+     gradient vanishes, i.e. where u underflowed: beyond about 700 sqrt(t) from the source);
   5. Poisson: L phi = -div X with (div X)_i = 1/2 sum over faces at i of
      cot(theta_1) (e_1 . X) + cot(theta_2) (e_2 . X) (e_1, e_2 the face's edges from i,
      theta_1, theta_2 the angles opposite them), phi fixed by phi(q) = 0 (q interpolated);
   6. per target y in face g with barycentrics c: distance d = sum_k c_k phi(v_k);
+     the direction away from the source at y is G_g = grad phi on g (the computed distance
+     field's own gradient; X only feeds the Poisson right-hand side);
      angle theta = arg sum_k c_k exp(i psi_k) conj(H_k), psi_k the vertex-frame angle of
-     X_g at corner k; the tangent at q is f0's layout x-axis turned by theta (world frame).
+     G_g at corner k; the tangent at q is f0's layout x-axis turned by theta (world frame).
 
 Parity unpinned: no.  Pins (tests/test_oracle_vhm.py): the cotan Laplacian annihilates
 constants everywhere and linear functions at interior vertices of a flat mesh; the mass
@@ -222,7 +225,9 @@ class VhmMesh:
         Y = self._vheat.solve(Y0)
         H = Y / np.abs(Y)
         g = self.grad(u)
-        X = -g / np.linalg.norm(g, axis=1)[:, None]
+        gn = np.linalg.norm(g, axis=1)
+        with np.errstate(divide="ignore", invalid="ignore"):   # where u underflowed: X = 0
+            X = np.where((gn > 0.0)[:, None], -g / gn[:, None], 0.0)
         rhs = np.concatenate([-self.div(X), [0.0]])
         phi = self._pois.solve(rhs)[:self.nv]
         phi -= float(np.dot(b0, phi[self.F[f0]]))
@@ -234,7 +239,8 @@ class VhmMesh:
         tf = np.asarray(tf, np.int64)
         tb = np.asarray(tb, np.float64)
         d = np.sum(tb * phi[self.F[tf]], axis=1)
-        beta = np.arctan2(X[tf, 1], X[tf, 0])
+        G = self.grad(phi)[tf]
+        beta = np.arctan2(G[:, 1], G[:, 0])
         z = np.zeros(len(tf), complex)
         for k in range(3):
             psi = self.to_vertex_angle(tf, k, beta)

@@ -28,7 +28,7 @@ SYMBOLS = ("css_create", "css_destroy", "css_last_error", "css_last_counters", "
            "css_particles_get", "css_particles_free", "css_geodesic_neighbors", "css_compute_forces",
            "css_integrate_step", "css_batch_create", "css_batch_step", "css_batch_free",
            "css_last_kernel_ms", "css_fma_peak", "css_particles_update", "css_get_launch", "css_autotune",
-           "css_trace_geodesics", "css_geodesic_paths", "css_particles_set_step")
+           "css_trace_geodesics", "css_geodesic_paths", "css_particles_set_step", "css_vhm_neighbors")
 
 
 class CssError(RuntimeError):
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
         "css_particles_get": [P, P, P, P, P, P, P],
         "css_particles_free": [P],
         "css_geodesic_neighbors": [P, D, C.c_int, I64, C.POINTER(I64), P, P, P, P],
+        "css_vhm_neighbors": [P, D, D, I64, C.POINTER(I64), P, P, P, P],
         "css_compute_forces": [P, P, D, C.c_int, P, P],
         "css_integrate_step": [P, P, P, D, C.c_int, I64, P, P],
         "css_batch_create": [P, P, I32, C.POINTER(C.c_void_p)],
@@ -287,6 +288,28 @@ def geodesic_neighbors(parts: Particles, r_c: float, precision: int = FP64, capa
         t = np.zeros((max(cap, 1), 3))
         rc = L.css_geodesic_neighbors(parts.h, float(r_c), int(precision), int(cap), C.byref(npairs),
                                       rs.ctypes.data, j.ctypes.data, d.ctypes.data, t.ctypes.data)
+        if rc == -5 and capacity is None:
+            cap = int(npairs.value)
+            continue
+        parts.ctx.check(rc)
+        k = int(npairs.value)
+        return rs, j[:k], d[:k], t[:k]
+
+
+def vhm_neighbors(parts: Particles, r_c: float, t_factor: float = 1.0, capacity: Optional[int] = None):
+    """Approximate neighbours (heat-method distances, vector-heat tangents; see
+    css_vhm_neighbors): CSR (row_start, j, dist, tangent) as host arrays."""
+    n = parts.n
+    L = load()
+    npairs = C.c_int64(0)
+    cap = capacity if capacity is not None else max(64, 32 * n)
+    while True:
+        rs = np.zeros(n + 1, np.int64)
+        j = np.zeros(max(cap, 1), np.int32)
+        d = np.zeros(max(cap, 1))
+        t = np.zeros((max(cap, 1), 3))
+        rc = L.css_vhm_neighbors(parts.h, float(r_c), float(t_factor), int(cap), C.byref(npairs),
+                                 rs.ctypes.data, j.ctypes.data, d.ctypes.data, t.ctypes.data)
         if rc == -5 and capacity is None:
             cap = int(npairs.value)
             continue

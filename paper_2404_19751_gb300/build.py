@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcss.so")
-UNITS = ["api.cu", "mesh_prep.cu", "geodesic.cu", "dynamics.cu", "peak.cu"]
+UNITS = ["api.cu", "mesh_prep.cu", "geodesic.cu", "dynamics.cu", "peak.cu", "vhm.cu"]
 HEADERS = ["css_dev.cuh", "css_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

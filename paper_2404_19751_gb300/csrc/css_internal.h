@@ -66,6 +66,11 @@ struct css_ctx {
     cudaEvent_t ev_order = nullptr;
 };
 
+namespace cssi {
+struct VhmOp;   // operators of the approximate solver (vhm.cu), built on first use
+void vhm_free(css_mesh* m);
+}  // namespace cssi
+
 struct css_mesh {
     css_ctx* ctx = nullptr;
     int64_t nv = 0, nf = 0, ne = 0, npseudo = 0;
@@ -87,6 +92,7 @@ struct css_mesh {
     css::HeRec32* he32 = nullptr;
     float* lay32 = nullptr;
     int32_t* frank = nullptr;   // nf: Morton rank of each face
+    cssi::VhmOp* vhm = nullptr;
     css::DMesh view() const;
 };
 
