@@ -80,9 +80,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the nested many-mesh measurement of the default workload")
-    ap.add_argument("--sweep", choices=["n", "v"], default=None,
+    ap.add_argument("--sweep", choices=["n", "v", "vhm"], default=None,
                     help="time per MD step against particle count (n) or mesh size (v) on a torus, "
-                         "with the fitted power-law exponents (not the benchmark line)")
+                         "with the fitted power-law exponents; vhm: the approximate solver against the "
+                         "exact one, all pairs, on the same tori (not the benchmark line)")
     return ap.parse_args()
 
 
@@ -779,10 +780,68 @@ def run_sweep(args):
     ctx.close()
 
 
+def run_vhm_sweep(args):
+    """All-pairs neighbours on the V-sweep tori (100 particles, aspect 3) by the approximate
+    solver (heat-method distances, vector-heat tangents, t = h^2) and by exact window
+    propagation (FP64 and FP32): median time of `--steps` calls after `--warmup`, and the
+    approximate solver's error against the exact FP64 distances and tangents."""
+    import numpy as np
+    import torch
+    import paper_2404_19751_gb300 as css
+    import synth
+    from synth.configs import torus_for_faces
+    ctx = css.create(0)
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup)):
+            out = fn()
+        t = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            t.append(1e3 * (time.perf_counter() - t0))
+        return float(np.median(t)), out
+
+    pts = []
+    for F in (1000, 2000, 4000, 8000, 16000):
+        m = torus_for_faces(F, 3.0, 1.0)
+        face, bary = synth.place_uniform(m, 100, 8)
+        mesh = css.mesh_upload(ctx, m.verts, m.faces)
+        parts = css.particles_set(ctx, mesh, face, bary)
+        ms_a, a = timed(lambda: css.vhm_neighbors(parts, math.inf, 1.0))
+        c = ctx.last_counters()
+        ms_e, e = timed(lambda: css.geodesic_neighbors(parts, math.inf, css.FP64))
+        ms_e32, _ = timed(lambda: css.geodesic_neighbors(parts, math.inf, css.FP32))
+        rel = np.abs(a[2] - e[2]) / np.maximum(e[2], 1e-12)
+        far = e[2] > 0.1 * np.max(e[2])
+        ang = np.arccos(np.clip(np.sum(a[3] * e[3], axis=1), -1.0, 1.0))
+        pts.append(dict(faces=m.nf, vertices=m.nv, pairs=int(len(e[2])), ms_vhm=ms_a, ms_exact_fp64=ms_e,
+                        ms_exact_fp32=ms_e32, heat_sweeps=int(c["windows"]), cg_iterations=int(c["propagated"]),
+                        rel_dist_err_mean=float(rel[far].mean()), rel_dist_err_p99=float(np.percentile(rel[far], 99)),
+                        tangent_angle_err_median=float(np.median(ang[far])),
+                        tangent_angle_err_p90=float(np.percentile(ang[far], 90))))
+        parts.free()
+        mesh.free()
+    xs = [p["faces"] for p in pts]
+
+    def slope(key):
+        return float(np.polyfit(np.log(xs), np.log([p[key] for p in pts]), 1)[0])
+    print(json.dumps({"sweep": "vhm", "what": "all pairs of 100 particles on aspect-3 tori, t = h^2; times are "
+                      "wall ms per call (host outputs included)", "points": pts,
+                      "exponent_vhm": slope("ms_vhm"), "exponent_exact_fp64": slope("ms_exact_fp64"),
+                      "exponent_rel_err": slope("rel_dist_err_mean")}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.sweep == "vhm":
+        run_vhm_sweep(args)
+        return
     if args.sweep:
         run_sweep(args)
         return

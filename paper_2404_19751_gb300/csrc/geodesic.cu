@@ -476,81 +476,70 @@ __device__ __forceinline__ void propagate(const DMesh& m, const Win<R>& W, doubl
     const int32_t vu = m.fv[h], vv = m.fv[3 * f + k1], vcid = m.fv[3 * f + k2];
     const R tolv = (R)Tol<R>::w * q.L;
     const R sx = fsx(W), sy = fsy(W);
-    if (W.b0 <= tolv && m.pseudo[vu]) {
-        VCand<R, L>& c = vc[nvc++];
-        c.v = vu; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact<R>(W, 0.0, 0.0);
-        win_tangent<R>(W, (R)0, (R)0, c.tx, c.ty);
-        if constexpr (L) win_link(m, W, 0.0, 0.0, 0, c);
-    }
-    if (W.b1 >= q.L - tolv && m.pseudo[vv]) {
-        VCand<R, L>& c = vc[nvc++];
-        c.v = vv; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact<R>(W, r.L, 0.0);
-        win_tangent<R>(W, q.L, (R)0, c.tx, c.ty);
-        if constexpr (L) win_link(m, W, r.L, 0.0, 1, c);
-    }
     const bool degen = win_degen<R>(W, q.L);
-    if (degen && !win_degen_sees<R>(W, q.L)) return;
+    const bool sees = !degen || win_degen_sees<R>(W, q.L);
     // occlusion predicate: where the ray s -> c crosses the edge line; in the FP32 form it is
     // re-evaluated in FP64 when it falls within 1e-5 L of an interval end
-    R xc = degen ? (R)0 : sx + (q.cx - sx) * (-sy) / (q.cy - sy);
-    if (sizeof(R) == sizeof(float) && !degen &&
-        (fabs(xc - W.b0) < (R)1e-5 * q.L || fabs(xc - W.b1) < (R)1e-5 * q.L)) {
-        xc = (R)(W.sx + (r.cx - W.sx) * (-W.sy) / (r.cy - W.sy));
+    R xc = (R)0;
+    if (!degen) {
+        xc = sx + (q.cx - sx) * (-sy) / (q.cy - sy);
+        if (sizeof(R) == sizeof(float) && (fabs(xc - W.b0) < (R)1e-5 * q.L || fabs(xc - W.b1) < (R)1e-5 * q.L))
+            xc = (R)(W.sx + (r.cx - W.sx) * (-W.sy) / (r.cy - W.sy));
     }
-    if ((degen || (xc >= W.b0 - tolv && xc <= W.b1 + tolv)) && m.pseudo[vcid]) {
+    // vertex candidates in the order start of the edge, end of the edge, far corner (one copy
+    // of the candidate code)
+    const bool take0 = W.b0 <= tolv && m.pseudo[vu];
+    const bool take1 = W.b1 >= q.L - tolv && m.pseudo[vv];
+    const bool take2 = sees && (degen || (xc >= W.b0 - tolv && xc <= W.b1 + tolv)) && m.pseudo[vcid];
+#pragma unroll 1
+    for (int a = 0; a < 3; ++a) {
+        if (!(a == 0 ? take0 : (a == 1 ? take1 : take2))) continue;
+        const double X = a == 0 ? 0.0 : (a == 1 ? r.L : r.cx), Y = a == 2 ? r.cy : 0.0;
+        const R Xf = a == 0 ? (R)0 : (a == 1 ? q.L : q.cx), Yf = a == 2 ? q.cy : (R)0;
         VCand<R, L>& c = vc[nvc++];
-        c.v = vcid; c.fixed = W.flags & WIN_FIXED; c.d = win_dist_exact<R>(W, r.cx, r.cy);
-        win_tangent<R>(W, q.cx, q.cy, c.tx, c.ty);
-        if constexpr (L) win_link(m, W, r.cx, r.cy, 2, c);
+        c.v = a == 0 ? vu : (a == 1 ? vv : vcid);
+        c.fixed = W.flags & WIN_FIXED;
+        c.d = win_dist_exact<R>(W, X, Y);
+        win_tangent<R>(W, Xf, Yf, c.tx, c.ty);
+        if constexpr (L) win_link(m, W, X, Y, a, c);
     }
-    if (r.tl >= 0 && (degen || xc > W.b0)) {
+    if (!sees) return;
+    // the children across the far edges: side 0 the edge u -> c (origin u, turned by
+    // -angle(c)), side 1 the edge c -> v (origin c, turned by -angle(v - c)); one copy of the
+    // child code
+#pragma unroll 1
+    for (int a = 0; a < 2; ++a) {
+        const int tw = a == 0 ? r.tl : r.tr;
+        if (tw < 0 || !(degen || (a == 0 ? xc > W.b0 : xc < W.b1))) continue;
+        const R ax = a == 0 ? (R)0 : q.cx, ay = a == 0 ? (R)0 : q.cy;
+        const R bx = a == 0 ? q.cx : q.L, by = a == 0 ? q.cy : (R)0;
+        const R co = a == 0 ? q.cl : q.cr, si = a == 0 ? q.sl : q.sr;
         R mu0 = (R)0, mu1 = (R)1;
         if (!degen) {
-            mu0 = ray_hit<R>(sx, sy, W.b0, (R)0, (R)0, q.cx, q.cy);
-            mu1 = (W.b1 >= xc) ? (R)1 : ray_hit<R>(sx, sy, W.b1, (R)0, (R)0, q.cx, q.cy);
+            mu0 = (a == 1 && W.b0 <= xc) ? (R)0 : ray_hit<R>(sx, sy, W.b0, ax, ay, bx, by);
+            mu1 = (a == 0 && W.b1 >= xc) ? (R)1 : ray_hit<R>(sx, sy, W.b1, ax, ay, bx, by);
             mu0 -= Widen<R>::mu; mu1 += Widen<R>::mu;
         }
         Win<R>& c = ch[nch];
         c = W;
-        c.he = r.tl;
-        c.sx = W.sx * r.cl + W.sy * r.sl;           // rotate by -angle(c), origin at u (FP64)
-        c.sy = -W.sx * r.sl + W.sy * r.cl;
+        c.he = tw;
+        const double dco = a == 0 ? r.cl : r.cr, dsi = a == 0 ? r.sl : r.sr;
+        const double px = a == 0 ? W.sx : W.sx - r.cx, py = a == 0 ? W.sy : W.sy - r.cy;   // FP64
+        c.sx = px * dco + py * dsi;
+        c.sy = -px * dsi + py * dco;
         if (c.sy > 0.0) c.sy = 0.0;
         set_fast(c);
         if (!(W.flags & WIN_FIXED)) {
-            c.ta = W.ta * q.cl + W.tb * q.sl;
-            c.tb = -W.ta * q.sl + W.tb * q.cl;
+            c.ta = W.ta * co + W.tb * si;
+            c.tb = -W.ta * si + W.tb * co;
         }
-        const R Lc = q.cx * q.cl + q.cy * q.sl;
-        c.b0 = mu0 * Lc; c.b1 = mu1 * Lc;
-        c.flags = (W.flags & WIN_FIXED) | WIN_ALIVE;
-        if ((double)win_key<R>(c) < rc) ++nch;
-    }
-    if (r.tr >= 0 && (degen || xc < W.b1)) {
-        R mu0 = (R)0, mu1 = (R)1;
-        if (!degen) {
-            mu0 = (W.b0 <= xc) ? (R)0 : ray_hit<R>(sx, sy, W.b0, q.cx, q.cy, q.L, (R)0);
-            mu1 = ray_hit<R>(sx, sy, W.b1, q.cx, q.cy, q.L, (R)0);
-            mu0 -= Widen<R>::mu; mu1 += Widen<R>::mu;
-        }
-        Win<R>& c = ch[nch];
-        c = W;
-        c.he = r.tr;
-        const double px = W.sx - r.cx, py = W.sy - r.cy;   // rotate by -angle(v - c), origin at c
-        c.sx = px * r.cr + py * r.sr;
-        c.sy = -px * r.sr + py * r.cr;
-        if (c.sy > 0.0) c.sy = 0.0;
-        set_fast(c);
-        if (!(W.flags & WIN_FIXED)) {
-            c.ta = W.ta * q.cr + W.tb * q.sr;
-            c.tb = -W.ta * q.sr + W.tb * q.cr;
-        }
-        const R Ld = (q.L - q.cx) * q.cr - q.cy * q.sr;
-        c.b0 = mu0 * Ld; c.b1 = mu1 * Ld;
+        const R Le = (bx - ax) * co + (by - ay) * si;   // length of the child's edge
+        c.b0 = mu0 * Le; c.b1 = mu1 * Le;
         c.flags = (W.flags & WIN_FIXED) | WIN_ALIVE;
         if ((double)win_key<R>(c) < rc) ++nch;
     }
 }
+
 
 // Points x in (lo, hi) where two windows carry equal distance: |x-a| - |x-b| = sb - sa squared
 // twice (FP64 in both forms: this is the near-degenerate intersection predicate).  Spurious
@@ -727,7 +716,7 @@ __device__ __forceinline__ bool split_f32(float csx, float csy, float csig, floa
     npieces = nb;
     const float E = 4.8e-7f * (fabsf(csx) + fabsf(csy) + fabsf(osx) + fabsf(osy) + 2.f * (fabsf(lo) + fabsf(hi)) + csig + osig) +
                     1e-30f;
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < 3; ++q) {
         if (q >= nb) break;
         const float x = 0.5f * (bp[q] + bp[q + 1]);
@@ -777,7 +766,7 @@ __device__ __noinline__ int split_exact(double ax, double ay, double sa, double 
     const float fax = (float)ax, fay = (float)ay, fsa = (float)sa, fbx = (float)bx, fby = (float)by, fsb = (float)sb;
     const float E = 4.8e-7f * (fabsf(fax) + fabsf(fay) + fabsf(fbx) + fabsf(fby) + 2.f * (fabsf((float)lo) + fabsf((float)hi)) +
                                fsa + fsb) + 1e-30f;
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < 3; ++q) {
         if (q > nr) break;
         const double xmd = 0.5 * (bp[q] + bp[q + 1]);
@@ -1211,6 +1200,7 @@ __device__ __noinline__ double query(const DMesh& m, const Ws<R, SH>& ws, int f0
             ql->len = (double)d;
         }
     }
+#pragma unroll 1
     for (int k = 0; k < 3; ++k) {
         const int h = 3 * fl + k;
         const int slot = ws_efind<R>(ws, m.edge[h]);
@@ -1279,6 +1269,7 @@ __device__ __noinline__ double query(const DMesh& m, const Ws<R, SH>& ws, int f0
             }
         }
     }
+#pragma unroll 1
     for (int k = 0; k < 3; ++k) {
         const int32_t v = m.fv[3 * fl + k];
         if (!m.pseudo[v]) continue;   // only pseudo-source vertices can bend a shortest path
