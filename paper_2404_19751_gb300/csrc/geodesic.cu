@@ -1213,6 +1213,19 @@ __device__ __noinline__ double query(const DMesh& m, const Ws<R, SH>& ws, int f0
         const R dx = (bx - ax) / L, dy = (by - ay) / L;
         const R hx = (px - ax) * dx + (py - ay) * dy;
         const R hy = dx * (py - ay) - dy * (px - ax);
+        // FP32 form: the target in this edge's frame from the FP64 layout, for exact lengths in
+        // near-ties (computed once per edge)
+        double hxd = 0.0, hyd = 0.0;
+        if (sizeof(R) == sizeof(float)) {
+            double axd, ayd, bxd, byd;
+            css::face_corner(m, fl, k, axd, ayd);
+            css::face_corner(m, fl, k + 1, bxd, byd);
+            const double Ldd = m.he[h].L;
+            const double pxd = bj[1] * m.lay[3 * fl] + bj[2] * m.lay[3 * fl + 1], pyd = bj[2] * m.lay[3 * fl + 2];
+            const double ddx = (bxd - axd) / Ldd, ddy = (byd - ayd) / Ldd;
+            hxd = (pxd - axd) * ddx + (pyd - ayd) * ddy;
+            hyd = ddx * (pyd - ayd) - ddy * (pxd - axd);
+        }
         // cone tolerance of the interval precision: adjacent windows stored in FP32 may
         // leave or overlap by an ulp of the edge length, which must not hide a target
         const R tol = (R)Tol<R>::w * L;
@@ -1233,33 +1246,13 @@ __device__ __noinline__ double query(const DMesh& m, const Ws<R, SH>& ws, int f0
             double t_tie = tie;
             double cmp_best = best;
             if (sizeof(R) == sizeof(float) && fabs(d - best) <= 1e-5 * d) {
-                // exact lengths: the target in this frame from the FP64 layout
-                double axd, ayd, bxd, byd;
-                css::face_corner(m, fl, k, axd, ayd);
-                css::face_corner(m, fl, k + 1, bxd, byd);
-                const double Ldd = m.he[h].L;
-                const double pxd = bj[1] * m.lay[3 * fl] + bj[2] * m.lay[3 * fl + 1], pyd = bj[2] * m.lay[3 * fl + 2];
-                const double ddx = (bxd - axd) / Ldd, ddy = (byd - ayd) / Ldd;
-                const double hxd = (pxd - axd) * ddx + (pyd - ayd) * ddy;
-                const double hyd = ddx * (pyd - ayd) - ddy * (pxd - axd);
-                d = win_dist_exact<R>(w, hxd, hyd);
+                d = win_dist_exact<R>(w, hxd, hyd);   // exact lengths near a tie
                 cmp_best = best_exact;
                 t_tie = 1e-13;
             }
             if (d < cmp_best - t_tie * d || (d <= cmp_best + t_tie * d && direct && best_fixed)) {
                 best = d < cmp_best ? d : cmp_best;
-                if (sizeof(R) == sizeof(float)) {
-                    double axd, ayd, bxd, byd;
-                    css::face_corner(m, fl, k, axd, ayd);
-                    css::face_corner(m, fl, k + 1, bxd, byd);
-                    const double Ldd = m.he[h].L;
-                    const double pxd = bj[1] * m.lay[3 * fl] + bj[2] * m.lay[3 * fl + 1], pyd = bj[2] * m.lay[3 * fl + 2];
-                    const double ddx = (bxd - axd) / Ldd, ddy = (byd - ayd) / Ldd;
-                    best_exact = win_dist_exact<R>(w, (pxd - axd) * ddx + (pyd - ayd) * ddy,
-                                                   ddx * (pyd - ayd) - ddy * (pxd - axd));
-                } else {
-                    best_exact = d;
-                }
+                best_exact = sizeof(R) == sizeof(float) ? win_dist_exact<R>(w, hxd, hyd) : d;
                 best_fixed = !direct;
                 win_tangent<R>(w, hx, hy, tx, ty);
                 if constexpr (SH == 2) {

@@ -632,3 +632,27 @@ def test_checkpoint_resume_is_bit_exact(ctx, kind):
     a.free()
     b.free()
     mesh.free()
+
+
+def test_path_through_a_flat_vertex_matches_oracle_and_is_straight(ctx):
+    """The GPU's shortest path between two particles on a line through an interior flat
+    vertex (hit exactly) equals the oracle's point by point and is the straight segment."""
+    from tests.test_oracle_geodesic import flat_vertex_pair
+    m, face, bary, V = flat_vertex_pair()
+    mesh, parts = _setup(ctx, m, face, bary)
+    om = O.OracleMesh(m)
+    x = synth.particles.world_positions(m, face, bary)
+    S = np.array([0, 1], np.int32)
+    D = np.array([1, 0], np.int32)
+    gp, gl, gd, gg = css.geodesic_paths(parts, math.inf, S, D)
+    op, ol, od, og = om.geodesic_paths(face, bary, math.inf, S, D)
+    for k in range(2):
+        a, b = x[S[k]], x[D[k]]
+        assert gd[k] == pytest.approx(np.linalg.norm(b - a), rel=1e-13)
+        assert len(gp[k]) == len(op[k]) and np.max(np.abs(gp[k] - op[k])) < 1e-12
+        u = (b - a) / np.linalg.norm(b - a)
+        assert np.linalg.norm(np.cross(gp[k] - a, u), axis=1).max() < 1e-12
+        assert np.min(np.linalg.norm(gp[k] - V, axis=1)) < 1e-12
+        assert gg[k] < 1e-12
+    parts.free()
+    mesh.free()

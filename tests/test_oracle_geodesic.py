@@ -573,3 +573,50 @@ def test_saddle_vertex_distances_and_bends_are_the_cone_closed_form():
         elif D < math.pi - 1e-6:
             assert legs[k] == 1
     assert bent >= 20 and np.max(gap) < 1e-13
+
+
+def _grid16_point(x, y):
+    """Face and barycentrics of (x, y) on grid_plane(17, 17) (spacing 1/16, quads split along
+    the rising diagonal); exact for coordinates that are multiples of 1/64."""
+    i, j = int(16 * x), int(16 * y)
+    u, v = 16 * x - i, 16 * y - j
+    q = j * 16 + i
+    if v <= u:   # below the diagonal: corners (a, b, d)
+        return 2 * q, (1.0 - u, u - v, v)
+    return 2 * q + 1, (1.0 - v, u, v - u)   # above: corners (a, d, c)
+
+
+def flat_vertex_pair():
+    """A flat sheet with 30 particles; particles 0 and 1 lie on a line through the interior
+    vertex (1/2, 1/2), all coordinates exact binary fractions, so the shortest path between
+    them passes through the vertex exactly."""
+    m = synth.grid_plane(17, 17)
+    face, bary = synth.place_uniform(m, 30, 21, area_weighted=False)
+    for k, (x, y) in enumerate(((29 / 64, 31 / 64), (41 / 64, 35 / 64))):
+        f, b = _grid16_point(x, y)
+        face[k], bary[k] = f, b
+    return m, face, bary, np.array([0.5, 0.5, 0.0])
+
+
+def test_path_through_a_flat_vertex_is_the_straight_segment():
+    """A shortest path that meets an interior flat vertex exactly goes straight through it: the
+    polyline lies on the segment between the two particles, contains the vertex and is as
+    long as the Euclidean distance (the pass-straight rule at angle pi, pinned by the plane's
+    closed form rather than by the walk's own arithmetic)."""
+    m, face, bary, V = flat_vertex_pair()
+    om = O.OracleMesh(m)
+    x = synth.particles.world_positions(m, face, bary)
+    P, Q = x[0], x[1]
+    assert np.linalg.norm(np.cross(Q - P, V - P)) < 1e-15          # collinear by construction
+    for s, d in ((0, 1), (1, 0)):
+        paths, legs, dist, gap = om.geodesic_paths(face, bary, math.inf, [s], [d])
+        pts = paths[0]
+        a, b = x[s], x[d]
+        assert dist[0] == pytest.approx(np.linalg.norm(b - a), rel=1e-13)
+        u = (b - a) / np.linalg.norm(b - a)
+        off = np.linalg.norm(np.cross(pts - a, u), axis=1)
+        assert off.max() < 1e-12
+        assert np.min(np.linalg.norm(pts - V, axis=1)) < 1e-12      # the vertex is on the polyline
+        proj = (pts - a) @ u
+        assert np.all(np.diff(proj) >= -1e-12)                       # monotone along the segment
+        assert np.linalg.norm(pts[0] - a) < 1e-12 and np.linalg.norm(pts[-1] - b) < 1e-12
