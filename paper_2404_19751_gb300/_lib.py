@@ -280,7 +280,7 @@ def geodesic_neighbors(parts: Particles, r_c: float, precision: int = FP64, capa
     n = parts.n
     L = load()
     npairs = C.c_int64(0)
-    cap = capacity if capacity is not None else max(64, 32 * n)
+    cap = capacity if capacity is not None else (max(64, 32 * n) if math.isfinite(r_c) else max(1, n * (n - 1)))
     while True:
         rs = np.zeros(n + 1, np.int64)
         j = np.zeros(max(cap, 1), np.int32)
@@ -302,7 +302,7 @@ def vhm_neighbors(parts: Particles, r_c: float, t_factor: float = 1.0, capacity:
     n = parts.n
     L = load()
     npairs = C.c_int64(0)
-    cap = capacity if capacity is not None else max(64, 32 * n)
+    cap = capacity if capacity is not None else (max(64, 32 * n) if math.isfinite(r_c) else max(1, n * (n - 1)))
     while True:
         rs = np.zeros(n + 1, np.int64)
         j = np.zeros(max(cap, 1), np.int32)

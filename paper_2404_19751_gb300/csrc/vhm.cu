@@ -210,6 +210,19 @@ __global__ void k_gersh(Op o, double t, unsigned long long* gmax) {
     atomicMax(gmax, (unsigned long long)__double_as_longlong(g));
 }
 
+// per call: the heat step's entries scaled by t (weight, and weight times the transport turn)
+// and the inverse diagonal, so a sweep spends five FP64 operations per entry
+__global__ void k_heat_entries(Op o, double t, double* wt, double* wc, double* wsn, double* inv_d) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < 6 * o.nf) {
+        const double w = t * o.ew[e];
+        wt[e] = w;
+        wc[e] = w * o.ec[e];
+        wsn[e] = w * o.es[e];
+    }
+    if (e < o.nv) inv_d[e] = 1.0 / (o.mass[e] + t * o.diag[e]);
+}
+
 // One (damped) Jacobi sweep of both heat systems, x <- x + omega (D^-1 (b + t W x) - x).
 // With all weights positive (an M-matrix) omega = 1 and every term is non-negative; an
 // obtuse mesh has negative cotan weights, and omega < 2 / (1 + max Gershgorin radius) keeps
@@ -217,31 +230,39 @@ __global__ void k_gersh(Op o, double t, unsigned long long* gmax) {
 // magnitude of the terms they are summed from raise *flag (an entry the sweeps have not
 // reached is 0 and changes when they do, so the flag stays up until every vertex has been
 // reached; below 1e-290 an entry has no relative accuracy left to converge to).
-__global__ void __launch_bounds__(VT) k_heat_sweep(Op o, int K, double t, double omega, const double* bu,
-                                                   const double* bY, const double* u, const double* Y, double* un,
-                                                   double* Yn, int check, int* flag) {
+__global__ void __launch_bounds__(VT) k_heat_sweep(Op o, int K, int nsrc, const double* wt, const double* wc,
+                                                   const double* wsn, const double* inv_d, double omega,
+                                                   const double* bu, const double* bY, const double* u, const double* Y,
+                                                   double* un, double* Yn, int check, int* flag) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool moved = false;
-    if (g < (int64_t)o.nv * K) {
-        const int v = (int)(g / K), s = (int)(g - (int64_t)v * K);
+    const int s = (int)(g % K);
+    if (g < (int64_t)o.nv * K && s < nsrc) {   // columns beyond the batch's sources stay 0
+        const int v = (int)(g / K);
         double au = bu[g], ar = bY[2 * g], ai = bY[2 * g + 1];
-        double su = fabs(au), sy = sqrt(ar * ar + ai * ai);
+        double su = 0.0, sy = 0.0;   // magnitudes of the summed terms (for the check only)
         for (int e = 2 * o.ring_start[v]; e < 2 * o.ring_start[v + 1]; ++e) {
             const size_t j = (size_t)o.ej[e] * K + s;
-            const double w = t * o.ew[e], c = o.ec[e], sn = o.es[e];
+            const double w = wt[e], c = wc[e], sn = wsn[e];
             const double uj = u[j], yr = Y[2 * j], yi = Y[2 * j + 1];
             au += w * uj;
-            ar += w * (c * yr - sn * yi);
-            ai += w * (sn * yr + c * yi);
-            su += fabs(w * uj);
-            sy += fabs(w) * sqrt(yr * yr + yi * yi);
+            ar += c * yr - sn * yi;
+            ai += sn * yr + c * yi;
+            if (check) {
+                su += fabs(w * uj);
+                sy += fabs(w) * sqrt(yr * yr + yi * yi);
+            }
         }
-        const double D = o.mass[v] + t * o.diag[v];
-        const double u0 = u[g], r0 = Y[2 * g], i0 = Y[2 * g + 1];
-        const double nu = u0 + omega * (au / D - u0);
-        const double nr = r0 + omega * (ar / D - r0), ni = i0 + omega * (ai / D - i0);
         if (check) {
-            const double su_d = su / D, sy_d = sy / D;
+            su += fabs(bu[g]);
+            sy += sqrt(bY[2 * g] * bY[2 * g] + bY[2 * g + 1] * bY[2 * g + 1]);
+        }
+        const double iD = inv_d[v];
+        const double u0 = u[g], r0 = Y[2 * g], i0 = Y[2 * g + 1];
+        const double nu = u0 + omega * (au * iD - u0);
+        const double nr = r0 + omega * (ar * iD - r0), ni = i0 + omega * (ai * iD - i0);
+        if (check) {
+            const double su_d = su * iD, sy_d = sy * iD;
             const double dr = nr - r0, di = ni - i0;
             moved = (su_d > 1e-290 && fabs(nu - u0) > 1e-14 * su_d) ||
                     (sy_d > 1e-290 && sqrt(dr * dr + di * di) > 1e-14 * sy_d);
@@ -612,7 +633,8 @@ struct Batch {
     std::vector<void*> owned;
     double *u = nullptr, *u2 = nullptr, *Y = nullptr, *Y2 = nullptr, *bu = nullptr, *bY = nullptr, *X = nullptr,
            *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *partial = nullptr,
-           *sc = nullptr, *od = nullptr, *ot = nullptr, *pj_d = nullptr, *pj_t = nullptr;
+           *sc = nullptr, *od = nullptr, *ot = nullptr, *pj_d = nullptr, *pj_t = nullptr, *wt = nullptr, *wc = nullptr,
+           *wsn = nullptr, *invd = nullptr;
     int32_t *src = nullptr, *keep = nullptr, *pj = nullptr;
     int* ints = nullptr;   // [0] flag, [1] active count, [2..2+K) active
     int64_t* cnt = nullptr;
@@ -660,6 +682,10 @@ int css_vhm_neighbors(css_parts* parts, double r_c, double t_factor, int64_t cap
     VTRY("vhm", B.get(&B.roff, (size_t)K));
     VTRY("vhm", B.get(&B.od, (size_t)K * n)); VTRY("vhm", B.get(&B.ot, 3 * (size_t)K * n));
     VTRY("vhm", B.get(&B.keep, (size_t)K * n));
+    VTRY("vhm", B.get(&B.wt, 6 * (size_t)nf)); VTRY("vhm", B.get(&B.wc, 6 * (size_t)nf));
+    VTRY("vhm", B.get(&B.wsn, 6 * (size_t)nf)); VTRY("vhm", B.get(&B.invd, (size_t)nv));
+    k_heat_entries<<<vblk(std::max<int64_t>(6 * (int64_t)nf, nv)), VT, 0, st>>>(op, t, B.wt, B.wc, B.wsn, B.invd);
+    VTRY("vhm", cudaGetLastError());
     double* bsum = B.sc;          // K
     double* rz = B.sc + K;        // K
     double* rz0 = B.sc + 2 * K;   // K
@@ -687,6 +713,8 @@ int css_vhm_neighbors(css_parts* parts, double r_c, double t_factor, int64_t cap
         VTRY("vhm", cudaMemsetAsync(B.bY, 0, 2 * VK * sizeof(double), st));
         VTRY("vhm", cudaMemsetAsync(B.u, 0, VK * sizeof(double), st));
         VTRY("vhm", cudaMemsetAsync(B.Y, 0, 2 * VK * sizeof(double), st));
+        VTRY("vhm", cudaMemsetAsync(B.u2, 0, VK * sizeof(double), st));      // columns past the batch's
+        VTRY("vhm", cudaMemsetAsync(B.Y2, 0, 2 * VK * sizeof(double), st));  // sources stay 0 in both
         k_heat_rhs<<<vblk(3 * ns), VT, 0, st>>>(op, K, ns, B.src, parts->face, parts->bary, B.bu, B.bY);
         VTRY("vhm heat", cudaGetLastError());
         double *u = B.u, *un = B.u2, *Y = B.Y, *Yn = B.Y2;
@@ -706,7 +734,8 @@ int css_vhm_neighbors(css_parts* parts, double r_c, double t_factor, int64_t cap
         for (;;) {
             VTRY("vhm heat", cudaMemsetAsync(flag, 0, sizeof(int), st));
             for (int k = 0; k < CHUNK; ++k) {
-                k_heat_sweep<<<nbv, VT, 0, st>>>(op, K, t, omega, B.bu, B.bY, u, Y, un, Yn, k == CHUNK - 1, flag);
+                k_heat_sweep<<<nbv, VT, 0, st>>>(op, K, ns, B.wt, B.wc, B.wsn, B.invd, omega, B.bu, B.bY, u, Y, un, Yn,
+                                                 k == CHUNK - 1, flag);
                 std::swap(u, un);
                 std::swap(Y, Yn);
             }
