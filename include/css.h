@@ -339,15 +339,20 @@ int css_fma_peak(css_ctx* ctx, int precision, double* flops_per_s);
  *                      0 = tied to window_capacity.  Tables sized for the patches of the
  *                      workload keep each source's entries on few cache lines; a source
  *                      that overflows them is deferred to the second pass
+ *   team               0: one warp per source; 1: all warps of a CTA (warps_per_cta >= 2) work
+ *                      on one source together -- each wave unfolds up to 32 x warps_per_cta
+ *                      windows and the insertions are spread over the warps by edge and vertex
+ *                      id -- for sets with fewer sources than resident warps
  * css_set_launch fails with CSS_ERR_INVALID_ARG when a value is out of range or the
  * shape's shared memory does not fit an SM.  Until a shape is set or tuned, a context
- * starts from {4, 0, 1, 1, 2048, 16384, 2, 1, 0} and adapts by itself: after an evaluation
+ * starts from {4, 0, 1, 1, 2048, 16384, 2, 1, 0, 0} and adapts by itself: after an evaluation
  * that deferred more than a quarter of its sources it switches the first pass to global
  * tables with a four times larger pool (up to 2^17 windows). */
 typedef struct css_launch {
     int32_t warps_per_cta, ctas_per_sm, tile, shared_scale;
     int32_t window_capacity, window_capacity2, warps2_per_sm, occupancy;
     int32_t table_capacity;
+    int32_t team;
 } css_launch;
 int css_set_launch(css_ctx* ctx, const css_launch* launch);
 int css_get_launch(const css_ctx* ctx, css_launch* launch);
@@ -358,8 +363,10 @@ int css_get_launch(const css_ctx* ctx, css_launch* launch);
  * times the scale (8192 for global tables, whose tables are tried both tied to the pool
  * and at 4096 slots), and four times that pool where more than 1 % of the sources were
  * deferred, then occupancy 2 with 4 or 8 warps per CTA (global tables with pools of 8192
- * and 32768 windows, tables tied or at 4096 slots, and the best pick's tables), then the
- * tile on the best -- and keeps the fastest in the context.  Each candidate runs `reps` times (>= 1) after one
+ * and 32768 windows, tables tied or at 4096 slots, and the best pick's tables), then, when the
+ * sources sampled are fewer than four times 8 warps per SM, the team form (shared or global
+ * tables x 2, 4, 8 warps per CTA x occupancy 1, 2), then the tile on the best (not for a
+ * team) -- and keeps the fastest in the context.  Each candidate runs `reps` times (>= 1) after one
  * untimed run; `sample` > 0 restricts every run to about that many sources spread over
  * the sets (0: all).  best (may be NULL) receives the chosen shape and best_ms its
  * time.  Particle states are unchanged; stored forces are marked stale.  Synchronises. */

@@ -46,7 +46,8 @@ class Launch(C.Structure):
     """Launch shape of the neighbour/force evaluation (see css_launch in css.h)."""
     _fields_ = [("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("tile", C.c_int32),
                 ("shared_scale", C.c_int32), ("window_capacity", C.c_int32), ("window_capacity2", C.c_int32),
-                ("warps2_per_sm", C.c_int32), ("occupancy", C.c_int32), ("table_capacity", C.c_int32)]
+                ("warps2_per_sm", C.c_int32), ("occupancy", C.c_int32), ("table_capacity", C.c_int32),
+                ("team", C.c_int32)]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

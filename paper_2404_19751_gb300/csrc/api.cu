@@ -73,6 +73,7 @@ int next_pow2(int x) {
 struct GeoPlan {
     GeoWs g1, g2;
     int wpc1 = 0, nctas1 = 0, wpc2 = 0, nctas2 = 0;
+    int team = 0;   // first pass in the team form (one source per CTA)
 };
 
 // size (and zero on a layout change, so old bytes never look like valid hash tags) one
@@ -117,11 +118,14 @@ int ensure_buf(css_ctx* c, cssi::WsBuf& b, int precision, int win_cap, int tab_c
 int ensure_plan(css_ctx* c, int precision, int64_t nitems, GeoPlan* P) {
     const cssi::LaunchCfg& L = c->cfg;
     // the occupancy query costs host time on every call: cached per shape
-    const int64_t bkey = ((int64_t)precision * 64 + L.warps_per_cta) * 64 + L.shared_scale * 4 + L.occupancy;
+    const int64_t bkey = (((int64_t)precision * 64 + L.warps_per_cta) * 64 + L.shared_scale * 4 + L.occupancy) * 2 + L.team;
     auto hit = c->bps_cache.find(bkey);
-    int bps = hit != c->bps_cache.end() ? hit->second
-                                        : (c->bps_cache[bkey] = cssi::geodesic_blocks_per_sm(precision, L.warps_per_cta,
-                                                                                              L.shared_scale, L.occupancy));
+    int bps = hit != c->bps_cache.end()
+                  ? hit->second
+                  : (c->bps_cache[bkey] = L.team ? cssi::geodesic_team_blocks_per_sm(precision, L.warps_per_cta,
+                                                                                     L.shared_scale, L.occupancy)
+                                                 : cssi::geodesic_blocks_per_sm(precision, L.warps_per_cta,
+                                                                                L.shared_scale, L.occupancy));
     if (bps < 1) {
         c->err = "launch shape does not fit an SM (" + std::to_string(L.warps_per_cta) + " warps per CTA, shared scale " +
                  std::to_string(L.shared_scale) + ")";
@@ -130,7 +134,10 @@ int ensure_plan(css_ctx* c, int precision, int64_t nitems, GeoPlan* P) {
     if (L.ctas_per_sm > 0) bps = std::min(bps, L.ctas_per_sm);
     P->wpc1 = L.warps_per_cta;
     P->nctas1 = c->sm_count * bps;
-    int rc = ensure_buf(c, c->ws1, precision, L.win_cap, L.tab_cap, L.shared_scale, P->nctas1 * P->wpc1, &P->g1);
+    P->team = L.team;
+    // one workspace slice per warp, or per CTA in the team form
+    int rc = ensure_buf(c, c->ws1, precision, L.win_cap, L.tab_cap, L.shared_scale,
+                        L.team ? P->nctas1 : P->nctas1 * P->wpc1, &P->g1);
     if (rc) return rc;
     P->g1.occupancy = L.occupancy;
     P->wpc2 = L.warps2_per_sm;
@@ -151,7 +158,8 @@ int ensure_plan(css_ctx* c, int precision, int64_t nitems, GeoPlan* P) {
 // the plan's identity, for keying captured graphs
 std::string plan_key(const css_ctx* c, const GeoPlan& P) {
     const int64_t v[8] = {c->ws1.key, c->ws2.key, (int64_t)(uintptr_t)c->ws1.ws, (int64_t)(uintptr_t)c->ws2.ws,
-                          (int64_t)(uintptr_t)c->defer, P.nctas1, c->cfg.tile * 8 + c->cfg.occupancy, P.nctas2};
+                          (int64_t)(uintptr_t)c->defer, P.nctas1, (c->cfg.tile * 8 + c->cfg.occupancy) * 2 + P.team,
+                          P.nctas2};
     return std::string((const char*)v, sizeof(v));
 }
 
@@ -208,8 +216,12 @@ int enqueue_passes(css_ctx* c, const GeoJob& j0, const GeoJob* djobs, const int3
     TRY(c, "reset", cudaMemsetAsync(c->dscal + 2, 0, 2 * sizeof(int), st));
     TRY(c, "event", record_ev(c, c->ev_geo0));
     cssi::GeoQueue q1{job_of_item, src_of_item, nitems, nullptr, nullptr, c->defer, c->dscal + 2, c->cfg.tile};
-    TRY(c, "geodesic", cssi::launch_geodesic(j0, djobs, q1, prec, P.g1, P.wpc1, P.nctas1, c->dscal, c->dscal + 1,
-                                             c->dcount, st));
+    if (P.team)
+        TRY(c, "geodesic", cssi::launch_geodesic_team(j0, djobs, q1, prec, P.g1, P.wpc1, P.nctas1, c->dscal,
+                                                      c->dscal + 1, c->dcount, st));
+    else
+        TRY(c, "geodesic", cssi::launch_geodesic(j0, djobs, q1, prec, P.g1, P.wpc1, P.nctas1, c->dscal, c->dscal + 1,
+                                                 c->dcount, st));
     cssi::GeoQueue q2{job_of_item, src_of_item, nitems, c->defer, c->dscal + 2, nullptr, nullptr, 1};
     TRY(c, "geodesic", cssi::launch_geodesic(j0, djobs, q2, prec, P.g2, P.wpc2, P.nctas2, c->dscal + 3, c->dscal + 1,
                                              c->dcount, st));
@@ -407,13 +419,15 @@ static bool launch_ok(const css_launch* l) {
            l->window_capacity >= 64 && l->window_capacity <= (1 << 20) && l->window_capacity2 >= 64 &&
            l->window_capacity2 <= (1 << 20) && l->warps2_per_sm >= 1 && l->warps2_per_sm <= 8 &&
            (l->occupancy == 1 || l->occupancy == 2) &&
-           (l->table_capacity == 0 || (l->table_capacity >= 64 && l->table_capacity <= (1 << 20)));
+           (l->table_capacity == 0 || (l->table_capacity >= 64 && l->table_capacity <= (1 << 20))) &&
+           (l->team == 0 || (l->team == 1 && l->warps_per_cta >= 2));
 }
 
 int css_set_launch(css_ctx* c, const css_launch* l) {
     if (!c || !l || !launch_ok(l)) return CSS_ERR_INVALID_ARG;
     for (int prec : {CSS_FP32, CSS_FP64})
-        if (cssi::geodesic_blocks_per_sm(prec, l->warps_per_cta, l->shared_scale, l->occupancy) < 1) {
+        if ((l->team ? cssi::geodesic_team_blocks_per_sm(prec, l->warps_per_cta, l->shared_scale, l->occupancy)
+                     : cssi::geodesic_blocks_per_sm(prec, l->warps_per_cta, l->shared_scale, l->occupancy)) < 1) {
             c->err = "launch shape does not fit an SM";
             return CSS_ERR_INVALID_ARG;
         }
@@ -426,6 +440,7 @@ int css_set_launch(css_ctx* c, const css_launch* l) {
     c->cfg.warps2_per_sm = l->warps2_per_sm;
     c->cfg.occupancy = l->occupancy;
     c->cfg.tab_cap = l->table_capacity ? next_pow2(l->table_capacity) : 0;
+    c->cfg.team = l->team;
     c->cfg_explicit = 1;
     return CSS_OK;
 }
@@ -441,6 +456,7 @@ int css_get_launch(const css_ctx* c, css_launch* l) {
     l->warps2_per_sm = c->cfg.warps2_per_sm;
     l->occupancy = c->cfg.occupancy;
     l->table_capacity = c->cfg.tab_cap;
+    l->team = c->cfg.team;
     return CSS_OK;
 }
 
@@ -1115,6 +1131,7 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
             for (int cps : {0, 1}) {
                 if (cps == 1 && bps == 1) continue;   // same shape as "as many as fit"
                 cssi::LaunchCfg L = base;
+                L.team = 0;
                 L.occupancy = 1;
                 L.shared_scale = s;
                 L.win_cap = POOL_UNIT * (s ? s : 4);   // the pool grows with the patch the tables hold
@@ -1172,8 +1189,34 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
             if (rc) break;
         }
     }
+    // the team form (all warps of a CTA on one source) where the sampled sources are too few to
+    // fill the resident warps one warp each
+    if (rc == CSS_OK && (int64_t)nitems < 4 * (int64_t)c->sm_count * 8) {
+        for (int s : {1, 0}) {
+            for (int wpc : {2, 4, 8}) {
+                for (int occ : {1, 2}) {
+                    if (cssi::geodesic_team_blocks_per_sm(precision, wpc, s, occ) < 1) continue;
+                    cssi::LaunchCfg L = base;
+                    L.team = 1;
+                    L.occupancy = occ;
+                    L.shared_scale = s;
+                    L.win_cap = POOL_UNIT * (s ? s : 4);
+                    L.tab_cap = 0;
+                    L.warps_per_cta = wpc;
+                    L.ctas_per_sm = 0;
+                    L.tile = 1;
+                    double t = 0.0;
+                    rc = measure(L, &t);
+                    if (rc) break;
+                    if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
+                }
+                if (rc) break;
+            }
+            if (rc) break;
+        }
+    }
     for (int tile : {2, 4, 8}) {
-        if (rc) break;
+        if (rc || pick.team) break;   // a team claims one source at a time
         cssi::LaunchCfg L = pick;
         L.tile = tile;
         double t = 0.0;

@@ -25,6 +25,7 @@ struct LaunchCfg {
     int warps2_per_sm = 2;   // second pass: warps per SM (one CTA each)
     int occupancy = 1;       // register budget of the first pass: 1 (255 regs) or 2 (128 regs)
     int tab_cap = 0;         // first pass with global tables: table slots (0: tied to win_cap)
+    int team = 0;            // 1: the warps of a CTA work on one source together (team form)
 };
 // a second-pass workspace (global tables)
 struct WsBuf {
@@ -222,6 +223,12 @@ cudaError_t launch_geodesic_links(const GeoJob& job, const GeoQueue& q, const Ge
                                   int nctas, int* work_counter, int* status, unsigned long long* counters,
                                   cudaStream_t st);
 int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared_scale, int occupancy);
+// team form of the first pass: all warps of a CTA (2..8) on one source; ws counts teams
+cudaError_t launch_geodesic_team(const GeoJob& job0, const GeoJob* djobs, const GeoQueue& q, int precision,
+                                 const GeoWs& ws, int warps_per_cta, int nctas, int* work_counter, int* status,
+                                 unsigned long long* counters, cudaStream_t st);
+int geodesic_team_blocks_per_sm(int precision, int warps_per_cta, int shared_scale, int occupancy);
+size_t geodesic_team_shared_bytes(int precision, int warps_per_cta, int shared_scale);
 size_t geodesic_shared_bytes(int precision, int warps_per_cta, int shared_scale);
 cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd,
                                  const double* pt, int pair_cap, const int64_t* row_start,

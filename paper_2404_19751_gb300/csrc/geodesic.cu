@@ -1357,15 +1357,12 @@ __device__ int select_wave(Ws<R, SH>& ws, WarpSm& sm, int npend, float kmin, flo
     return mine;
 }
 
+// Start a source: empty tables and counters, the source's face, distance candidates for its
+// pseudo-source corners and one window per edge of its face covering the whole edge (run by
+// one warp).
 template <class R, int SH>
-__device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, int lane, int* status,
-                           unsigned long long* counters, int item, int32_t* defer_list, int* defer_count) {
-    const DMesh& m = J.m;
-    const double rc = J.rc;
-    const int f0 = J.face[i];
-    const double* b = J.bary + 3 * (size_t)i;
-    const double qxd = b[1] * m.lay[3 * f0] + b[2] * m.lay[3 * f0 + 1];
-    const double qyd = b[2] * m.lay[3 * f0 + 2];
+__device__ __forceinline__ void seed_source(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int f0, double qxd, double qyd,
+                                            double rc, int lane) {
     ws_clear_shared<R>(ws, lane);
     if (lane == 0) { sm.nwin = 0; sm.npend = 0; sm.nface = 0; sm.nemit = 0; sm.err = 0; }
     __syncwarp();
@@ -1424,6 +1421,116 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
         }
         child_round<R>(m, ws, sm, has, c, rc, lane);
     }
+}
+
+// The targets in the faces flist[fb .. fb + 32) (one warp): each particle's distance and
+// tangent at the source, its pair row entry (slots(ballot of pairs) gives where this chunk's
+// pairs start in the row) and its force and energy terms.
+template <class R, int SH, class Slots>
+__device__ __forceinline__ void eval_face_block(const cssi::GeoJob& J, int i, const Ws<R, SH>& ws, int f0, R qx, R qy,
+                                                int fb, int nface, int lane, int item, Slots slots, double& fx,
+                                                double& fy, double& en) {
+    const DMesh& m = J.m;
+    const double rc = J.rc;
+    const bool wp = J.want_pairs != 0;
+    const int fi = fb + lane;
+    int fl = -1, st = 0, cnt = 0;
+    if (fi < nface) {
+        fl = ws.flist[fi];
+        const int key = m.frank ? m.frank[fl] : fl;
+        st = J.fstart[key];
+        cnt = J.fstart[key + 1] - st;
+    }
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(CSS_FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(CSS_FULL, incl, 31);
+    for (int tb = 0; tb < total; tb += 32) {
+        const int t = tb + lane;
+        int owner = 0;
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int v = __shfl_sync(CSS_FULL, incl, owner + step - 1);
+            if (v <= t) owner += step;
+        }
+        owner = min(owner, 31);
+        const int o_fl = __shfl_sync(CSS_FULL, fl, owner);
+        const int o_st = __shfl_sync(CSS_FULL, st, owner);
+        const int o_ex = __shfl_sync(CSS_FULL, incl - cnt, owner);
+        bool ispair = false;
+        double d = 0.0;
+        R tx = (R)0, ty = (R)0;
+        int j = -1;
+        VLink<SH == 2> ql;
+        if (t < total) {
+            j = J.fitems[o_st + (t - o_ex)];
+            if (j != i) {
+                d = query<R>(m, ws, f0, qx, qy, o_fl, J.bary + 3 * (size_t)j, tx, ty, &ql);
+                ispair = d < rc;
+            }
+        }
+        const unsigned pm = __ballot_sync(CSS_FULL, ispair);
+        const int pbase = slots(pm);   // the row slots of this chunk's pairs start here
+        if constexpr (SH == 2) {
+            // the pair's legs, from the target back to the source: its own link, then the
+            // link of each vertex on the way (still in this source's table)
+            const int pos = pbase + __popc(pm & css::lanemask_lt());
+            if (ispair && pos < J.pair_cap) {
+                const size_t o = (size_t)item * J.pair_cap + pos;
+                int nl = 0;
+                VLink<true> l = ql;
+                for (;;) {
+                    if (nl >= J.lmax) { nl = -1; break; }
+                    const size_t a = o * J.lmax + nl;
+                    J.lfk[a] = l.fk;
+                    J.ldir[2 * a] = l.dx;
+                    J.ldir[2 * a + 1] = l.dy;
+                    J.llen[a] = l.len;
+                    ++nl;
+                    if (l.par < 0) break;
+                    const int slot = ws_vfind<R>(ws, l.par);
+                    if (slot < 0) { nl = -2; break; }
+                    l.par = ws.lpar[slot];
+                    l.fk = ws.lfk[slot];
+                    l.dx = ws.ldir[2 * slot];
+                    l.dy = ws.ldir[2 * slot + 1];
+                    l.len = ws.llen[slot];
+                }
+                J.lnum[o] = nl;
+            }
+        }
+        if (wp && ispair) {
+            const int pos = pbase + __popc(pm & css::lanemask_lt());
+            if (pos < J.pair_cap) {
+                const size_t o = (size_t)i * J.pair_cap + pos;
+                J.pj[o] = j;
+                J.pd[o] = d;
+                const double* fr = m.frame + 9 * (size_t)f0;
+                J.pt[3 * o] = (double)tx * fr[3] + (double)ty * fr[6];
+                J.pt[3 * o + 1] = (double)tx * fr[4] + (double)ty * fr[7];
+                J.pt[3 * o + 2] = (double)tx * fr[5] + (double)ty * fr[8];
+            }
+        }
+        if (ispair && J.want_forces) {
+            const double du = pot_dudl(J.pot, d);
+            fx += du * (double)tx;
+            fy += du * (double)ty;
+            en += 0.5 * pot_u(J.pot, d);
+        }
+    }
+}
+
+template <class R, int SH>
+__device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, int lane, int* status,
+                           unsigned long long* counters, int item, int32_t* defer_list, int* defer_count) {
+    const DMesh& m = J.m;
+    const double rc = J.rc;
+    const int f0 = J.face[i];
+    const double* b = J.bary + 3 * (size_t)i;
+    const double qxd = b[1] * m.lay[3 * f0] + b[2] * m.lay[3 * f0 + 1];
+    const double qyd = b[2] * m.lay[3 * f0 + 2];
+    seed_source<R>(m, ws, sm, f0, qxd, qyd, rc, lane);
     unsigned long long n_prop = 0;
     const int max_waves = 4 * ws.wcap + 64;
     for (int wave = 0;; ++wave) {
@@ -1475,94 +1582,9 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
     double fx = 0.0, fy = 0.0, en = 0.0;
     int npair = 0;
     const bool wp = J.want_pairs != 0;
-    for (int fb = 0; fb < nface; fb += 32) {
-        const int fi = fb + lane;
-        int fl = -1, st = 0, cnt = 0;
-        if (fi < nface) {
-            fl = ws.flist[fi];
-            const int key = m.frank ? m.frank[fl] : fl;
-            st = J.fstart[key];
-            cnt = J.fstart[key + 1] - st;
-        }
-        int incl = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(CSS_FULL, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int total = __shfl_sync(CSS_FULL, incl, 31);
-        for (int tb = 0; tb < total; tb += 32) {
-            const int t = tb + lane;
-            int owner = 0;
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int v = __shfl_sync(CSS_FULL, incl, owner + step - 1);
-                if (v <= t) owner += step;
-            }
-            owner = min(owner, 31);
-            const int o_fl = __shfl_sync(CSS_FULL, fl, owner);
-            const int o_st = __shfl_sync(CSS_FULL, st, owner);
-            const int o_ex = __shfl_sync(CSS_FULL, incl - cnt, owner);
-            bool ispair = false;
-            double d = 0.0;
-            R tx = (R)0, ty = (R)0;
-            int j = -1;
-            VLink<SH == 2> ql;
-            if (t < total) {
-                j = J.fitems[o_st + (t - o_ex)];
-                if (j != i) {
-                    d = query<R>(m, ws, f0, qx, qy, o_fl, J.bary + 3 * (size_t)j, tx, ty, &ql);
-                    ispair = d < rc;
-                }
-            }
-            const unsigned pm = __ballot_sync(CSS_FULL, ispair);
-            if constexpr (SH == 2) {
-                // the pair's legs, from the target back to the source: its own link, then the
-                // link of each vertex on the way (still in this source's table)
-                const int pos = npair + __popc(pm & css::lanemask_lt());
-                if (ispair && pos < J.pair_cap) {
-                    const size_t o = (size_t)item * J.pair_cap + pos;
-                    int nl = 0;
-                    VLink<true> l = ql;
-                    for (;;) {
-                        if (nl >= J.lmax) { nl = -1; break; }
-                        const size_t a = o * J.lmax + nl;
-                        J.lfk[a] = l.fk;
-                        J.ldir[2 * a] = l.dx;
-                        J.ldir[2 * a + 1] = l.dy;
-                        J.llen[a] = l.len;
-                        ++nl;
-                        if (l.par < 0) break;
-                        const int slot = ws_vfind<R>(ws, l.par);
-                        if (slot < 0) { nl = -2; break; }
-                        l.par = ws.lpar[slot];
-                        l.fk = ws.lfk[slot];
-                        l.dx = ws.ldir[2 * slot];
-                        l.dy = ws.ldir[2 * slot + 1];
-                        l.len = ws.llen[slot];
-                    }
-                    J.lnum[o] = nl;
-                }
-            }
-            if (wp && ispair) {
-                const int pos = npair + __popc(pm & css::lanemask_lt());
-                if (pos < J.pair_cap) {
-                    const size_t o = (size_t)i * J.pair_cap + pos;
-                    J.pj[o] = j;
-                    J.pd[o] = d;
-                    const double* fr = m.frame + 9 * (size_t)f0;
-                    J.pt[3 * o] = (double)tx * fr[3] + (double)ty * fr[6];
-                    J.pt[3 * o + 1] = (double)tx * fr[4] + (double)ty * fr[7];
-                    J.pt[3 * o + 2] = (double)tx * fr[5] + (double)ty * fr[8];
-                }
-            }
-            npair += __popc(pm);
-            if (ispair && J.want_forces) {
-                const double du = pot_dudl(J.pot, d);
-                fx += du * (double)tx;
-                fy += du * (double)ty;
-                en += 0.5 * pot_u(J.pot, d);
-            }
-        }
-    }
+    for (int fb = 0; fb < nface; fb += 32)
+        eval_face_block<R>(J, i, ws, f0, qx, qy, fb, nface, lane, item,
+                           [&](unsigned pm) { const int b = npair; npair += __popc(pm); return b; }, fx, fy, en);
     fx = css::warp_sum(fx);
     fy = css::warp_sum(fy);
     en = css::warp_sum(en);
@@ -1584,6 +1606,301 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
         atomicAdd(counters + 3, (unsigned long long)npair);
     }
     __syncwarp();
+}
+
+// ------------------------------------------------------------------ team form
+// The W warps of a CTA work on one source.  For sets with fewer sources than resident warps
+// one warp per source leaves SMs idle and the launch lasts one source's chain; a team makes
+// each wave W times wider and spreads the insertions over W warps.  Every wave warp 0 picks
+// up to 32 W pending windows; each warp unfolds 32 of them; the children and vertex
+// candidates are staged in shared memory in (warp, lane, slot) order, and warp w inserts
+// those whose edge (vertex) id is w modulo W, so no two warps ever touch one edge list or
+// one vertex entry (the hash tables, the pool and the queues take concurrent claims through
+// atomics); emissions run on warp 0 between waves while the others wait.  Barriers separate
+// the phases, and every loop containing one has a trip count that is the same for all
+// threads of the CTA (read from shared memory after a barrier).
+constexpr int MAX_TEAM = 8;
+
+struct TeamSm {
+    int item;         // the team's current work item (>= nitems: none left)
+    int action;       // next step of the wave loop: 0 finished, 1 look again, 2 unfold nsel windows
+    int nsel;
+    int npair;        // slots taken in the source's pair row
+    double fx[MAX_TEAM], fy[MAX_TEAM], en[MAX_TEAM];
+    unsigned long long nprop[MAX_TEAM];
+    int sel[32 * MAX_TEAM];
+};
+
+// shared memory of a team besides the static part: its tables (shared placement), then the
+// staged children (64 per warp) and vertex candidates (96 per warp)
+template <class R>
+__host__ __device__ inline size_t team_child_off(int shared_scale) {
+    return al16(shared_scale ? sh_bytes_per_warp<R>(shared_scale) : 0);
+}
+template <class R>
+__host__ __device__ inline size_t team_vcand_off(int shared_scale, int W) {
+    return team_child_off<R>(shared_scale) + al16((size_t)64 * W * sizeof(Win<R>));
+}
+template <class R>
+__host__ __device__ inline size_t team_smem_bytes(int shared_scale, int W) {
+    return team_vcand_off<R>(shared_scale, W) + (size_t)96 * W * sizeof(VCand<R, false>);
+}
+
+// The next wave of a team: as select_wave, with up to `cap` windows written to sel[]
+// (run by one warp); returns how many were taken.
+template <class R, int SH>
+__device__ int select_wave_cap(Ws<R, SH>& ws, WarpSm& sm, int npend, float kmin, float kmax, int lane, int cap,
+                               int* sel) {
+    float T = kmax;
+    if (npend > cap) {
+        float lo = kmin, hi = kmax;
+        for (int it = 0; it < 12; ++it) {
+            const float mid = 0.5f * (lo + hi);
+            if (!(mid > lo && mid < hi)) break;
+            int c = 0;
+            for (int i = lane; i < npend; i += 32) c += ws.pk[i] <= mid ? 1 : 0;
+            c = (int)__reduce_add_sync(CSS_FULL, (unsigned)c);
+            if (c < cap) lo = mid;
+            else {
+                hi = mid;
+                T = mid;
+                if (c <= 2 * cap) break;
+            }
+        }
+    }
+    int taken = 0, kept = 0;
+    for (int base = 0; base < npend; base += 32) {
+        const int i = base + lane;
+        int id = -1;
+        float k = 0.0f;
+        if (i < npend) { id = ws.pq[i]; k = ws.pk[i]; }
+        __syncwarp();
+        const bool cand = i < npend && k <= T;
+        const unsigned cm = __ballot_sync(CSS_FULL, cand);
+        const int r = taken + __popc(cm & css::lanemask_lt());
+        const bool take = cand && r < cap;
+        const bool keep = i < npend && !take;
+        const unsigned km = __ballot_sync(CSS_FULL, keep);
+        if (take) sel[r] = id;
+        if (keep) {   // kept entries move forward only: p <= i
+            const int p = kept + __popc(km & css::lanemask_lt());
+            ws.pq[p] = id;
+            ws.pk[p] = k;
+        }
+        taken = min(cap, taken + __popc(cm));
+        kept += __popc(km);
+    }
+    __syncwarp();
+    if (lane == 0) sm.npend = kept;
+    __syncwarp();
+    return taken;
+}
+
+// One source processed by the team of the W warps of this CTA (see the team form above).
+template <class R, int SH>
+__device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, TeamSm& tm, Win<R>* cst,
+                                VCand<R, false>* vst, int W, int wid, int lane, int* status,
+                                unsigned long long* counters, int item, int32_t* defer_list, int* defer_count) {
+    const DMesh& m = J.m;
+    const double rc = J.rc;
+    const int f0 = J.face[i];
+    const double* b = J.bary + 3 * (size_t)i;
+    const double qxd = b[1] * m.lay[3 * f0] + b[2] * m.lay[3 * f0 + 1];
+    const double qyd = b[2] * m.lay[3 * f0 + 2];
+    if (wid == 0) {
+        seed_source<R>(m, ws, sm, f0, qxd, qyd, rc, lane);
+        if (lane == 0) tm.npair = 0;
+    }
+    __syncthreads();
+    unsigned long long n_prop = 0;
+    const int max_waves = 4 * ws.wcap + 64;
+    for (int wave = 0;; ++wave) {
+        // warp 0: emissions and the wave's selection; the others wait at the barrier
+        if (wid == 0) {
+            __syncwarp();
+            int act = 2;
+            const int npend = min(sm.npend, ws.wcap);
+            if ((npend == 0 && sm.nemit == 0) || sm.err) act = 0;
+            else if (wave > max_waves) {
+                if (lane == 0) atomicOr(&sm.err, css::ST_ITER_LIMIT);
+                act = 0;
+            } else {
+                float kmin, kmax;
+                pending_range<R>(ws, npend, lane, kmin, kmax);
+                if (sm.nemit > 0 && emit_round<R>(m, ws, sm, rc, npend ? (double)kmin : INFINITY, lane) > 0) act = 1;
+                else if (npend == 0) act = 1;
+                else {
+                    const int taken = select_wave_cap<R>(ws, sm, npend, kmin, kmax, lane, 32 * W, tm.sel);
+                    if (lane == 0) tm.nsel = taken;
+                }
+            }
+            if (lane == 0) tm.action = act;
+        }
+        __syncthreads();
+        const int act = tm.action;
+        const int nsel = tm.nsel;
+        __syncthreads();   // everyone has read the decision before warp 0 writes the next one
+        if (act == 0) break;
+        if (act == 1) continue;
+        // every warp unfolds its 32 windows and stages what they produce
+        const int k = wid * 32 + lane;
+        Win<R> w;
+        bool on = false;
+        if (k < nsel) {
+            const int idx = tm.sel[k];
+            w = ws.win[idx];
+            on = (w.flags & WIN_ALIVE) && !(w.flags & WIN_DONE) && (double)win_key<R>(w) < rc;
+            if (on) ws.win[idx].flags = w.flags | WIN_DONE;
+        }
+        VCand<R, false> vc[3];
+        Win<R> ch[2];
+        int nvc = 0, nch = 0;
+        if (on) propagate<R, false>(m, w, rc, vc, nvc, ch, nch);
+        n_prop += __popc(__ballot_sync(CSS_FULL, on));
+#pragma unroll 1
+        for (int q = 0; q < 3; ++q) {
+            VCand<R, false> c = q == 0 ? vc[0] : (q == 1 ? vc[1] : vc[2]);
+            if (q >= nvc) c.v = -1;
+            vst[3 * k + q] = c;
+        }
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+            Win<R> c = q == 0 ? ch[0] : ch[1];
+            if (q >= nch) c.he = -1;
+            cst[2 * k + q] = c;
+        }
+        __syncthreads();
+        // each warp takes the staged vertex candidates it owns (vertex id modulo W), in order
+        for (int base = 0; base < 3 * nsel; base += 32) {
+            const int s = base + lane;
+            VCand<R, false> c;
+            bool has = false;
+            if (s < 3 * nsel) {
+                c = vst[s];
+                has = c.v >= 0 && c.v % W == wid;
+            }
+            vertex_round<R>(m, ws, sm, has, c, rc, lane);
+        }
+        __syncthreads();
+        // and the staged children on the edges it owns (undirected edge id modulo W)
+        for (int base = 0; base < 2 * nsel; base += 32) {
+            const int s = base + lane;
+            Win<R> c;
+            bool has = false;
+            if (s < 2 * nsel) {
+                c = cst[s];
+                has = c.he >= 0 && m.edge[c.he] % W == wid;
+            }
+            child_round<R>(m, ws, sm, has, c, rc, lane);
+        }
+        __syncthreads();
+    }
+    const int err = sm.err;
+    // a patch too large for this pass's tables or pool: hand the source to the second pass
+    if (defer_list && (err & (css::ST_WIN_OVERFLOW | css::ST_HASH_OVERFLOW | css::ST_ITER_LIMIT))) {
+        if (wid == 0 && lane == 0) {
+            defer_list[atomicAdd(defer_count, 1)] = item;
+            atomicAdd(counters + 4, 1ull);
+        }
+        return;
+    }
+    // target evaluation: warp w takes the face blocks w, w + W, ...; pair slots from the
+    // team's counter; forces summed per warp, then over the warps in order
+    const int nface = min(sm.nface, ws.fcap);
+    const R qx = (R)qxd, qy = (R)qyd;
+    double fx = 0.0, fy = 0.0, en = 0.0;
+    for (int fb = 32 * wid; fb < nface; fb += 32 * W)
+        eval_face_block<R>(J, i, ws, f0, qx, qy, fb, nface, lane, item,
+                           [&](unsigned pm) {
+                               int base = 0;
+                               if (lane == 0 && pm) base = atomicAdd(&tm.npair, __popc(pm));
+                               return __shfl_sync(CSS_FULL, base, 0);
+                           },
+                           fx, fy, en);
+    fx = css::warp_sum(fx);
+    fy = css::warp_sum(fy);
+    en = css::warp_sum(en);
+    if (lane == 0) {
+        tm.fx[wid] = fx;
+        tm.fy[wid] = fy;
+        tm.en[wid] = en;
+        tm.nprop[wid] = n_prop;
+    }
+    __syncthreads();
+    if (wid == 0 && lane == 0) {
+        double sx = 0.0, sy = 0.0, se = 0.0;
+        unsigned long long np = 0;
+        for (int w2 = 0; w2 < W; ++w2) {
+            sx += tm.fx[w2];
+            sy += tm.fy[w2];
+            se += tm.en[w2];
+            np += tm.nprop[w2];
+        }
+        const int npair = tm.npair;
+        if (J.want_forces) {
+            const double* fr = m.frame + 9 * (size_t)f0;
+            J.force[3 * (size_t)i] = sx * fr[3] + sy * fr[6];
+            J.force[3 * (size_t)i + 1] = sx * fr[4] + sy * fr[7];
+            J.force[3 * (size_t)i + 2] = sx * fr[5] + sy * fr[8];
+            if (J.epot) atomicAdd(J.epot, se);
+        }
+        if (J.pcnt) J.pcnt[i] = npair;
+        int st = err;
+        if (J.want_pairs && npair > J.pair_cap) st |= css::ST_PAIR_OVERFLOW;
+        if (st) atomicOr(status, st);
+        atomicAdd(counters + 0, 1ull);
+        atomicAdd(counters + 1, (unsigned long long)min(sm.nwin, ws.wcap));
+        atomicAdd(counters + 2, np);
+        atomicAdd(counters + 3, (unsigned long long)npair);
+    }
+}
+
+// Team kernel: one CTA (W = blockDim / 32 warps, 2..8) per source at a time, persistent over
+// the work items; one workspace slice per CTA (g.nwarps counts teams).
+template <class R, int OCC, int SH>
+__global__ void __launch_bounds__(256, OCC) k_geodesic_team(const __grid_constant__ cssi::GeoJob job0,
+                                                       const cssi::GeoJob* jobs, cssi::GeoQueue q, cssi::GeoWs g,
+                                                       int* work, int* status, unsigned long long* counters) {
+    static_assert(SH != 2, "the path form runs one warp per source");
+    __shared__ WarpSm sm;
+    __shared__ TeamSm tm;
+    __shared__ Ws<R, SH> ws;
+    const int W = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int team = blockIdx.x;
+    if (team >= g.nwarps) return;   // the whole CTA
+    extern __shared__ __align__(16) unsigned char dsm[];
+    Win<R>* cst = (Win<R>*)(dsm + team_child_off<R>(g.shared));
+    VCand<R, false>* vst = (VCand<R, false>*)(dsm + team_vcand_off<R>(g.shared, W));
+    uint32_t gen = 0;
+    if (threadIdx.x == 0) {
+        ws = ws_bind<R, SH>(g, team);
+        if constexpr (SH == 1) ws_bind_shared<R, SH>(ws, dsm, g.shared);
+        gen = g.gen[team];
+    }
+    __syncthreads();
+    const int nitems = q.item_count ? min(*(volatile const int*)q.item_count, q.nitems) : q.nitems;
+    for (;;) {
+        if (threadIdx.x == 0) tm.item = atomicAdd(work, 1);
+        __syncthreads();
+        const int k = tm.item;
+        if (k >= nitems) break;
+        const int item = q.item_list ? q.item_list[k] : k;
+        const int jid = q.job_of_item ? q.job_of_item[item] : 0;
+        const cssi::GeoJob& J = jobs ? jobs[jid] : job0;
+        const int pos = q.src_of_item ? q.src_of_item[item] : item;
+        const int src = J.order ? J.order[pos] : pos;
+        if (threadIdx.x == 0) {
+            ++gen;
+            if (gen == 0) gen = 1;   // 0 marks never-used entries
+            ws.gen = gen;
+        }
+        __syncthreads();
+        run_source_team<R>(J, src, ws, sm, tm, cst, vst, W, wid, lane, status, counters, item, q.defer_list,
+                           q.defer_count);
+        __syncthreads();   // the team's state is free before the next claim
+    }
+    if (threadIdx.x == 0) g.gen[team] = gen;
 }
 
 // OCC = CTAs of 256 threads per SM the register budget must allow: 1 gives up to 255
@@ -1755,6 +2072,67 @@ int geodesic_blocks_per_sm(int precision, int warps_per_cta, int shared_scale, i
     }
     if (sh) return f32 ? blocks_per_sm<float, 1, true>(warps_per_cta, dyn) : blocks_per_sm<double, 1, true>(warps_per_cta, dyn);
     return f32 ? blocks_per_sm<float, 1, false>(warps_per_cta, dyn) : blocks_per_sm<double, 1, false>(warps_per_cta, dyn);
+}
+
+size_t geodesic_team_shared_bytes(int precision, int warps_per_cta, int shared_scale) {
+    return precision == CSS_FP32 ? team_smem_bytes<float>(shared_scale, warps_per_cta)
+                                 : team_smem_bytes<double>(shared_scale, warps_per_cta);
+}
+
+cudaError_t launch_geodesic_team(const GeoJob& job0, const GeoJob* djobs, const GeoQueue& q, int precision,
+                                 const GeoWs& ws, int warps_per_cta, int nctas, int* work_counter, int* status,
+                                 unsigned long long* counters, cudaStream_t st) {
+    if (warps_per_cta < 2 || warps_per_cta > MAX_TEAM) return cudaErrorInvalidValue;
+    const dim3 block(32 * warps_per_cta);
+    const size_t sm = geodesic_team_shared_bytes(precision, warps_per_cta, ws.shared);
+    const bool light = ws.occupancy == 2, sh = ws.shared != 0;
+#define CSS_LAUNCH(RT, O, S) \
+    k_geodesic_team<RT, O, S><<<nctas, block, sm, st>>>(job0, djobs, q, ws, work_counter, status, counters)
+    if (precision == CSS_FP32) {
+        if (light) { if (sh) CSS_LAUNCH(float, 2, 1); else CSS_LAUNCH(float, 2, 0); }
+        else { if (sh) CSS_LAUNCH(float, 1, 1); else CSS_LAUNCH(float, 1, 0); }
+    } else {
+        if (light) { if (sh) CSS_LAUNCH(double, 2, 1); else CSS_LAUNCH(double, 2, 0); }
+        else { if (sh) CSS_LAUNCH(double, 1, 1); else CSS_LAUNCH(double, 1, 0); }
+    }
+#undef CSS_LAUNCH
+    return cudaGetLastError();
+}
+
+// resident team CTAs per SM (0: the shape does not fit an SM)
+template <class R, int OCC, int SH>
+static int team_blocks_per_sm(int warps_per_cta, size_t dyn) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_geodesic_team<R, OCC, SH>) != cudaSuccess) { cudaGetLastError(); return 0; }
+    const int room = optin - (int)fa.sharedSizeBytes;
+    if (dyn > (size_t)room) return 0;
+    if (cudaFuncSetAttribute(k_geodesic_team<R, OCC, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, room) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_geodesic_team<R, OCC, SH>, 32 * warps_per_cta, dyn) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+int geodesic_team_blocks_per_sm(int precision, int warps_per_cta, int shared_scale, int occupancy) {
+    if (warps_per_cta < 2 || warps_per_cta > MAX_TEAM) return 0;
+    const size_t dyn = geodesic_team_shared_bytes(precision, warps_per_cta, shared_scale);
+    const bool f32 = precision == CSS_FP32, sh = shared_scale != 0;
+    if (occupancy == 2) {
+        if (sh) return f32 ? team_blocks_per_sm<float, 2, 1>(warps_per_cta, dyn) : team_blocks_per_sm<double, 2, 1>(warps_per_cta, dyn);
+        return f32 ? team_blocks_per_sm<float, 2, 0>(warps_per_cta, dyn) : team_blocks_per_sm<double, 2, 0>(warps_per_cta, dyn);
+    }
+    if (sh) return f32 ? team_blocks_per_sm<float, 1, 1>(warps_per_cta, dyn) : team_blocks_per_sm<double, 1, 1>(warps_per_cta, dyn);
+    return f32 ? team_blocks_per_sm<float, 1, 0>(warps_per_cta, dyn) : team_blocks_per_sm<double, 1, 0>(warps_per_cta, dyn);
 }
 
 cudaError_t launch_pairs_compact(int32_t n, const int32_t* pcnt, const int32_t* pj, const double* pd,

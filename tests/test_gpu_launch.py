@@ -17,7 +17,7 @@ css = pytest.importorskip("paper_2404_19751_gb300")
 pytestmark = pytest.mark.gpu
 
 BASE = dict(warps_per_cta=4, ctas_per_sm=0, tile=1, shared_scale=1, window_capacity=2048,
-            window_capacity2=16384, warps2_per_sm=2, occupancy=1, table_capacity=0)
+            window_capacity2=16384, warps2_per_sm=2, occupancy=1, table_capacity=0, team=0)
 
 SHAPES = [
     dict(),
@@ -32,6 +32,11 @@ SHAPES = [
     dict(occupancy=2, shared_scale=0, window_capacity=8192, tile=2),
     dict(shared_scale=0, window_capacity=8192, table_capacity=256),    # small tables: some deferred
     dict(occupancy=2, shared_scale=0, window_capacity=32768, table_capacity=2048, warps_per_cta=8),
+    # team form: all warps of a CTA on one source
+    dict(team=1, warps_per_cta=2),
+    dict(team=1, warps_per_cta=8, shared_scale=0, window_capacity=8192),
+    dict(team=1, warps_per_cta=4, occupancy=2, shared_scale=0, window_capacity=8192),
+    dict(team=1, warps_per_cta=4, window_capacity=64, window_capacity2=128),   # most sources deferred
 ]
 
 
@@ -66,13 +71,19 @@ def test_results_do_not_depend_on_launch_shape(case):
         if ref is None:
             ref = (F, g)
         else:
-            # each pair's distance and tangent is the same computation in every shape; only the
-            # order of a row's force sum may differ (which lane claims a face first)
+            # one warp per source: each pair's distance and tangent is the same computation in
+            # every shape, and only the order of a row's force sum may differ (which lane claims
+            # a face first); a team unfolds wider waves, so its windows (and the last bits of a
+            # distance reached through another but equally long unfolding) may differ
             assert np.max(np.abs(F - ref[0])) <= 1e-13 * np.max(np.abs(F0)), sh
             assert np.array_equal(g[0], ref[1][0]) and np.array_equal(g[1], ref[1][1])
-            assert np.array_equal(g[2], ref[1][2])
+            if sh.get("team"):
+                np.testing.assert_allclose(g[2], ref[1][2], rtol=1e-14, atol=0)
+            else:
+                assert np.array_equal(g[2], ref[1][2])
     assert deferred[0] == 0 and deferred[6] > len(face) // 2   # the tiny pool defers most sources
     assert deferred[10] > 0                                    # so do tables of 256 edge slots
+    assert deferred[15] > len(face) // 2                       # and a team's tiny pool
     parts.free()
     mesh.free()
     ctx.close()
@@ -82,7 +93,8 @@ def test_launch_shape_validation():
     ctx = css.create(0)
     for bad in (dict(warps_per_cta=0), dict(warps_per_cta=9), dict(shared_scale=3), dict(tile=0),
                 dict(window_capacity=10), dict(warps2_per_sm=0), dict(shared_scale=8, warps_per_cta=8),
-                dict(occupancy=3), dict(table_capacity=10), dict(table_capacity=1 << 21)):
+                dict(occupancy=3), dict(table_capacity=10), dict(table_capacity=1 << 21),
+                dict(team=1, warps_per_cta=1), dict(team=2)):
         with pytest.raises(css.CssError):
             ctx.set_launch(**dict(BASE, **bad))
     assert ctx.get_launch() == dict(BASE)    # a rejected shape leaves the old one
@@ -139,4 +151,46 @@ def test_autotuner_on_a_batch_then_batched_steps_match_single_sets():
         p.free()
     for mh in meshes:
         mh.free()
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["flat64", "saddle_fan8_n40"])
+def test_team_form_matches_oracle(name):
+    """The team form on all-pairs workloads with few sources (the flat plane's 64, a saddle
+    cone's 40): FP64 neighbours and forces equal the oracle's, FP32 within its bar, and an
+    NVE step equals the oracle's step."""
+    from tests.test_gpu_parity import WORKLOADS
+    from tests._common import FP32_REL_DIAM, descent_checker
+    import math
+    m, face, bary, r_c = WORKLOADS[name]()
+    sig = 0.3
+    pot = dict(kind=css.POT_HARMONIC, eps=1.0, sigma=sig, r_cut=sig)
+    ctx = css.create(0)
+    mesh = css.mesh_upload(ctx, m.verts, m.faces, m.period)
+    om = O.OracleMesh(m)
+    rows = om.neighbors_gap(face, bary, r_c)
+    F0, E0 = om.forces(face, bary, sig, pot)
+    for sh in (dict(team=1, warps_per_cta=8), dict(team=1, warps_per_cta=4, shared_scale=0, window_capacity=8192)):
+        ctx.set_launch(**dict(BASE, **sh))
+        parts = css.particles_set(ctx, mesh, face, bary)
+        g = css.geodesic_neighbors(parts, r_c, css.FP64)
+        compare_pairs(g, rows, r_c, FP64_RTOL, 1e-7)
+        F, E = css.compute_forces(parts, pot, sig, css.FP64)
+        assert np.max(np.abs(F - F0)) <= FP64_RTOL * np.max(np.abs(F0))
+        assert E == pytest.approx(E0, rel=1e-10)
+        tol = FP32_REL_DIAM * synth.bbox_diagonal(m)
+        g32 = css.geodesic_neighbors(parts, r_c, css.FP32)
+        compare_pairs(g32, rows, r_c, tol, 1e-5, rel=False, band=tol, tie=tol,
+                      walker=descent_checker(om, face, bary, r_c), land_tol=1e-7)
+        parts.free()
+    vel = synth.gaussian_tangent_velocities(m, face, 0.1, 1.0, 5)
+    integ = dict(kind=css.INT_NVE, dt=0.002, kT=0.1, lam=1.0, v0=0.0, Dr=0.0, mass=1.0, max_disp=math.inf)
+    parts = css.particles_set(ctx, mesh, face, bary, vel)
+    css.integrate_step(parts, pot, integ, sig, css.FP64, 2)
+    s = css.particles_get(parts)
+    o = om.integrate(face, bary, vel, None, F0, pot, integ, sig, 2)
+    assert np.array_equal(s["face"], o["face"])
+    np.testing.assert_allclose(s["bary"], o["bary"], atol=1e-9)
+    parts.free()
+    mesh.free()
     ctx.close()
