@@ -488,6 +488,7 @@ int css_mesh_free(css_mesh* m) {
     cudaFree(m->frame); cudaFree(m->theta); cudaFree(m->pseudo); cudaFree(m->bnd);
     cudaFree(m->ring_start); cudaFree(m->ring); cudaFree(m->X); cudaFree(m->he32); cudaFree(m->lay32);
     cudaFree(m->frank);
+    cudaFree(m->cang);
     cssi::vhm_free(m);
     delete m;
     return CSS_OK;

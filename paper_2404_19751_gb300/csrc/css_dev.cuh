@@ -46,6 +46,9 @@ struct DMesh {
     const HeRec32* he32;          // 3 nf, FP32 copies of he
     const float* lay32;           // 3 nf, FP32 copies of lay
     const int32_t* frank;         // nf: rank of each face along a Morton curve (bucket order)
+    const float2* cang;           // 3 nf: (start, width) of corner h around its vertex, angles
+                                  // counted counter-clockwise from one fixed edge; NaN on boundary
+                                  // and non-manifold vertices
 };
 
 __device__ __forceinline__ double cross2(double ax, double ay, double bx, double by) { return ax * by - ay * bx; }

@@ -93,6 +93,7 @@ struct css_mesh {
     css::HeRec32* he32 = nullptr;
     float* lay32 = nullptr;
     int32_t* frank = nullptr;   // nf: Morton rank of each face
+    float2* cang = nullptr;     // 3 nf: corner (start, width) around its vertex
     cssi::VhmOp* vhm = nullptr;
     css::DMesh view() const;
 };

@@ -427,7 +427,18 @@ struct VCand : VLink<L> {
     int32_t fixed;   // tangent comes from a pseudo-source path
     double d;        // exact FP64 length
     R tx, ty;
+    float back;      // direction of the path's last leg, seen from the vertex, as a cumulative
+                     // corner angle (DMesh::cang); NaN where it is not known
 };
+
+// Cumulative angle at a vertex of the direction g, given the vertex's corner hc whose first
+// edge runs along e (both in one face layout); NaN when g is too short to have a reliable
+// direction or the corner has no cumulative angle.
+__device__ __forceinline__ float back_angle(const DMesh& m, int hc, double ex, double ey, double gx, double gy,
+                                            double scale) {
+    if (hc < 0 || !(gx * gx + gy * gy > 1e-12 * scale * scale)) return __int_as_float(0x7fffffff);
+    return m.cang[hc].x + atan2f((float)(ex * gy - ey * gx), (float)(ex * gx + ey * gy));
+}
 
 // The link of the point (X, Y) of window W's half-edge frame straight back to W's
 // pseudo-source: which = 2 the far corner of the face W enters (the direction lies in that
@@ -501,6 +512,12 @@ __device__ __forceinline__ void propagate(const DMesh& m, const Win<R>& W, doubl
         c.fixed = W.flags & WIN_FIXED;
         c.d = win_dist_exact<R>(W, X, Y);
         win_tangent<R>(W, Xf, Yf, c.tx, c.ty);
+        // the last leg back to the pseudo-source: at the start vertex it leaves below corner
+        // h's first edge (u -> v), at the end vertex it lies in the corner of the face across
+        // the edge (first edge v -> u), at the far corner inside corner c (first edge c -> u)
+        c.back = degen ? __int_as_float(0x7fffffff)
+                       : back_angle(m, a == 0 ? h : (a == 1 ? m.twin[h] : 3 * f + k2), a == 0 ? 1.0 : (a == 1 ? -1.0 : -r.cx),
+                                    a == 2 ? -r.cy : 0.0, W.sx - X, W.sy - Y, r.L);
         if constexpr (L) win_link(m, W, X, Y, a, c);
     }
     if (!sees) return;
@@ -979,6 +996,15 @@ __device__ __forceinline__ int group_rounds(bool has, int key, int lane, int& ra
     return (int)__reduce_max_sync(CSS_FULL, (unsigned)__popc(grp));
 }
 
+// Vertex table flags: bit 0 queued for emission, bit 1 distance from a pseudo-source path,
+// bits 16..31 the back direction of the recorded path (DMesh::cang units) in steps of 1/4096
+// rad offset by 4 rad; 0xffff where it is unknown or out of range.
+constexpr float BACK_STEP = 4096.0f, BACK_OFF = 4.0f;
+__device__ __forceinline__ unsigned pack_back(float b) {
+    const float t = (b + BACK_OFF) * BACK_STEP;
+    return (t >= 0.0f && t < 65535.0f) ? (unsigned)__float2int_rn(t) : 0xffffu;   // NaN -> unknown
+}
+
 template <class R, int SH>
 __device__ __noinline__ void vertex_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, bool has,
                                           const VCand<R, SH == 2>& c, double rc, int lane) {
@@ -1008,7 +1034,7 @@ __device__ __noinline__ void vertex_round(const DMesh& m, Ws<R, SH>& ws, WarpSm&
                 ws.vdist[slot] = d < vd ? d : vd;
                 ws.vtan[2 * slot] = c.tx;
                 ws.vtan[2 * slot + 1] = c.ty;
-                ws.vflag[slot] = c.fixed ? (vf | 2) : (vf & ~2);
+                ws.vflag[slot] = (int)((pack_back(c.back) << 16) | (unsigned)(c.fixed ? ((vf | 2) & 3) : (vf & 1)));
                 if constexpr (SH == 2) {
                     ws.lpar[slot] = c.par;
                     ws.lfk[slot] = c.fk;
@@ -1054,6 +1080,14 @@ __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& 
 // candidate a window yields is at least that window's key, so vertices with
 // d(v) <= kmin (the smallest queued key) go now and the others wait.  Returns the number
 // of vertices emitted.
+// Only corners that meet the vertex's shadow get a window: a shortest path that passes
+// through an interior vertex of angle sum T leaves it at least pi away from its incoming
+// direction on both sides, i.e. within [b + pi, b + T - pi] of the back direction b of any
+// shortest path to the vertex (outside that range the bend can be cut short on the side
+// where it is below pi, so the continuation is not shortest).  The range is widened by
+// SHADOW_TOL for the rounding of b and of the corner angles; vertices without a known back
+// direction, boundary and non-manifold vertices emit on every corner.
+constexpr float SHADOW_TOL = 1e-3f;
 template <class R, int SH>
 __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, double rc, double kmin, int lane) {
     __syncwarp();
@@ -1081,14 +1115,24 @@ __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm
         int vid = 0, rs = 0, len = 0;
         double dv = 0.0;
         R tx = (R)0, ty = (R)0;
+        float lo = -INFINITY, hi = INFINITY, th = 0.0f;   // the shadow, [lo, hi] (mod th)
         if (has) {
             vid = ws.vvid[vs];
             dv = ws.vdist[vs];
             tx = ws.vtan[2 * vs];
             ty = ws.vtan[2 * vs + 1];
-            ws.vflag[vs] &= ~1;
+            const int fl = ws.vflag[vs];
+            ws.vflag[vs] = fl & ~1;
             rs = m.ring_start[vid];
             len = m.ring_start[vid + 1] - rs;
+            const unsigned qb = (unsigned)fl >> 16;
+            if (qb != 0xffffu) {
+                th = (float)m.theta[vid];
+                const float b = (float)qb * (1.0f / BACK_STEP) - BACK_OFF;
+                lo = b + 3.14159265f - SHADOW_TOL;
+                lo -= th * floorf(lo / th);
+                hi = lo + (th - 6.28318531f + 2.0f * SHADOW_TOL);
+            }
         }
         // one window per (emitting vertex, opposite edge), 32 at a time: lane t takes the
         // t-th pair of the flattened list (owner = the vertex whose ring holds it)
@@ -1113,6 +1157,9 @@ __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm
             const double o_dv = __shfl_sync(CSS_FULL, dv, owner);
             const R o_tx = __shfl_sync(CSS_FULL, tx, owner);
             const R o_ty = __shfl_sync(CSS_FULL, ty, owner);
+            const float o_lo = __shfl_sync(CSS_FULL, lo, owner);
+            const float o_hi = __shfl_sync(CSS_FULL, hi, owner);
+            const float o_th = __shfl_sync(CSS_FULL, th, owner);
             int o_vid = 0;
             if constexpr (SH == 2) o_vid = __shfl_sync(CSS_FULL, vid, owner);
             bool hh = t < total;
@@ -1123,7 +1170,16 @@ __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm
                 const int hop = 3 * f + (k == 2 ? 0 : k + 1);
                 face_add(ws, sm, f);
                 const int tw = m.twin[hop];
-                if (tw < 0) hh = false;
+                // the corner's wedge [a, a + w] against the shadow, one turn either way; NaN
+                // bounds never miss
+                const float2 cw = m.cang[hc];
+                bool miss = true;
+#pragma unroll 1
+                for (int s = -1; s <= 1; ++s) {
+                    const float a = cw.x + (float)s * o_th;
+                    if (!(a > o_hi || a + cw.y < o_lo)) miss = false;
+                }
+                if (tw < 0 || miss) hh = false;
                 else {
                     const HeRec r = m.he[hop];
                     c.he = tw;
@@ -1380,6 +1436,9 @@ __device__ __forceinline__ void seed_source(const DMesh& m, Ws<R, SH>& ws, WarpS
             c.d = d;
             c.tx = (R)(d > 0.0 ? dx / d : 1.0);
             c.ty = (R)(d > 0.0 ? dy / d : 0.0);
+            double nx, ny;   // the corner's first edge runs to the next corner of the face
+            css::face_corner(m, f0, lane + 1, nx, ny);
+            c.back = back_angle(m, 3 * f0 + lane, nx - vx, ny - vy, -dx, -dy, m.lay[3 * f0]);
             if constexpr (SH == 2) {   // straight back to the source
                 c.par = -1;
                 c.fk = 4 * f0 + lane;

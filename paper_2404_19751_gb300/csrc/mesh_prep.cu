@@ -169,8 +169,14 @@ __global__ void k_ring_scatter(const int32_t* F, int64_t nf, const int32_t* ring
 }
 
 // sort each ring by half-edge id (deterministic order), sum corner angles, set flags
-__global__ void k_vertices(int64_t nv, const int32_t* ring_start, int32_t* ring, const HeRec* he, double* theta,
-                           const uint8_t* bnd, uint8_t* pseudo, unsigned long long* n_pseudo) {
+// Angle sum of every vertex and its pseudo-source flag (boundary, flat or saddle); and the
+// cumulative angle of every corner around its vertex: starting from the corner of smallest
+// half-edge id, corners follow counter-clockwise (the next corner is the one across the edge
+// the current corner ends on), each at the sum of the widths before it.  A ring that is not
+// one closed fan (boundary, non-manifold vertex) gets NaN.
+__global__ void k_vertices(int64_t nv, const int32_t* ring_start, int32_t* ring, const HeRec* he,
+                           const int32_t* twin, double* theta, const uint8_t* bnd, uint8_t* pseudo, float2* cang,
+                           unsigned long long* n_pseudo) {
     int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= nv) return;
     int s = ring_start[v], e = ring_start[v + 1];
@@ -189,6 +195,28 @@ __global__ void k_vertices(int64_t nv, const int32_t* ring_start, int32_t* ring,
     uint8_t p = (uint8_t)(bnd[v] || th >= TWO_PI - 1e-9);
     pseudo[v] = p;
     if (p) atomicAdd(n_pseudo, 1ull);
+    bool closed = false;
+    if (!bnd[v] && e > s) {
+        const int32_t h0 = ring[s];
+        int32_t h = h0;
+        double cum = 0.0;
+        int steps = 0;
+        while (steps < e - s) {
+            const HeRec& r = he[h];
+            const double w = atan2(r.cy, r.cx);
+            cang[h] = make_float2((float)cum, (float)w);
+            cum += w;
+            ++steps;
+            const int32_t f = h / 3, k = h - 3 * f;
+            const int32_t nh = twin[3 * f + (k == 0 ? 2 : k - 1)];   // the corner across the edge c -> v
+            if (nh < 0) break;
+            h = nh;
+            if (h == h0) { closed = true; break; }
+        }
+        closed = closed && steps == e - s;
+    }
+    if (!closed)
+        for (int i = s; i < e; ++i) cang[ring[i]] = make_float2(NAN, NAN);
 }
 
 inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
@@ -236,6 +264,7 @@ css::DMesh css_mesh::view() const {
     d.he32 = he32;
     d.lay32 = lay32;
     d.frank = frank;
+    d.cang = cang;
     return d;
 }
 
@@ -291,6 +320,7 @@ int build_mesh(css_ctx* ctx, const double* dX, int64_t nv, const int32_t* dF, in
     CK(cudaMalloc(&m->he32, nh * sizeof(css::HeRec32)));
     CK(cudaMalloc(&m->lay32, 3 * nf * sizeof(float)));
     CK(cudaMalloc(&m->frank, nf * sizeof(int32_t)));
+    CK(cudaMalloc(&m->cang, nh * sizeof(float2)));
     CK(cudaMalloc(&ring_cnt, (nv + 1) * sizeof(int32_t)));
     CK(cudaMalloc(&tmp, scan_tmp_ints(nv + 1) * sizeof(int32_t)));
     CK(cudaMemcpyAsync(m->X, dX, 3 * nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -320,7 +350,8 @@ int build_mesh(css_ctx* ctx, const double* dX, int64_t nv, const int32_t* dF, in
     CK(launch_scan_i32(ring_cnt, m->ring_start, nv + 1, tmp, st));
     CK(cudaMemsetAsync(ring_cnt, 0, (nv + 1) * sizeof(int32_t), st));
     k_ring_scatter<<<nblk(nh), 256, 0, st>>>(dF, nf, m->ring_start, ring_cnt, m->ring);
-    k_vertices<<<nblk(nv), 256, 0, st>>>(nv, m->ring_start, m->ring, m->he, m->theta, m->bnd, m->pseudo, dcnt + 1);
+    k_vertices<<<nblk(nv), 256, 0, st>>>(nv, m->ring_start, m->ring, m->he, m->twin, m->theta, m->bnd, m->pseudo,
+                                         m->cang, dcnt + 1);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(hcnt, dcnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
