@@ -1074,8 +1074,8 @@ __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& 
     }
 }
 
-// Pseudo-source vertices whose distance is final start windows on every edge opposite
-// them; their one-ring faces join the target faces (paths may bend there, Sec. 2.2).  A
+// Pseudo-source vertices whose distance is final start windows on the edges opposite
+// them; those one-ring faces join the target faces (paths may bend there, Sec. 2.2).  A
 // vertex's distance is final once no queued window can still shorten it: every
 // candidate a window yields is at least that window's key, so vertices with
 // d(v) <= kmin (the smallest queued key) go now and the others wait.  Returns the number
@@ -1168,10 +1168,9 @@ __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm
                 const int hc = m.ring[o_rs + (t - o_ex)];
                 const int f = hc / 3, k = hc - 3 * f;
                 const int hop = 3 * f + (k == 2 ? 0 : k + 1);
-                face_add(ws, sm, f);
-                const int tw = m.twin[hop];
                 // the corner's wedge [a, a + w] against the shadow, one turn either way; NaN
-                // bounds never miss
+                // bounds never miss.  A corner outside the shadow adds neither a window nor its
+                // face: no shortest path leaves the vertex into it
                 const float2 cw = m.cang[hc];
                 bool miss = true;
 #pragma unroll 1
@@ -1179,7 +1178,9 @@ __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm
                     const float a = cw.x + (float)s * o_th;
                     if (!(a > o_hi || a + cw.y < o_lo)) miss = false;
                 }
-                if (tw < 0 || miss) hh = false;
+                if (!miss) face_add(ws, sm, f);
+                const int tw = miss ? -1 : m.twin[hop];
+                if (tw < 0) hh = false;
                 else {
                     const HeRec r = m.he[hop];
                     c.he = tw;
