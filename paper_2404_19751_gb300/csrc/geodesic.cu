@@ -628,6 +628,14 @@ __device__ __forceinline__ void ivl_add(Ivl<R>& L, R x0, R x1, bool cover = true
     else if (cover) L.b[MAXP - 1] = x1;
 }
 
+// a[i] = x for a runtime index into a register array (predicated moves, no local memory)
+template <class T, int N>
+__device__ __forceinline__ void reg_set(T (&a)[N], int i, const T& x) {
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        if (k == i) a[k] = x;
+}
+
 template <class R, int SH>
 __device__ __forceinline__ void face_add(Ws<R, SH>& ws, WarpSm& sm, int32_t f) {
     bool claimed;
@@ -807,166 +815,270 @@ __device__ __forceinline__ bool same_family(const Win<R>& a, const Win<R>& b) {
            __double_as_longlong(a.sig) == __double_as_longlong(b.sig);
 }
 
-// Insert candidate window c on its edge (list slot es), intersecting it with every window
-// already on the edge from either side: on each overlap both keep only where they carry
-// the smaller distance.  Executed by one lane per edge.
-template <class R, int SH>
-__device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int es, Win<R> c, double rc);
-
-template <class R, int SH>
-__device__ __forceinline__ void insert_window(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int es, const Win<R>& c0,
-                                              double rc) {
-    if (ws.ehead[es] >= 0) { insert_window_general<R>(m, ws, sm, es, c0, rc); return; }
-    // first window on this edge: nothing to intersect with
-    Win<R> c = c0;
-    const R Lr = sizeof(R) == sizeof(float) ? (R)m.he32[c.he].L : (R)m.he[c.he].L;
-    if (c.b0 < (R)0) c.b0 = (R)0;
-    if (c.b1 > Lr) c.b1 = Lr;
-    if (!(c.b1 - c.b0 > (R)Tol<R>::w * Lr) || !((double)win_key<R>(c) < rc)) return;
-    const int id = win_alloc<R>(sm, ws.wcap);
-    if (id < 0) return;
-    c.flags = (c.flags & WIN_FIXED) | WIN_ALIVE;
-    c.next = -1;
-    ws.win[id] = c;
-    ws.ehead[es] = id;
-    push_pending<R>(ws, sm, id, (float)win_key<R>(c));
-    face_add(ws, sm, c.he / 3);
+// Subtract [x0, x1] from a sorted piece list.  Parts narrower than tolw are dropped; a cut
+// that would need more than MAXP pieces leaves the piece whole (more coverage, never less).
+template <class R>
+__device__ __forceinline__ void ivl_sub(Ivl<R>& P, R x0, R x1, R tolw) {
+    if (!(x1 > x0)) return;
+    Ivl<R> out;
+    out.n = 0;
+#pragma unroll
+    for (int k = 0; k < MAXP; ++k) { out.a[k] = (R)0; out.b[k] = (R)0; }
+#pragma unroll 1
+    for (int p = 0; p < P.n; ++p) {
+        const R a = ivl_get<R>(P.a, p), b = ivl_get<R>(P.b, p);
+        const bool l = x0 - a > tolw, r = b - x1 > tolw;
+        if (!(x1 > a && x0 < b) || out.n + (l ? 1 : 0) + (r ? 1 : 0) + (P.n - 1 - p) > MAXP) {
+            ivl_add<R>(out, a, b);
+            continue;
+        }
+        if (l) ivl_add<R>(out, a, x0);
+        if (r) ivl_add<R>(out, x1, b);
+    }
+    P = out;
 }
 
+// Window o (id oi, on the candidate's edge, interval [o0, o1] in the candidate's frame) loses
+// the pieces `lost`: it keeps the rest (padded outward by the FP32 widening), in place, as
+// extra windows linked right after it, or not at all (then it is marked dead and left in
+// the list; the next walk over the list unlinks it).
 template <class R, int SH>
-__device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int es, Win<R> c, double rc) {
-    const double Ld = m.he[c.he].L;
-    const R Lr = (R)Ld;
-    const R tolw = (R)Tol<R>::w * Lr;
-    const bool c_direct = !(c.flags & WIN_FIXED);
-    if (c.b0 < (R)0) c.b0 = (R)0;
-    if (c.b1 > Lr) c.b1 = Lr;
-    if (!(c.b1 - c.b0 > tolw) || !((double)win_key<R>(c) < rc)) return;
+__device__ __forceinline__ void window_keep(Ws<R, SH>& ws, WarpSm& sm, const Win<R>& o, int oi, bool same, R o0, R o1,
+                                            R Lr, R tolw, const Ivl<R>& lost) {
+    Ivl<R> keep;
+    keep.n = 0;
+#pragma unroll
+    for (int k = 0; k < MAXP; ++k) { keep.a[k] = keep.b[k] = (R)0; }
+    R cur = o0;
+#pragma unroll 1
+    for (int q = 0; q < lost.n; ++q) {
+        const R l0 = ivl_get<R>(lost.a, q), l1 = ivl_get<R>(lost.b, q);
+        if (l0 - cur > tolw) ivl_add<R>(keep, cur, l0);
+        if (l1 > cur) cur = l1;
+    }
+    if (o1 - cur > tolw) ivl_add<R>(keep, cur, o1);
+    if (keep.n == 0) {
+        ws.win[oi].flags = o.flags & ~WIN_ALIVE;
+        return;
+    }
+    int tail = oi;
+    const int onext = ws.win[oi].next;
+    const R wpad = (R)Widen<R>::mu * Lr;   // outward rounding of the kept parts
+#pragma unroll 1
+    for (int q = 0; q < keep.n; ++q) {
+        const R ka = ivl_get<R>(keep.a, q), kb = ivl_get<R>(keep.b, q);
+        R k0 = (same ? ka : Lr - kb) - wpad;
+        R k1 = (same ? kb : Lr - ka) + wpad;
+        k0 = k0 < (R)0 ? (R)0 : k0;
+        k1 = k1 > Lr ? Lr : k1;
+        if (q == 0) { ws.win[oi].b0 = k0; ws.win[oi].b1 = k1; }
+        else {
+            const int pid = win_alloc<R>(sm, ws.wcap);
+            if (pid < 0) break;
+            Win<R> piece = o;
+            piece.b0 = k0; piece.b1 = k1;
+            piece.next = onext;
+            ws.win[pid] = piece;
+            if (!(o.flags & WIN_DONE)) push_pending<R>(ws, sm, pid, (float)win_key<R>(piece));
+            ws.win[tail].next = pid;          // keep the list order
+            tail = pid;
+        }
+    }
+}
+
+// Compare candidate c (pseudo-source (csx, csy), length csig, interval [h0, h1] on its
+// half-edge che of length Lr) with window o (id oi) of the same edge: on their overlap both
+// keep only where they carry the smaller distance.  o's loss is applied at once; the
+// candidate's loss (at most three pieces) is returned in cl.
+template <class R, int SH>
+__device__ __forceinline__ void compare_pair(Ws<R, SH>& ws, WarpSm& sm, int oi, double csx, double csy, double csig,
+                                             int che, int cflags, R h0, R h1, R Lr, R tolw, Ivl<R>& cl) {
+    cl.n = 0;
+#pragma unroll
+    for (int k = 0; k < MAXP; ++k) { cl.a[k] = cl.b[k] = (R)0; }
+    const Win<R> o = ws.win[oi];
+    const bool same = (o.he == che);
+    const R o0 = same ? o.b0 : Lr - o.b1, o1 = same ? o.b1 : Lr - o.b0;
+    const R lo = h0 > o0 ? h0 : o0, hi = h1 < o1 ? h1 : o1;
+    if (!(hi - lo > tolw)) return;
+    const bool c_direct = !(cflags & WIN_FIXED);
+    Ivl<R> lost;
+    lost.n = 0;
+#pragma unroll
+    for (int k = 0; k < MAXP; ++k) { lost.a[k] = lost.b[k] = (R)0; }
+    // FP32 copies of both pseudo-sources in the candidate's frame (conversions in the FP64
+    // form; the margins of the FP32 tests cover their rounding)
+    const float fcx = (float)csx, fcy = (float)csy, fcs = (float)csig;
+    const float fox = same ? (float)fsx(o) : (float)Lr - (float)fsx(o);
+    const float foy = same ? (float)fsy(o) : -(float)fsy(o);
+    const float fos = (float)fsig(o);
+    const bool eq_sig = __double_as_longlong(csig) == __double_as_longlong(o.sig);
+    int cmp = CMP_SPLIT;
+    if (same && eq_sig && __double_as_longlong(csx) == __double_as_longlong(o.sx) &&
+        __double_as_longlong(csy) == __double_as_longlong(o.sy))
+        cmp = CMP_EXISTING;   // the same path family: equal everywhere, ties stay
+    else if (!eq_sig) cmp = dominance_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi);
+    // equal sigma: the exact bisector split below is cheaper than any FP32 attempt
+    if (cmp == CMP_EXISTING) ivl_add<R>(cl, lo, hi, false);
+    else if (cmp == CMP_CANDIDATE) ivl_add<R>(lost, lo, hi, false);
+    else {
+        // split of the overlap at the equal-distance points: FP32 with rigorous margins
+        // where it can decide, else exact
+        R bq[4];
+        bool cw[3];
+        int npz = 0;
+        bool done32 = false;
+        if (sizeof(R) == sizeof(float) && !eq_sig) {
+            float bpf[4];
+            done32 = split_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi, bpf, cw, npz);
+            if (done32) { bq[0] = (R)bpf[0]; bq[1] = (R)bpf[1]; bq[2] = (R)bpf[2]; bq[3] = (R)bpf[3]; }
+        }
+        if (!done32) {
+            const double Ld = (double)Lr;
+            const double osx = same ? o.sx : Ld - o.sx, osy = same ? o.sy : -o.sy;
+            double bp[4];
+            npz = split_exact(csx, csy, csig, osx, osy, o.sig, (double)lo, (double)hi,
+                              c_direct && (o.flags & WIN_FIXED), bp, cw);
+            bq[0] = (R)bp[0]; bq[1] = (R)bp[1]; bq[2] = (R)bp[2]; bq[3] = (R)bp[3];
+        }
+#pragma unroll 1
+        for (int q = 0; q < npz; ++q) {
+            if (cw[q]) ivl_add<R>(lost, bq[q], bq[q + 1], false);
+            else ivl_add<R>(cl, bq[q], bq[q + 1], false);
+        }
+    }
+    if (lost.n > 0) window_keep<R>(ws, sm, o, oi, same, o0, o1, Lr, tolw, lost);
+}
+
+// Windows a lane collects per walk of an insertion round.
+constexpr int WALK_K = 4;
+
+// One insertion round, all lanes together.  Lane l (has) inserts candidate c into the list
+// of edge slot es; lanes of one round hold different edges.  A candidate on an empty edge
+// is linked at once.  The others alternate walks and comparisons until their lists are
+// done: each lane walks its list (unlinking dead windows) and collects up to WALK_K live
+// windows overlapping its candidate's hull; the collected (candidate, window) pairs are
+// spread over all 32 lanes, each compares one pair, applies the window's loss, and hands the
+// candidate's loss back to its lane, which cuts it from the candidate's pieces.  Every window
+// on an edge is compared with the whole candidate; the candidate keeps the points where it
+// beats all of them, and each window the points where the candidate does not beat it, so
+// the smallest distance at every point stays covered.  What remains of the candidate is
+// linked at the head of the list.
+template <class R, int SH>
+__device__ __noinline__ void insert_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, bool has, int es,
+                                          const Win<R>& c0, double rc, int lane) {
+    Win<R> c = c0;
+    R Lr = (R)0, tolw = (R)0;
+    int cursor = -1;
+    if (has) {
+        Lr = sizeof(R) == sizeof(float) ? (R)m.he32[c.he].L : (R)m.he[c.he].L;
+        tolw = (R)Tol<R>::w * Lr;
+        if (c.b0 < (R)0) c.b0 = (R)0;
+        if (c.b1 > Lr) c.b1 = Lr;
+        has = (c.b1 - c.b0 > tolw) && (double)win_key<R>(c) < rc;
+        if (has) cursor = ws.ehead[es];
+        c.flags = (c.flags & WIN_FIXED) | WIN_ALIVE;
+    }
+    if (has && cursor < 0) {   // first window on this edge: nothing to intersect with
+        has = false;
+        const int id = win_alloc<R>(sm, ws.wcap);
+        if (id >= 0) {
+            c.next = -1;
+            ws.win[id] = c;
+            ws.ehead[es] = id;
+            push_pending<R>(ws, sm, id, (float)win_key<R>(c));
+            face_add(ws, sm, c.he / 3);
+        }
+    }
+    if (!__any_sync(CSS_FULL, has)) return;
     Ivl<R> pc;
-    pc.n = 1;
+    pc.n = has ? 1 : 0;
     pc.a[0] = c.b0; pc.b[0] = c.b1;
 #pragma unroll
     for (int k = 1; k < MAXP; ++k) { pc.a[k] = (R)0; pc.b[k] = (R)0; }
-    int prev = -1;
-    int oi = ws.ehead[es];
-    int guard = 0;
-    int err = 0;
-    while (oi >= 0 && pc.n > 0) {
-        if (++guard > ws.wcap) { err |= css::ST_ITER_LIMIT; break; }
-        Win<R> o = ws.win[oi];
-        const int onext = o.next;
-        if (!(o.flags & WIN_ALIVE)) {                       // unlink dead windows
-            if (prev < 0) ws.ehead[es] = onext; else ws.win[prev].next = onext;
-            oi = onext;
-            continue;
-        }
-        const bool same = (o.he == c.he);
-        const R o0 = same ? o.b0 : Lr - o.b1, o1 = same ? o.b1 : Lr - o.b0;
-        Ivl<R> npc, lost;
-        npc.n = 0; lost.n = 0;
+    int prev = -1, guard = 0, err = 0;
+    while (__any_sync(CSS_FULL, has && cursor >= 0 && pc.n > 0)) {
+        // ---- walk: up to WALK_K live windows overlapping the candidate's hull
+        int ids[WALK_K];
 #pragma unroll
-        for (int k = 0; k < MAXP; ++k) { npc.a[k] = npc.b[k] = lost.a[k] = lost.b[k] = (R)0; }
-#pragma unroll 1
-        for (int p = 0; p < pc.n; ++p) {      // one copy of the comparison code (instruction cache)
-            const R a0 = ivl_get<R>(pc.a, p), a1 = ivl_get<R>(pc.b, p);
-            const R lo = a0 > o0 ? a0 : o0, hi = a1 < o1 ? a1 : o1;
-            if (!(hi - lo > tolw)) { ivl_add<R>(npc, a0, a1); continue; }
-            int cmp = CMP_SPLIT;
-            // FP32 copies of both pseudo-sources in the candidate's frame (conversions in the
-            // FP64 form; the margins of the FP32 tests cover their rounding)
-            const float fcx = (float)fsx(c), fcy = (float)fsy(c), fcs = (float)fsig(c);
-            const float fox = same ? (float)fsx(o) : (float)Lr - (float)fsx(o);
-            const float foy = same ? (float)fsy(o) : -(float)fsy(o);
-            const float fos = (float)fsig(o);
-            const bool eq_sig = __double_as_longlong(c.sig) == __double_as_longlong(o.sig);
-            if (same && same_family<R>(c, o)) cmp = CMP_EXISTING;   // equal everywhere: ties stay
-            else if (!eq_sig) cmp = dominance_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi);
-            // equal sigma: the exact bisector split below is cheaper than any FP32 attempt
-            if (cmp == CMP_EXISTING) { ivl_add<R>(npc, a0, lo); ivl_add<R>(npc, hi, a1); continue; }
-            if (cmp == CMP_CANDIDATE) { ivl_add<R>(npc, a0, a1); ivl_add<R>(lost, lo, hi, false); continue; }
-            // split of the overlap at the equal-distance points: FP32 with rigorous margins
-            // where it can decide, else exact
-            R bq[4];
-            bool cw[3];
-            int npz = 0;
-            bool done32 = false;
-            if (sizeof(R) == sizeof(float) && !eq_sig) {
-                float bpf[4];
-                done32 = split_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi, bpf, cw, npz);
-                if (done32) { bq[0] = (R)bpf[0]; bq[1] = (R)bpf[1]; bq[2] = (R)bpf[2]; bq[3] = (R)bpf[3]; }
+        for (int k = 0; k < WALK_K; ++k) ids[k] = -1;
+        int n = 0;
+        const R h0 = pc.n > 0 ? ivl_get<R>(pc.a, 0) : (R)0, h1 = pc.n > 0 ? ivl_get<R>(pc.b, pc.n - 1) : (R)0;
+        if (has && pc.n > 0) {
+            // windows split by the last comparisons sit between prev and cursor
+            if (prev >= 0) {
+                int x = ws.win[prev].next;
+                while (x >= 0 && x != cursor && guard <= ws.wcap) { prev = x; x = ws.win[x].next; ++guard; }
             }
-            if (!done32) {
-                const double osx = same ? o.sx : Ld - o.sx, osy = same ? o.sy : -o.sy;
-                double bp[4];
-                npz = split_exact(c.sx, c.sy, c.sig, osx, osy, o.sig, (double)lo, (double)hi,
-                                  c_direct && (o.flags & WIN_FIXED), bp, cw);
-                bq[0] = (R)bp[0]; bq[1] = (R)bp[1]; bq[2] = (R)bp[2]; bq[3] = (R)bp[3];
-            }
-            ivl_add<R>(npc, a0, lo);
-#pragma unroll 1
-            for (int q = 0; q < npz; ++q)
-                if (cw[q]) {
-                    ivl_add<R>(npc, bq[q], bq[q + 1]);
-                    ivl_add<R>(lost, bq[q], bq[q + 1], false);
+            while (cursor >= 0 && n < WALK_K) {
+                if (++guard > ws.wcap) { err |= css::ST_ITER_LIMIT; cursor = -1; break; }
+                const Win<R> o = ws.win[cursor];
+                if (!(o.flags & WIN_ALIVE)) {                 // unlink dead windows
+                    if (prev < 0) ws.ehead[es] = o.next; else ws.win[prev].next = o.next;
+                    cursor = o.next;
+                    continue;
                 }
-            ivl_add<R>(npc, hi, a1);
-        }
-        pc.n = 0;
-#pragma unroll 1
-        for (int p = 0; p < npc.n; ++p) {
-            const R x0 = ivl_get<R>(npc.a, p), x1 = ivl_get<R>(npc.b, p);
-            if (x1 - x0 > tolw) {
-                ivl_set<R>(pc.a, pc.n, x0);
-                ivl_set<R>(pc.b, pc.n, x1);
-                ++pc.n;
+                const bool same = (o.he == c.he);
+                const R o0 = same ? o.b0 : Lr - o.b1, o1 = same ? o.b1 : Lr - o.b0;
+                const R lo = h0 > o0 ? h0 : o0, hi = h1 < o1 ? h1 : o1;
+                if (hi - lo > tolw) { reg_set(ids, n, cursor); ++n; }
+                prev = cursor;
+                cursor = o.next;
             }
         }
-        if (lost.n > 0) {
-            Ivl<R> keep;
-            keep.n = 0;
+        // ---- the pairs of all lanes, dense in lane order
+        int incl = n;
 #pragma unroll
-            for (int k = 0; k < MAXP; ++k) { keep.a[k] = keep.b[k] = (R)0; }
-            R cur = o0;
-#pragma unroll 1
-            for (int q = 0; q < lost.n; ++q) {
-                const R l0 = ivl_get<R>(lost.a, q), l1 = ivl_get<R>(lost.b, q);
-                if (l0 - cur > tolw) ivl_add<R>(keep, cur, l0);
-                if (l1 > cur) cur = l1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(CSS_FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(CSS_FULL, incl, 31);
+        const int excl = incl - n;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int v = __shfl_sync(CSS_FULL, incl, owner + step - 1);
+                if (v <= t) owner += step;
             }
-            if (o1 - cur > tolw) ivl_add<R>(keep, cur, o1);
-            if (keep.n == 0) {
-                ws.win[oi].flags = o.flags & ~WIN_ALIVE;
-                if (prev < 0) ws.ehead[es] = onext; else ws.win[prev].next = onext;
-                oi = onext;
-                continue;
+            owner = min(owner, 31);
+            const int j = t - __shfl_sync(CSS_FULL, excl, owner);
+            int oi = -1;
+#pragma unroll
+            for (int k = 0; k < WALK_K; ++k) {
+                const int v = __shfl_sync(CSS_FULL, ids[k], owner);
+                if (k == j) oi = v;
             }
-            int tail = oi;
-            const R wpad = (R)Widen<R>::mu * Lr;   // outward rounding of the kept parts
+            const double csx = __shfl_sync(CSS_FULL, c.sx, owner), csy = __shfl_sync(CSS_FULL, c.sy, owner);
+            const double csig = __shfl_sync(CSS_FULL, c.sig, owner);
+            const int che = __shfl_sync(CSS_FULL, c.he, owner), cfl = __shfl_sync(CSS_FULL, c.flags, owner);
+            const R ch0 = __shfl_sync(CSS_FULL, h0, owner), ch1 = __shfl_sync(CSS_FULL, h1, owner);
+            const R cL = __shfl_sync(CSS_FULL, Lr, owner), ctol = __shfl_sync(CSS_FULL, tolw, owner);
+            Ivl<R> cl;
+            cl.n = 0;
+#pragma unroll
+            for (int k = 0; k < MAXP; ++k) { cl.a[k] = cl.b[k] = (R)0; }
+            if (t < total && oi >= 0) compare_pair<R>(ws, sm, oi, csx, csy, csig, che, cfl, ch0, ch1, cL, ctol, cl);
+            // each lane takes back its pairs' losses from the lanes that compared them (a
+            // comparison's loss is at most two pieces: the winners of its sub-intervals
+            // alternate once the touching ones are merged)
 #pragma unroll 1
-            for (int q = 0; q < keep.n; ++q) {
-                const R ka = ivl_get<R>(keep.a, q), kb = ivl_get<R>(keep.b, q);
-                R k0 = (same ? ka : Lr - kb) - wpad;
-                R k1 = (same ? kb : Lr - ka) + wpad;
-                k0 = k0 < (R)0 ? (R)0 : k0;
-                k1 = k1 > Lr ? Lr : k1;
-                if (q == 0) { ws.win[oi].b0 = k0; ws.win[oi].b1 = k1; }
-                else {
-                    const int pid = win_alloc<R>(sm, ws.wcap);
-                    if (pid < 0) break;
-                    Win<R> piece = o;
-                    piece.b0 = k0; piece.b1 = k1;
-                    piece.next = onext;
-                    ws.win[pid] = piece;
-                    if (!(o.flags & WIN_DONE)) push_pending<R>(ws, sm, pid, (float)win_key<R>(piece));
-                    ws.win[tail].next = pid;          // keep the list order, skip the pieces
-                    tail = pid;
+            for (int k = 0; k < WALK_K; ++k) {
+                const int src = excl + k - t0;
+                const bool in = k < n && src >= 0 && src < 32;
+                const int s = in ? src : lane;
+                const int nl = __shfl_sync(CSS_FULL, cl.n, s);
+#pragma unroll 1
+                for (int r = 0; r < 2; ++r) {
+                    const R x0 = __shfl_sync(CSS_FULL, ivl_get<R>(cl.a, r), s);
+                    const R x1 = __shfl_sync(CSS_FULL, ivl_get<R>(cl.b, r), s);
+                    if (in && r < nl) ivl_sub<R>(pc, x0, x1, tolw);
                 }
             }
-            prev = tail;
-        } else {
-            prev = oi;
         }
-        oi = onext;
+        __syncwarp();
     }
     if (err) atomicOr(&sm.err, err);
     bool added = false;
@@ -975,7 +1087,6 @@ __device__ __noinline__ void insert_window_general(const DMesh& m, Ws<R, SH>& ws
         Win<R> w = c;
         w.b0 = ivl_get<R>(pc.a, p);
         w.b1 = ivl_get<R>(pc.b, p);
-        w.flags = (c.flags & WIN_FIXED) | WIN_ALIVE;
         if (!((double)win_key<R>(w) < rc)) continue;
         const int id = win_alloc<R>(sm, ws.wcap);
         if (id < 0) break;
@@ -1069,7 +1180,7 @@ __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& 
     int rank;
     const int rounds = group_rounds(has, slot, lane, rank);
     for (int q = 0; q < rounds; ++q) {
-        if (has && rank == q) insert_window<R>(m, ws, sm, slot, c, rc);
+        insert_round<R>(m, ws, sm, has && rank == q, slot, c, rc, lane);
         __syncwarp();
     }
 }
