@@ -1692,9 +1692,40 @@ __device__ __forceinline__ void eval_face_block(const cssi::GeoJob& J, int i, co
     }
 }
 
+// Inclusive prefix sum of x over the warp.
+__device__ __forceinline__ int warp_incl_scan(int x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(CSS_FULL, x, o);
+        if (lane >= o) x += t;
+    }
+    return x;
+}
+
+// The lane whose inclusive-scan range holds item t (31 for t beyond the total).
+__device__ __forceinline__ int scan_owner(int incl, int t) {
+    int owner = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int v = __shfl_sync(CSS_FULL, incl, owner + step - 1);
+        if (v <= t) owner += step;
+    }
+    return min(owner, 31);
+}
+
+// Per-warp staging (shared memory) of a wave's vertex candidates and then of its children,
+// so that each round takes 32 of them whatever lane produced them; the two phases use the
+// buffer in turn.
+template <class R>
+union WaveStage {
+    VCand<R, false> vc[3][32];
+    Win<R> ch[2][32];
+};
+
 template <class R, int SH>
-__device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, int lane, int* status,
-                           unsigned long long* counters, int item, int32_t* defer_list, int* defer_count) {
+__device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, WaveStage<R>* stg, int lane,
+                           int* status, unsigned long long* counters, int item, int32_t* defer_list,
+                           int* defer_count) {
     const DMesh& m = J.m;
     const double rc = J.rc;
     const int f0 = J.face[i];
@@ -1731,10 +1762,50 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
         __syncwarp();
         // one call site per round kind keeps the kernel's instruction footprint small
         // (divergent insertion code otherwise thrashes the instruction cache)
+        if constexpr (SH == 2) {   // the path kernel: one round per candidate slot
 #pragma unroll 1
-        for (int q = 0; q < 3; ++q) vertex_round<R>(m, ws, sm, q < nvc, q == 0 ? vc[0] : (q == 1 ? vc[1] : vc[2]), rc, lane);
+            for (int q = 0; q < 3; ++q)
+                vertex_round<R>(m, ws, sm, q < nvc, q == 0 ? vc[0] : (q == 1 ? vc[1] : vc[2]), rc, lane);
 #pragma unroll 1
-        for (int q = 0; q < 2; ++q) child_round<R>(m, ws, sm, q < nch, q == 0 ? ch[0] : ch[1], rc, lane);
+            for (int q = 0; q < 2; ++q) child_round<R>(m, ws, sm, q < nch, q == 0 ? ch[0] : ch[1], rc, lane);
+        } else {
+            // the wave's vertex candidates (up to three a lane), 32 to a round
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (q < nvc) stg->vc[q][lane] = vc[q];
+            __syncwarp();
+            const int vi = warp_incl_scan(nvc, lane);
+            const int vt = __shfl_sync(CSS_FULL, vi, 31);
+#pragma unroll 1
+            for (int base = 0; base < vt; base += 32) {
+                const int t = base + lane;
+                const int owner = scan_owner(vi, t);
+                const int slot = t - (__shfl_sync(CSS_FULL, vi, owner) - __shfl_sync(CSS_FULL, nvc, owner));
+                VCand<R, false> c;
+                const bool has = t < vt;
+                if (has) c = stg->vc[slot][owner];
+                vertex_round<R>(m, ws, sm, has, c, rc, lane);
+            }
+            __syncwarp();
+            // then its children (up to two a lane), 32 to a round
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (q < nch) stg->ch[q][lane] = ch[q];
+            __syncwarp();
+            const int ci = warp_incl_scan(nch, lane);
+            const int ct = __shfl_sync(CSS_FULL, ci, 31);
+#pragma unroll 1
+            for (int base = 0; base < ct; base += 32) {
+                const int t = base + lane;
+                const int owner = scan_owner(ci, t);
+                const int slot = t - (__shfl_sync(CSS_FULL, ci, owner) - __shfl_sync(CSS_FULL, nch, owner));
+                Win<R> c;
+                const bool has = t < ct;
+                if (has) c = stg->ch[slot][owner];
+                child_round<R>(m, ws, sm, has, c, rc, lane);
+            }
+            __syncwarp();
+        }
     }
     __syncwarp();
     const int err = sm.err;
@@ -2098,6 +2169,11 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic(const __grid_constant__ c
         ws = ws_bind<R, SH>(g, gw);
         if constexpr (SH == 1) ws_bind_shared<R, SH>(ws, dsm + (size_t)wib * sh_bytes_per_warp<R>(g.shared), g.shared);
     }
+    // the wave staging buffers follow the CTA's tables
+    WaveStage<R>* stg = nullptr;
+    if constexpr (SH != 2)
+        stg = reinterpret_cast<WaveStage<R>*>(
+                  dsm + (SH == 1 ? (size_t)(blockDim.x >> 5) * sh_bytes_per_warp<R>(g.shared) : 0)) + wib;
     __syncwarp();
     uint32_t gen = 0;
     if (lane == 0) gen = g.gen[gw];
@@ -2122,7 +2198,7 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic(const __grid_constant__ c
             __syncwarp();
             if (lane == 0) ws.gen = gen;
             __syncwarp();
-            run_source<R>(J, src, ws, sm, lane, status, counters, item, q.defer_list, q.defer_count);
+            run_source<R>(J, src, ws, sm, stg, lane, status, counters, item, q.defer_list, q.defer_count);
         }
     }
     if (lane == 0) g.gen[gw] = gen;
@@ -2176,9 +2252,11 @@ size_t geo_ws_bytes_per_warp(int precision, int win_cap, int tab_cap, int* log_e
 }
 
 size_t geodesic_shared_bytes(int precision, int warps_per_cta, int shared_scale) {
-    if (!shared_scale) return 0;
-    return (size_t)warps_per_cta * (precision == CSS_FP32 ? sh_bytes_per_warp<float>(shared_scale)
-                                                          : sh_bytes_per_warp<double>(shared_scale));
+    const bool f32 = precision == CSS_FP32;
+    const size_t stage = f32 ? sizeof(WaveStage<float>) : sizeof(WaveStage<double>);
+    const size_t tables = !shared_scale ? 0 : (f32 ? sh_bytes_per_warp<float>(shared_scale)
+                                                   : sh_bytes_per_warp<double>(shared_scale));
+    return (size_t)warps_per_cta * (tables + stage);
 }
 
 cudaError_t launch_geodesic(const GeoJob& job0, const GeoJob* djobs, const GeoQueue& q, int precision,
