@@ -703,56 +703,6 @@ __device__ __forceinline__ int dominance_f32(float csx, float csy, float csig, f
     return ub < -E ? CMP_CANDIDATE : CMP_SPLIT;
 }
 
-// FP32 location of the equal-distance points of two windows on the overlap (coordinates
-// centred on the overlap to keep the squared terms small) and the winner of each piece,
-// each confirmed by an evaluated distance difference beyond the rounding margin.  Returns
-// false when some piece cannot be decided in FP32 (then the FP64 split is used).
-__device__ __forceinline__ bool split_f32(float csx, float csy, float csig, float osx, float osy, float osig, float lo,
-                                          float hi, float* bp, bool* cwin, int& npieces) {
-    const float xm = 0.5f * (lo + hi);
-    const float ax = csx - xm, bx = osx - xm, l0 = lo - xm, h0 = hi - xm;
-    const float del = osig - csig;
-    const float al = bx - ax;
-    const float be = (ax * ax + csy * csy) - (bx * bx + osy * osy) - del * del;
-    const float c2 = del * del - al * al;
-    const float c1 = -(2.f * del * del * bx + al * be);
-    const float c0 = del * del * (bx * bx + osy * osy) - 0.25f * be * be;
-    float r[2];
-    int nc = 0;
-    const float scale = fabsf(c2) + fabsf(c1) / (fabsf(h0) + fabsf(l0) + 1e-30f) + 1e-30f;
-    if (fabsf(c2) <= 1e-6f * scale) {
-        if (c1 != 0.f) r[nc++] = -c0 / c1;
-    } else {
-        float disc = c1 * c1 - 4.f * c2 * c0;
-        if (disc < 0.f) disc = 0.f;
-        const float sq = sqrtf(disc);
-        const float qq = -0.5f * (c1 + (c1 >= 0.f ? sq : -sq));
-        if (qq != 0.f) { r[nc++] = qq / c2; r[nc++] = c0 / qq; }
-        else r[nc++] = -c1 / (2.f * c2);
-    }
-    bp[0] = lo;
-    int nb = 1;
-    float ra = 2.f * hi, rb = 2.f * hi;   // sorted roots inside (lo, hi)
-    if (nc > 0 && r[0] + xm > lo && r[0] + xm < hi) ra = r[0] + xm;
-    if (nc > 1 && r[1] + xm > lo && r[1] + xm < hi) { const float t = r[1] + xm; if (t < ra) { rb = ra; ra = t; } else rb = t; }
-    if (ra < hi) bp[nb++] = ra;
-    if (rb < hi) bp[nb++] = rb;
-    bp[nb] = hi;
-    npieces = nb;
-    const float E = 4.8e-7f * (fabsf(csx) + fabsf(csy) + fabsf(osx) + fabsf(osy) + 2.f * (fabsf(lo) + fabsf(hi)) + csig + osig) +
-                    1e-30f;
-#pragma unroll 1
-    for (int q = 0; q < 3; ++q) {
-        if (q >= nb) break;
-        const float x = 0.5f * (bp[q] + bp[q + 1]);
-        const float dc = csig + sqrtf((x - csx) * (x - csx) + csy * csy);
-        const float dd = dc - (osig + sqrtf((x - osx) * (x - osx) + osy * osy));
-        if (!(fabsf(dd) > E + 4.8e-7f * 2.f * dc)) return false;
-        cwin[q] = dd < 0.f;
-    }
-    return true;
-}
-
 // Exact split of an overlap [lo, hi] between candidate (a, sa) and existing (b, sb): the
 // equal-distance points in FP64, the winner of each piece decided in FP32 when the evaluated
 // difference clears its rounding margin, else in FP64 with the exact tie rule (a direct
@@ -922,25 +872,16 @@ __device__ __forceinline__ void compare_pair(Ws<R, SH>& ws, WarpSm& sm, int oi, 
     if (cmp == CMP_EXISTING) ivl_add<R>(cl, lo, hi, false);
     else if (cmp == CMP_CANDIDATE) ivl_add<R>(lost, lo, hi, false);
     else {
-        // split of the overlap at the equal-distance points: FP32 with rigorous margins
-        // where it can decide, else exact
+        // split of the overlap at the equal-distance points (FP64 roots in both forms; an
+        // FP32 attempt with rigorous margins decided too few splits to pay for its code)
         R bq[4];
         bool cw[3];
-        int npz = 0;
-        bool done32 = false;
-        if (sizeof(R) == sizeof(float) && !eq_sig) {
-            float bpf[4];
-            done32 = split_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi, bpf, cw, npz);
-            if (done32) { bq[0] = (R)bpf[0]; bq[1] = (R)bpf[1]; bq[2] = (R)bpf[2]; bq[3] = (R)bpf[3]; }
-        }
-        if (!done32) {
-            const double Ld = (double)Lr;
-            const double osx = same ? o.sx : Ld - o.sx, osy = same ? o.sy : -o.sy;
-            double bp[4];
-            npz = split_exact(csx, csy, csig, osx, osy, o.sig, (double)lo, (double)hi,
-                              c_direct && (o.flags & WIN_FIXED), bp, cw);
-            bq[0] = (R)bp[0]; bq[1] = (R)bp[1]; bq[2] = (R)bp[2]; bq[3] = (R)bp[3];
-        }
+        const double Ld = (double)Lr;
+        const double osx = same ? o.sx : Ld - o.sx, osy = same ? o.sy : -o.sy;
+        double bp[4];
+        const int npz = split_exact(csx, csy, csig, osx, osy, o.sig, (double)lo, (double)hi,
+                                    c_direct && (o.flags & WIN_FIXED), bp, cw);
+        bq[0] = (R)bp[0]; bq[1] = (R)bp[1]; bq[2] = (R)bp[2]; bq[3] = (R)bp[3];
 #pragma unroll 1
         for (int q = 0; q < npz; ++q) {
             if (cw[q]) ivl_add<R>(lost, bq[q], bq[q + 1], false);
