@@ -867,8 +867,10 @@ __device__ __forceinline__ void compare_pair(Ws<R, SH>& ws, WarpSm& sm, int oi, 
     if (same && eq_sig && __double_as_longlong(csx) == __double_as_longlong(o.sx) &&
         __double_as_longlong(csy) == __double_as_longlong(o.sy))
         cmp = CMP_EXISTING;   // the same path family: equal everywhere, ties stay
-    else if (!eq_sig) cmp = dominance_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi);
+    // the FP32 dominance test (FP64 form only: in the FP32 form it decided too few overlaps to
+    // pay for itself on the cutoff workloads, and every overlap goes to the exact split);
     // equal sigma: the exact bisector split below is cheaper than any FP32 attempt
+    else if (sizeof(R) == sizeof(double) && !eq_sig) cmp = dominance_f32(fcx, fcy, fcs, fox, foy, fos, (float)lo, (float)hi);
     if (cmp == CMP_EXISTING) ivl_add<R>(cl, lo, hi, false);
     else if (cmp == CMP_CANDIDATE) ivl_add<R>(lost, lo, hi, false);
     else {
