@@ -244,8 +244,9 @@ int css_geodesic_paths(css_parts* parts, double r_c, int64_t n_pairs, const int3
  *                          source face's x-axis): H = Y / |Y| is that axis transported;
  *   L phi = -div(-grad u / |grad u|)   (right-hand side made mean-free), phi(q) = 0;
  * then l_ij = phi(x_j) (linear interpolation) and t_ij = the source face's x-axis turned by the
- * angle of grad phi against H at x_j.  The heat steps are solved by Jacobi sweeps (damped
- * where obtuse triangles make cotan weights negative) until no entry changes by more than
+ * angle of grad phi against H at x_j.  The heat steps are solved by Gauss-Seidel sweeps over
+ * a colouring of the vertex graph (convergent on any mesh: the systems are symmetric positive
+ * definite) until no entry changes by more than
  * 1e-14 of the terms it is summed from (entries below 1e-290, i.e. farther than about
  * 660 sqrt(t) from the source, have no relative accuracy left), the Poisson step by
  * conjugate gradients to 1e-14 of the preconditioned residual.  t_factor > 0 (1: t = h^2).

@@ -19,10 +19,12 @@
 //
 // GPU organisation: K sources at a time (K a power of two <= 256), fields vertex-major
 // with the K sources contiguous, thread (v, s) at v K + s, so the K threads of a row share
-// the row's operator entries.  The heat systems are solved by Jacobi sweeps: the scalar
-// matrix is an M-matrix, every sweep adds non-negative terms, and the solution keeps its
-// relative accuracy where it is tiny far from the source (a Krylov solver's residual norm
-// would not); the sweeps stop when no entry changes by more than 1e-14 of itself.  The
+// the row's operator entries.  The heat systems are solved by Gauss-Seidel sweeps over a
+// colouring of the vertex graph (one launch per colour): the matrices are symmetric positive
+// definite, so the sweeps converge on any mesh; where the scalar matrix is an M-matrix every
+// sweep adds non-negative terms, and the solution keeps its relative accuracy where it is
+// tiny far from the source (a Krylov solver's residual norm would not); the sweeps stop when
+// no entry changes by more than 1e-14 of the terms it is summed from.  The
 // Poisson system is solved by Jacobi-preconditioned conjugate gradients, one column per
 // source, with per-source reductions in a fixed order (the result does not depend on
 // thread timing).
@@ -199,17 +201,6 @@ __global__ void k_heat_rhs(Op o, int K, int nsrc, const int32_t* src, const int3
     bY[2 * a + 1] = b * sin(psi);
 }
 
-// Gershgorin radius of the Jacobi-scaled heat matrix at each vertex, t sum |w| / (m + t sum w),
-// maximised over the vertices (non-negative doubles order like their bit patterns)
-__global__ void k_gersh(Op o, double t, unsigned long long* gmax) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= o.nv) return;
-    double a = 0.0;
-    for (int e = 2 * o.ring_start[v]; e < 2 * o.ring_start[v + 1]; ++e) a += fabs(o.ew[e]);
-    const double g = t * a / (o.mass[v] + t * o.diag[v]);
-    atomicMax(gmax, (unsigned long long)__double_as_longlong(g));
-}
-
 // per call: the heat step's entries scaled by t (weight, and weight times the transport turn)
 // and the inverse diagonal, so a sweep spends five FP64 operations per entry
 __global__ void k_heat_entries(Op o, double t, double* wt, double* wc, double* wsn, double* inv_d) {
@@ -223,23 +214,28 @@ __global__ void k_heat_entries(Op o, double t, double* wt, double* wc, double* w
     if (e < o.nv) inv_d[e] = 1.0 / (o.mass[e] + t * o.diag[e]);
 }
 
-// One (damped) Jacobi sweep of both heat systems, x <- x + omega (D^-1 (b + t W x) - x).
-// With all weights positive (an M-matrix) omega = 1 and every term is non-negative; an
-// obtuse mesh has negative cotan weights, and omega < 2 / (1 + max Gershgorin radius) keeps
-// the sweeps convergent.  With check, entries that still change by more than 1e-14 of the
-// magnitude of the terms they are summed from raise *flag (an entry the sweeps have not
-// reached is 0 and changes when they do, so the flag stays up until every vertex has been
-// reached; below 1e-290 an entry has no relative accuracy left to converge to).
-__global__ void __launch_bounds__(VT) k_heat_sweep(Op o, int K, int nsrc, const double* wt, const double* wc,
-                                                   const double* wsn, const double* inv_d, double omega,
-                                                   const double* bu, const double* bY, const double* u, const double* Y,
-                                                   double* un, double* Yn, int check, int* flag) {
+// One colour of a Gauss-Seidel sweep of both heat systems, in place: every vertex of the
+// colour takes x_v <- D_v^-1 (b_v + t sum_j w_vj x_j) from its neighbours' current values (no
+// two vertices of a colour are neighbours, so the order within a colour does not matter).
+// (M + t L) is symmetric positive definite for any mesh (L is the Dirichlet form of the
+// piecewise-linear interpolant, the connection Laplacian that of the transported field), so
+// the sweeps converge without damping; with all weights positive every term is
+// non-negative, which keeps far-field entries relatively accurate.  With check, entries
+// that still change by more than 1e-14 of the magnitude of the terms they are summed from
+// raise *flag (an entry the sweeps have not reached is 0 and changes when they do, so the
+// flag stays up until every vertex has been reached; below 1e-290 an entry has no relative
+// accuracy left to converge to).
+__global__ void __launch_bounds__(VT) k_heat_gs(Op o, int K, int nsrc, const double* wt, const double* wc,
+                                                const double* wsn, const double* inv_d, const int32_t* verts,
+                                                int nverts, const double* bu, const double* bY, double* u, double* Y,
+                                                int check, int* flag) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool moved = false;
     const int s = (int)(g % K);
-    if (g < (int64_t)o.nv * K && s < nsrc) {   // columns beyond the batch's sources stay 0
-        const int v = (int)(g / K);
-        double au = bu[g], ar = bY[2 * g], ai = bY[2 * g + 1];
+    if (g < (int64_t)nverts * K && s < nsrc) {   // columns beyond the batch's sources stay 0
+        const int v = verts[g / K];
+        const size_t a = (size_t)v * K + s;
+        double au = bu[a], ar = bY[2 * a], ai = bY[2 * a + 1];
         double su = 0.0, sy = 0.0;   // magnitudes of the summed terms (for the check only)
         for (int e = 2 * o.ring_start[v]; e < 2 * o.ring_start[v + 1]; ++e) {
             const size_t j = (size_t)o.ej[e] * K + s;
@@ -254,22 +250,20 @@ __global__ void __launch_bounds__(VT) k_heat_sweep(Op o, int K, int nsrc, const 
             }
         }
         if (check) {
-            su += fabs(bu[g]);
-            sy += sqrt(bY[2 * g] * bY[2 * g] + bY[2 * g + 1] * bY[2 * g + 1]);
+            su += fabs(bu[a]);
+            sy += sqrt(bY[2 * a] * bY[2 * a] + bY[2 * a + 1] * bY[2 * a + 1]);
         }
         const double iD = inv_d[v];
-        const double u0 = u[g], r0 = Y[2 * g], i0 = Y[2 * g + 1];
-        const double nu = u0 + omega * (au * iD - u0);
-        const double nr = r0 + omega * (ar * iD - r0), ni = i0 + omega * (ai * iD - i0);
+        const double nu = au * iD, nr = ar * iD, ni = ai * iD;
         if (check) {
             const double su_d = su * iD, sy_d = sy * iD;
-            const double dr = nr - r0, di = ni - i0;
-            moved = (su_d > 1e-290 && fabs(nu - u0) > 1e-14 * su_d) ||
+            const double dr = nr - Y[2 * a], di = ni - Y[2 * a + 1];
+            moved = (su_d > 1e-290 && fabs(nu - u[a]) > 1e-14 * su_d) ||
                     (sy_d > 1e-290 && sqrt(dr * dr + di * di) > 1e-14 * sy_d);
         }
-        un[g] = nu;
-        Yn[2 * g] = nr;
-        Yn[2 * g + 1] = ni;
+        u[a] = nu;
+        Y[2 * a] = nr;
+        Y[2 * a + 1] = ni;
     }
     if (check && __any_sync(CSS_FULL, moved) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
@@ -540,6 +534,8 @@ struct VhmOp {
     double *ang = nullptr, *cot = nullptr, *gam = nullptr, *area = nullptr, *mass = nullptr, *diag = nullptr,
            *scale = nullptr, *phi = nullptr, *ew = nullptr, *ec = nullptr, *es = nullptr;
     int32_t *pos = nullptr, *ej = nullptr;
+    int32_t* cverts = nullptr;        // vertices grouped by colour (no two neighbours share one)
+    std::vector<int32_t> cstart;      // colour c is cverts[cstart[c] .. cstart[c + 1])
 };
 
 void vhm_free(css_mesh* m) {
@@ -547,7 +543,7 @@ void vhm_free(css_mesh* m) {
     if (!o) return;
     cudaFree(o->ang); cudaFree(o->cot); cudaFree(o->gam); cudaFree(o->area); cudaFree(o->mass);
     cudaFree(o->diag); cudaFree(o->scale); cudaFree(o->phi); cudaFree(o->ew); cudaFree(o->ec); cudaFree(o->es);
-    cudaFree(o->pos); cudaFree(o->ej);
+    cudaFree(o->pos); cudaFree(o->ej); cudaFree(o->cverts);
     delete o;
     m->vhm = nullptr;
 }
@@ -618,6 +614,44 @@ int build_op(css_mesh* m) {
         c->err = "vhm: a vertex's faces do not form one disk or half-disk";
         return CSS_ERR_NONMANIFOLD;
     }
+    // greedy colouring of the vertex graph (each vertex takes the smallest colour none of its
+    // already coloured neighbours has), for the Gauss-Seidel sweeps
+    std::vector<int32_t> rs((size_t)nv + 1), ej((size_t)6 * nf);
+    e = cudaMemcpyAsync(rs.data(), m->ring_start, rs.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ej.data(), o->ej, ej.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cssi::vhm_free(m);
+        c->err = std::string("vhm operators: ") + cudaGetErrorString(e);
+        return CSS_ERR_CUDA;
+    }
+    std::vector<int32_t> col((size_t)nv, -1);
+    std::vector<char> used;
+    int ncol = 0;
+    for (int32_t v = 0; v < nv; ++v) {
+        used.assign((size_t)ncol + 1, 0);
+        for (int32_t k = 2 * rs[v]; k < 2 * rs[v + 1]; ++k) {
+            const int32_t j = ej[k];
+            if (j != v && col[j] >= 0) used[col[j]] = 1;
+        }
+        int cv = 0;
+        while (used[cv]) ++cv;
+        col[v] = cv;
+        ncol = std::max(ncol, cv + 1);
+    }
+    o->cstart.assign((size_t)ncol + 1, 0);
+    for (int32_t v = 0; v < nv; ++v) ++o->cstart[col[v] + 1];
+    for (int cc = 0; cc < ncol; ++cc) o->cstart[cc + 1] += o->cstart[cc];
+    std::vector<int32_t> order((size_t)nv), fill(o->cstart.begin(), o->cstart.end() - 1);
+    for (int32_t v = 0; v < nv; ++v) order[fill[col[v]]++] = v;
+    e = cudaMalloc(&o->cverts, std::max<size_t>(nv, 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(o->cverts, order.data(), (size_t)nv * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cssi::vhm_free(m);
+        c->err = std::string("vhm operators: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? CSS_ERR_OOM : CSS_ERR_CUDA;
+    }
     return CSS_OK;
 }
 
@@ -628,10 +662,20 @@ bool dev_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// an executable graph, destroyed with its owner
+struct GraphExec {
+    cudaGraphExec_t exec = nullptr;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+    }
+    ~GraphExec() { reset(); }
+};
+
 // device buffers of one batch of K columns
 struct Batch {
     std::vector<void*> owned;
-    double *u = nullptr, *u2 = nullptr, *Y = nullptr, *Y2 = nullptr, *bu = nullptr, *bY = nullptr, *X = nullptr,
+    double *u = nullptr, *Y = nullptr, *bu = nullptr, *bY = nullptr, *X = nullptr,
            *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *partial = nullptr,
            *sc = nullptr, *od = nullptr, *ot = nullptr, *pj_d = nullptr, *pj_t = nullptr, *wt = nullptr, *wc = nullptr,
            *wsn = nullptr, *invd = nullptr;
@@ -672,8 +716,8 @@ int css_vhm_neighbors(css_parts* parts, double r_c, double t_factor, int64_t cap
     Batch B;
     const size_t VK = (size_t)nv * K;
     const int nbv = (int)vblk((int64_t)VK);
-    VTRY("vhm", B.get(&B.u, VK)); VTRY("vhm", B.get(&B.u2, VK)); VTRY("vhm", B.get(&B.Y, 2 * VK));
-    VTRY("vhm", B.get(&B.Y2, 2 * VK)); VTRY("vhm", B.get(&B.bu, VK)); VTRY("vhm", B.get(&B.bY, 2 * VK));
+    VTRY("vhm", B.get(&B.u, VK)); VTRY("vhm", B.get(&B.Y, 2 * VK));
+    VTRY("vhm", B.get(&B.bu, VK)); VTRY("vhm", B.get(&B.bY, 2 * VK));
     VTRY("vhm", B.get(&B.X, 2 * (size_t)nf * K)); VTRY("vhm", B.get(&B.b, VK)); VTRY("vhm", B.get(&B.x, VK));
     VTRY("vhm", B.get(&B.r, VK)); VTRY("vhm", B.get(&B.z, VK)); VTRY("vhm", B.get(&B.p, VK));
     VTRY("vhm", B.get(&B.q, VK)); VTRY("vhm", B.get(&B.partial, (size_t)nbv * K));
@@ -701,45 +745,48 @@ int css_vhm_neighbors(css_parts* parts, double r_c, double t_factor, int64_t cap
     std::vector<int64_t> rows((size_t)n + 1, 0);
     int64_t total = 0;
     int64_t iters_heat = 0, iters_cg = 0;
-    double omega = 1.0;
     const int MAX_SWEEPS = 50000, MAX_CG = 50000, CHUNK = 16;
+    GraphExec chunk;
+    int chunk_ns = -1;
     for (int s0 = 0; s0 < n; s0 += K) {
         const int ns = std::min(K, n - s0);
         std::vector<int32_t> hsrc(K);
         for (int s = 0; s < K; ++s) hsrc[s] = s0 + std::min(s, ns - 1);
         VTRY("vhm", cudaMemcpyAsync(B.src, hsrc.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        // ---- heat steps (Jacobi sweeps from zero)
+        // ---- heat steps (Gauss-Seidel sweeps from zero, colour by colour)
         VTRY("vhm", cudaMemsetAsync(B.bu, 0, VK * sizeof(double), st));
         VTRY("vhm", cudaMemsetAsync(B.bY, 0, 2 * VK * sizeof(double), st));
         VTRY("vhm", cudaMemsetAsync(B.u, 0, VK * sizeof(double), st));
         VTRY("vhm", cudaMemsetAsync(B.Y, 0, 2 * VK * sizeof(double), st));
-        VTRY("vhm", cudaMemsetAsync(B.u2, 0, VK * sizeof(double), st));      // columns past the batch's
-        VTRY("vhm", cudaMemsetAsync(B.Y2, 0, 2 * VK * sizeof(double), st));  // sources stay 0 in both
         k_heat_rhs<<<vblk(3 * ns), VT, 0, st>>>(op, K, ns, B.src, parts->face, parts->bary, B.bu, B.bY);
         VTRY("vhm heat", cudaGetLastError());
-        double *u = B.u, *un = B.u2, *Y = B.Y, *Yn = B.Y2;
+        double *u = B.u, *Y = B.Y;
         int sweeps = 0;
-        if (s0 == 0) {   // damping of the sweeps from the Gershgorin bound (once per call)
-            unsigned long long* dg = (unsigned long long*)B.cnt;
-            unsigned long long hg = 0;
-            VTRY("vhm heat", cudaMemsetAsync(dg, 0, sizeof(unsigned long long), st));
-            k_gersh<<<vblk(nv), VT, 0, st>>>(op, t, dg);
-            VTRY("vhm heat", cudaGetLastError());
-            VTRY("vhm heat", cudaMemcpyAsync(&hg, dg, sizeof(hg), cudaMemcpyDeviceToHost, st));
-            VTRY("vhm heat", cudaStreamSynchronize(st));
-            double gmax = 0.0;
-            memcpy(&gmax, &hg, sizeof(double));
-            omega = gmax < 1.0 ? 1.0 : 1.9 / (1.0 + gmax);
+        // a chunk of sweeps (one launch per colour and sweep) is captured once as a graph and
+        // replayed: on small meshes the launches, not the sweeps, would set the time
+        if (!chunk.exec || chunk_ns != ns) {
+            chunk.reset();
+            cudaGraph_t graph = nullptr;
+            VTRY("vhm capture", cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+            const int ncol = (int)O.cstart.size() - 1;
+            for (int k = 0; k < CHUNK && e == cudaSuccess; ++k)
+                for (int cc = 0; cc < ncol; ++cc) {
+                    const int nvc = O.cstart[cc + 1] - O.cstart[cc];
+                    k_heat_gs<<<vblk((int64_t)nvc * K), VT, 0, st>>>(op, K, ns, B.wt, B.wc, B.wsn, B.invd,
+                                                                      O.cverts + O.cstart[cc], nvc, B.bu, B.bY, u, Y,
+                                                                      k == CHUNK - 1, flag);
+                }
+            if (e == cudaSuccess) e = cudaGetLastError();
+            const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&chunk.exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            VTRY("vhm capture", e);
+            chunk_ns = ns;
         }
         for (;;) {
-            VTRY("vhm heat", cudaMemsetAsync(flag, 0, sizeof(int), st));
-            for (int k = 0; k < CHUNK; ++k) {
-                k_heat_sweep<<<nbv, VT, 0, st>>>(op, K, ns, B.wt, B.wc, B.wsn, B.invd, omega, B.bu, B.bY, u, Y, un, Yn,
-                                                 k == CHUNK - 1, flag);
-                std::swap(u, un);
-                std::swap(Y, Yn);
-            }
-            VTRY("vhm heat", cudaGetLastError());
+            VTRY("vhm heat", cudaGraphLaunch(chunk.exec, st));
             sweeps += CHUNK;
             int hf = 0;
             VTRY("vhm heat", cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
