@@ -1827,8 +1827,12 @@ __host__ __device__ inline size_t team_vcand_off(int shared_scale, int W) {
     return team_child_off<R>(shared_scale) + al16((size_t)64 * W * sizeof(Win<R>));
 }
 template <class R>
+__host__ __device__ inline size_t team_idx_off(int shared_scale, int W) {
+    return team_vcand_off<R>(shared_scale, W) + al16((size_t)96 * W * sizeof(VCand<R, false>));
+}
+template <class R>
 __host__ __device__ inline size_t team_smem_bytes(int shared_scale, int W) {
-    return team_vcand_off<R>(shared_scale, W) + (size_t)96 * W * sizeof(VCand<R, false>);
+    return team_idx_off<R>(shared_scale, W) + (size_t)96 * W * W * sizeof(int);
 }
 
 // The next wave of a team: as select_wave, with up to `cap` windows written to sel[]
@@ -1884,7 +1888,7 @@ __device__ int select_wave_cap(Ws<R, SH>& ws, WarpSm& sm, int npend, float kmin,
 // One source processed by the team of the W warps of this CTA (see the team form above).
 template <class R, int SH>
 __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, TeamSm& tm, Win<R>* cst,
-                                VCand<R, false>* vst, int W, int wid, int lane, int* status,
+                                VCand<R, false>* vst, int* ilist, int W, int wid, int lane, int* status,
                                 unsigned long long* counters, int item, int32_t* defer_list, int* defer_count) {
     const DMesh& m = J.m;
     const double rc = J.rc;
@@ -1955,27 +1959,38 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
             cst[2 * k + q] = c;
         }
         __syncthreads();
-        // each warp takes the staged vertex candidates it owns (vertex id modulo W), in order
+        // each warp lists the staged vertex candidates it owns (vertex id modulo W), in order,
+        // and takes them 32 to a round
+        int nown = 0;
         for (int base = 0; base < 3 * nsel; base += 32) {
             const int s = base + lane;
+            const bool own = s < 3 * nsel && vst[s].v >= 0 && vst[s].v % W == wid;
+            const unsigned om = __ballot_sync(CSS_FULL, own);
+            if (own) ilist[nown + __popc(om & css::lanemask_lt())] = s;
+            nown += __popc(om);
+        }
+        __syncwarp();
+        for (int base = 0; base < nown; base += 32) {
             VCand<R, false> c;
-            bool has = false;
-            if (s < 3 * nsel) {
-                c = vst[s];
-                has = c.v >= 0 && c.v % W == wid;
-            }
+            const bool has = base + lane < nown;
+            if (has) c = vst[ilist[base + lane]];
             vertex_round<R>(m, ws, sm, has, c, rc, lane);
         }
         __syncthreads();
         // and the staged children on the edges it owns (undirected edge id modulo W)
+        nown = 0;
         for (int base = 0; base < 2 * nsel; base += 32) {
             const int s = base + lane;
+            const bool own = s < 2 * nsel && cst[s].he >= 0 && m.edge[cst[s].he] % W == wid;
+            const unsigned om = __ballot_sync(CSS_FULL, own);
+            if (own) ilist[nown + __popc(om & css::lanemask_lt())] = s;
+            nown += __popc(om);
+        }
+        __syncwarp();
+        for (int base = 0; base < nown; base += 32) {
             Win<R> c;
-            bool has = false;
-            if (s < 2 * nsel) {
-                c = cst[s];
-                has = c.he >= 0 && m.edge[c.he] % W == wid;
-            }
+            const bool has = base + lane < nown;
+            if (has) c = cst[ilist[base + lane]];
             child_round<R>(m, ws, sm, has, c, rc, lane);
         }
         __syncthreads();
@@ -2057,6 +2072,7 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic_team(const __grid_constan
     extern __shared__ __align__(16) unsigned char dsm[];
     Win<R>* cst = (Win<R>*)(dsm + team_child_off<R>(g.shared));
     VCand<R, false>* vst = (VCand<R, false>*)(dsm + team_vcand_off<R>(g.shared, W));
+    int* ilist = (int*)(dsm + team_idx_off<R>(g.shared, W)) + (size_t)wid * 96 * W;   // this warp's list
     uint32_t gen = 0;
     if (threadIdx.x == 0) {
         ws = ws_bind<R, SH>(g, team);
@@ -2081,7 +2097,7 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic_team(const __grid_constan
             ws.gen = gen;
         }
         __syncthreads();
-        run_source_team<R>(J, src, ws, sm, tm, cst, vst, W, wid, lane, status, counters, item, q.defer_list,
+        run_source_team<R>(J, src, ws, sm, tm, cst, vst, ilist, W, wid, lane, status, counters, item, q.defer_list,
                            q.defer_count);
         __syncthreads();   // the team's state is free before the next claim
     }
