@@ -1143,8 +1143,10 @@ __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& 
 // direction, boundary and non-manifold vertices emit on every corner.
 constexpr float SHADOW_TOL = 1e-3f;
 template <class R, int SH>
-__device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, double rc, double kmin, int lane) {
+__device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, double rc, double kmin, int lane,
+                                       Win<R>* stage = nullptr, int cap = 0, int* nstaged = nullptr) {
     __syncwarp();
+    int staged = 0;   // windows handed to the caller in stage (team form) instead of inserted
     const int ne = min(sm.nemit, ws.emcap);
     if (ne == 0) return 0;
     // the vertices that wait are compacted to the front of the list in place (a write
@@ -1251,12 +1253,23 @@ __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm
                     if constexpr (SH == 2) c.pv = o_vid;
                 }
             }
+            if (stage) {   // the team inserts these together; what does not fit is inserted here
+                const unsigned hm = __ballot_sync(CSS_FULL, hh);
+                if (staged + __popc(hm) <= cap) {
+                    if (hh) stage[staged + __popc(hm & css::lanemask_lt())] = c;
+                    staged += __popc(hm);
+                    continue;
+                }
+            }
             child_round<R>(m, ws, sm, hh, c, rc, lane);
         }
         emitted += __popc(gm);
     }
     __syncwarp();
-    if (lane == 0) sm.nemit = n_wait;   // inserting windows never touches the vertex list
+    if (lane == 0) {
+        sm.nemit = n_wait;   // inserting windows never touches the vertex list
+        if (nstaged) *nstaged = staged;
+    }
     __syncwarp();
     return emitted;
 }
@@ -1810,6 +1823,7 @@ struct TeamSm {
     int item;         // the team's current work item (>= nitems: none left)
     int action;       // next step of the wave loop: 0 finished, 1 look again, 2 unfold nsel windows
     int nsel;
+    int nstaged;      // emitted windows staged for the whole team to insert
     int npair;        // slots taken in the source's pair row
     double fx[MAX_TEAM], fy[MAX_TEAM], en[MAX_TEAM];
     unsigned long long nprop[MAX_TEAM];
@@ -1886,6 +1900,29 @@ __device__ int select_wave_cap(Ws<R, SH>& ws, WarpSm& sm, int npend, float kmin,
 }
 
 // One source processed by the team of the W warps of this CTA (see the team form above).
+// The staged windows cst[0 .. count) (he < 0: an empty slot) inserted by the team: each warp
+// lists those on the edges it owns (undirected edge id modulo W), in order, and inserts them
+// 32 to a round.
+template <class R, int SH>
+__device__ __forceinline__ void team_insert(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, const Win<R>* cst, int count,
+                                            int* ilist, int W, int wid, int lane, double rc) {
+    int nown = 0;
+    for (int base = 0; base < count; base += 32) {
+        const int s = base + lane;
+        const bool own = s < count && cst[s].he >= 0 && m.edge[cst[s].he] % W == wid;
+        const unsigned om = __ballot_sync(CSS_FULL, own);
+        if (own) ilist[nown + __popc(om & css::lanemask_lt())] = s;
+        nown += __popc(om);
+    }
+    __syncwarp();
+    for (int base = 0; base < nown; base += 32) {
+        Win<R> c;
+        const bool has = base + lane < nown;
+        if (has) c = cst[ilist[base + lane]];
+        child_round<R>(m, ws, sm, has, c, rc, lane);
+    }
+}
+
 template <class R, int SH>
 __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, TeamSm& tm, Win<R>* cst,
                                 VCand<R, false>* vst, int* ilist, int W, int wid, int lane, int* status,
@@ -1916,7 +1953,9 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
             } else {
                 float kmin, kmax;
                 pending_range<R>(ws, npend, lane, kmin, kmax);
-                if (sm.nemit > 0 && emit_round<R>(m, ws, sm, rc, npend ? (double)kmin : INFINITY, lane) > 0) act = 1;
+                if (sm.nemit > 0 &&
+                    emit_round<R>(m, ws, sm, rc, npend ? (double)kmin : INFINITY, lane, cst, 64 * W, &tm.nstaged) > 0)
+                    act = tm.nstaged > 0 ? 3 : 1;
                 else if (npend == 0) act = 1;
                 else {
                     const int taken = select_wave_cap<R>(ws, sm, npend, kmin, kmax, lane, 32 * W, tm.sel);
@@ -1928,9 +1967,15 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
         __syncthreads();
         const int act = tm.action;
         const int nsel = tm.nsel;
+        const int nstaged = tm.nstaged;
         __syncthreads();   // everyone has read the decision before warp 0 writes the next one
         if (act == 0) break;
         if (act == 1) continue;
+        if (act == 3) {   // the emitted windows warp 0 staged, inserted by their edges' owners
+            team_insert<R>(m, ws, sm, cst, nstaged, ilist, W, wid, lane, rc);
+            __syncthreads();
+            continue;
+        }
         // every warp unfolds its 32 windows and stages what they produce
         const int k = wid * 32 + lane;
         Win<R> w;
@@ -1978,21 +2023,7 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
         }
         __syncthreads();
         // and the staged children on the edges it owns (undirected edge id modulo W)
-        nown = 0;
-        for (int base = 0; base < 2 * nsel; base += 32) {
-            const int s = base + lane;
-            const bool own = s < 2 * nsel && cst[s].he >= 0 && m.edge[cst[s].he] % W == wid;
-            const unsigned om = __ballot_sync(CSS_FULL, own);
-            if (own) ilist[nown + __popc(om & css::lanemask_lt())] = s;
-            nown += __popc(om);
-        }
-        __syncwarp();
-        for (int base = 0; base < nown; base += 32) {
-            Win<R> c;
-            const bool has = base + lane < nown;
-            if (has) c = cst[ilist[base + lane]];
-            child_round<R>(m, ws, sm, has, c, rc, lane);
-        }
+        team_insert<R>(m, ws, sm, cst, 2 * nsel, ilist, W, wid, lane, rc);
         __syncthreads();
     }
     const int err = sm.err;
