@@ -52,9 +52,9 @@ DEFAULT_WORKLOAD = "noisy_ico8_n65536"
 # sources it was taken on; a kernel changed since then reports null
 TRAFFIC = {
     # k_geodesic<float, 2, 0> (128-register variant, global tables, 8 warps per CTA, pool of 32768
-    # windows) over 8192 of the 65536 sources on the same noisy L8 sphere: 4.946 GB read +
-    # 1.990 GB written in 10.5 ms (profiles/k_geodesic_fp32_noisy_ico8.md)
-    "noisy_ico8_n65536": {"bytes": 4945834240 + 1990208512, "sources": 8192, "kernel": "3263806b2359d68f"},
+    # windows) over 8192 of the 65536 sources on the same noisy L8 sphere: 4.955 GB read +
+    # 1.994 GB written in 10.4 ms (profiles/k_geodesic_fp32_noisy_ico8.md)
+    "noisy_ico8_n65536": {"bytes": 4955052032 + 1994200576, "sources": 8192, "kernel": "e1ba5cd1320c9ac4"},
 }
 KERNEL_SOURCES = ("paper_2404_19751_gb300/csrc/geodesic.cu", "paper_2404_19751_gb300/csrc/css_dev.cuh",
                   "paper_2404_19751_gb300/csrc/css_internal.h")

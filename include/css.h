@@ -365,8 +365,9 @@ int css_get_launch(const css_ctx* ctx, css_launch* launch);
  * and at 4096 slots), and four times that pool where more than 1 % of the sources were
  * deferred, then occupancy 2 with 4 or 8 warps per CTA (global tables with pools of 8192
  * and 32768 windows, tables tied or at 4096 slots, and the best pick's tables), then, when the
- * sources sampled are fewer than four times 8 warps per SM, the team form (shared or global
- * tables x 2, 4, 8 warps per CTA x occupancy 1, 2), then the tile on the best (not for a
+ * sources sampled are fewer than four times 8 warps per SM, the team form (shared tables at
+ * scale 1 or 4 or global tables x 2, 4, 8 warps per CTA x occupancy 1, 2, pools grown four and
+ * sixteen times while sources are deferred), then the tile on the best (not for a
  * team) -- and keeps the fastest in the context.  Each candidate runs `reps` times (>= 1) after one
  * untimed run; `sample` > 0 restricts every run to about that many sources spread over
  * the sets (0: all).  best (may be NULL) receives the chosen shape and best_ms its

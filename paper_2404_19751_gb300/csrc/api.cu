@@ -1193,7 +1193,7 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
     // the team form (all warps of a CTA on one source) where the sampled sources are too few to
     // fill the resident warps one warp each
     if (rc == CSS_OK && (int64_t)nitems < 4 * (int64_t)c->sm_count * 8) {
-        for (int s : {1, 0}) {
+        for (int s : {1, 4, 0}) {
             for (int wpc : {2, 4, 8}) {
                 for (int occ : {1, 2}) {
                     if (cssi::geodesic_team_blocks_per_sm(precision, wpc, s, occ) < 1) continue;
@@ -1210,6 +1210,16 @@ int css_autotune(css_ctx* c, css_parts* const* sets, int32_t n_sets, const css_p
                     rc = measure(L, &t);
                     if (rc) break;
                     if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
+                    // a team's wider waves unfold more windows: sources deferred for want of
+                    // pool run twice, so try pools four and sixteen times larger
+                    for (int grow = 0; grow < 2 && c->last_counters[4] * 100 > nitems && L.win_cap * 4 <= (1 << 20);
+                         ++grow) {
+                        L.win_cap *= 4;
+                        rc = measure(L, &t);
+                        if (rc) break;
+                        if (t < pick_ms) { pick_ms = t; pick = c->cfg; }
+                    }
+                    if (rc) break;
                 }
                 if (rc) break;
             }
