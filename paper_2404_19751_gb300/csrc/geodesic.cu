@@ -1550,6 +1550,74 @@ __device__ __forceinline__ void seed_source(const DMesh& m, Ws<R, SH>& ws, WarpS
     }
 }
 
+// One chunk of targets (one warp): lane l evaluates particle j in face fl if has: its distance
+// and tangent at the source, its pair row entry (slots(ballot of pairs) gives where this
+// chunk's pairs start in the row) and its force and energy terms.
+template <class R, int SH, class Slots>
+__device__ __forceinline__ void eval_targets(const cssi::GeoJob& J, int i, const Ws<R, SH>& ws, int f0, R qx, R qy,
+                                             bool has, int o_fl, int j, int lane, int item, Slots slots, double& fx,
+                                             double& fy, double& en) {
+    const DMesh& m = J.m;
+    const double rc = J.rc;
+    const bool wp = J.want_pairs != 0;
+    bool ispair = false;
+    double d = 0.0;
+    R tx = (R)0, ty = (R)0;
+    VLink<SH == 2> ql;
+    if (has) {
+        d = query<R>(m, ws, f0, qx, qy, o_fl, J.bary + 3 * (size_t)j, tx, ty, &ql);
+        ispair = d < rc;
+    }
+    const unsigned pm = __ballot_sync(CSS_FULL, ispair);
+    const int pbase = slots(pm);   // the row slots of this chunk's pairs start here
+    if constexpr (SH == 2) {
+        // the pair's legs, from the target back to the source: its own link, then the
+        // link of each vertex on the way (still in this source's table)
+        const int pos = pbase + __popc(pm & css::lanemask_lt());
+        if (ispair && pos < J.pair_cap) {
+            const size_t o = (size_t)item * J.pair_cap + pos;
+            int nl = 0;
+            VLink<true> l = ql;
+            for (;;) {
+                if (nl >= J.lmax) { nl = -1; break; }
+                const size_t a = o * J.lmax + nl;
+                J.lfk[a] = l.fk;
+                J.ldir[2 * a] = l.dx;
+                J.ldir[2 * a + 1] = l.dy;
+                J.llen[a] = l.len;
+                ++nl;
+                if (l.par < 0) break;
+                const int slot = ws_vfind<R>(ws, l.par);
+                if (slot < 0) { nl = -2; break; }
+                l.par = ws.lpar[slot];
+                l.fk = ws.lfk[slot];
+                l.dx = ws.ldir[2 * slot];
+                l.dy = ws.ldir[2 * slot + 1];
+                l.len = ws.llen[slot];
+            }
+            J.lnum[o] = nl;
+        }
+    }
+    if (wp && ispair) {
+        const int pos = pbase + __popc(pm & css::lanemask_lt());
+        if (pos < J.pair_cap) {
+            const size_t o = (size_t)i * J.pair_cap + pos;
+            J.pj[o] = j;
+            J.pd[o] = d;
+            const double* fr = m.frame + 9 * (size_t)f0;
+            J.pt[3 * o] = (double)tx * fr[3] + (double)ty * fr[6];
+            J.pt[3 * o + 1] = (double)tx * fr[4] + (double)ty * fr[7];
+            J.pt[3 * o + 2] = (double)tx * fr[5] + (double)ty * fr[8];
+        }
+    }
+    if (ispair && J.want_forces) {
+        const double du = pot_dudl(J.pot, d);
+        fx += du * (double)tx;
+        fy += du * (double)ty;
+        en += 0.5 * pot_u(J.pot, d);
+    }
+}
+
 // The targets in the faces flist[fb .. fb + 32) (one warp): each particle's distance and
 // tangent at the source, its pair row entry (slots(ballot of pairs) gives where this chunk's
 // pairs start in the row) and its force and energy terms.
@@ -1558,8 +1626,6 @@ __device__ __forceinline__ void eval_face_block(const cssi::GeoJob& J, int i, co
                                                 int fb, int nface, int lane, int item, Slots slots, double& fx,
                                                 double& fy, double& en) {
     const DMesh& m = J.m;
-    const double rc = J.rc;
-    const bool wp = J.want_pairs != 0;
     const int fi = fb + lane;
     int fl = -1, st = 0, cnt = 0;
     if (fi < nface) {
@@ -1585,66 +1651,9 @@ __device__ __forceinline__ void eval_face_block(const cssi::GeoJob& J, int i, co
         const int o_fl = __shfl_sync(CSS_FULL, fl, owner);
         const int o_st = __shfl_sync(CSS_FULL, st, owner);
         const int o_ex = __shfl_sync(CSS_FULL, incl - cnt, owner);
-        bool ispair = false;
-        double d = 0.0;
-        R tx = (R)0, ty = (R)0;
         int j = -1;
-        VLink<SH == 2> ql;
-        if (t < total) {
-            j = J.fitems[o_st + (t - o_ex)];
-            if (j != i) {
-                d = query<R>(m, ws, f0, qx, qy, o_fl, J.bary + 3 * (size_t)j, tx, ty, &ql);
-                ispair = d < rc;
-            }
-        }
-        const unsigned pm = __ballot_sync(CSS_FULL, ispair);
-        const int pbase = slots(pm);   // the row slots of this chunk's pairs start here
-        if constexpr (SH == 2) {
-            // the pair's legs, from the target back to the source: its own link, then the
-            // link of each vertex on the way (still in this source's table)
-            const int pos = pbase + __popc(pm & css::lanemask_lt());
-            if (ispair && pos < J.pair_cap) {
-                const size_t o = (size_t)item * J.pair_cap + pos;
-                int nl = 0;
-                VLink<true> l = ql;
-                for (;;) {
-                    if (nl >= J.lmax) { nl = -1; break; }
-                    const size_t a = o * J.lmax + nl;
-                    J.lfk[a] = l.fk;
-                    J.ldir[2 * a] = l.dx;
-                    J.ldir[2 * a + 1] = l.dy;
-                    J.llen[a] = l.len;
-                    ++nl;
-                    if (l.par < 0) break;
-                    const int slot = ws_vfind<R>(ws, l.par);
-                    if (slot < 0) { nl = -2; break; }
-                    l.par = ws.lpar[slot];
-                    l.fk = ws.lfk[slot];
-                    l.dx = ws.ldir[2 * slot];
-                    l.dy = ws.ldir[2 * slot + 1];
-                    l.len = ws.llen[slot];
-                }
-                J.lnum[o] = nl;
-            }
-        }
-        if (wp && ispair) {
-            const int pos = pbase + __popc(pm & css::lanemask_lt());
-            if (pos < J.pair_cap) {
-                const size_t o = (size_t)i * J.pair_cap + pos;
-                J.pj[o] = j;
-                J.pd[o] = d;
-                const double* fr = m.frame + 9 * (size_t)f0;
-                J.pt[3 * o] = (double)tx * fr[3] + (double)ty * fr[6];
-                J.pt[3 * o + 1] = (double)tx * fr[4] + (double)ty * fr[7];
-                J.pt[3 * o + 2] = (double)tx * fr[5] + (double)ty * fr[8];
-            }
-        }
-        if (ispair && J.want_forces) {
-            const double du = pot_dudl(J.pot, d);
-            fx += du * (double)tx;
-            fy += du * (double)ty;
-            en += 0.5 * pot_u(J.pot, d);
-        }
+        if (t < total) j = J.fitems[o_st + (t - o_ex)];
+        eval_targets<R>(J, i, ws, f0, qx, qy, t < total && j != i, o_fl, j, lane, item, slots, fx, fy, en);
     }
 }
 
@@ -1671,11 +1680,12 @@ __device__ __forceinline__ int scan_owner(int incl, int t) {
 
 // Per-warp staging (shared memory) of a wave's vertex candidates and then of its children,
 // so that each round takes 32 of them whatever lane produced them; the two phases use the
-// buffer in turn.
+// buffer in turn, and after the waves it holds the source's targets.
 template <class R>
 union WaveStage {
     VCand<R, false> vc[3][32];
     Win<R> ch[2][32];
+    int2 tq[2 * 32 * sizeof(Win<R>) / sizeof(int2)];   // (face, particle) targets, after the waves
 };
 
 template <class R, int SH>
@@ -1780,9 +1790,65 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
     double fx = 0.0, fy = 0.0, en = 0.0;
     int npair = 0;
     const bool wp = J.want_pairs != 0;
-    for (int fb = 0; fb < nface; fb += 32)
-        eval_face_block<R>(J, i, ws, f0, qx, qy, fb, nface, lane, item,
-                           [&](unsigned pm) { const int b = npair; npair += __popc(pm); return b; }, fx, fy, en);
+    auto slots = [&](unsigned pm) { const int b = npair; npair += __popc(pm); return b; };
+    if constexpr (SH == 2) {
+        for (int fb = 0; fb < nface; fb += 32)
+            eval_face_block<R>(J, i, ws, f0, qx, qy, fb, nface, lane, item, slots, fx, fy, en);
+    } else {
+        // the targets of all the faces are gathered in the stage first and then evaluated 32 at a
+        // time (a block of 32 faces holds only a few particles on the sparse workloads)
+        constexpr int TQ = (int)(sizeof(WaveStage<R>::tq) / sizeof(int2));
+        int2* tq = stg->tq;
+        int nt = 0;
+        // one loop, one evaluation site (instruction footprint): each turn either reads the
+        // next block of 32 faces, queues up to 32 of its targets, or evaluates the queue (when
+        // it could not take another 32, or at the end)
+        int fb = 0, tb = 0, total = 0, incl = 0, fl = -1, st = 0, cnt = 0;
+#pragma unroll 1
+        for (;;) {
+            if (fb < nface && tb >= total) {   // the next block's buckets
+                const int fi = fb + lane;
+                fl = -1; st = 0; cnt = 0;
+                if (fi < nface) {
+                    fl = ws.flist[fi];
+                    const int key = m.frank ? m.frank[fl] : fl;
+                    st = J.fstart[key];
+                    cnt = J.fstart[key + 1] - st;
+                }
+                incl = warp_incl_scan(cnt, lane);
+                total = __shfl_sync(CSS_FULL, incl, 31);
+                tb = 0;
+                if (total == 0) { fb += 32; continue; }
+            }
+            const bool done = fb >= nface;
+            if (done || nt + 32 > TQ) {
+                __syncwarp();
+#pragma unroll 1
+                for (int base = 0; base < nt; base += 32) {
+                    const bool has = base + lane < nt;
+                    const int2 e = has ? tq[base + lane] : make_int2(-1, -1);
+                    eval_targets<R>(J, i, ws, f0, qx, qy, has, e.x, e.y, lane, item, slots, fx, fy, en);
+                }
+                __syncwarp();
+                nt = 0;
+                if (done) break;
+                continue;
+            }
+            const int t = tb + lane;
+            const int owner = scan_owner(incl, t);
+            const int o_fl = __shfl_sync(CSS_FULL, fl, owner);
+            const int o_st = __shfl_sync(CSS_FULL, st, owner);
+            const int o_ex = __shfl_sync(CSS_FULL, incl - cnt, owner);
+            int j = -1;
+            if (t < total) j = J.fitems[o_st + (t - o_ex)];
+            const bool valid = t < total && j != i;
+            const unsigned vm = __ballot_sync(CSS_FULL, valid);
+            if (valid) tq[nt + __popc(vm & css::lanemask_lt())] = make_int2(o_fl, j);
+            nt += __popc(vm);
+            tb += 32;
+            if (tb >= total) fb += 32;
+        }
+    }
     fx = css::warp_sum(fx);
     fy = css::warp_sum(fy);
     en = css::warp_sum(en);
