@@ -108,6 +108,7 @@ struct Tie<float> {
 
 struct WarpSm {
     int nwin, npend, nface, nemit, err;
+    unsigned emin;    // a lower bound on the distances of the queued emitting vertices (FP32 bits)
     int sel[32];      // window ids picked for the current wave
 };
 
@@ -1096,6 +1097,7 @@ __device__ __noinline__ void vertex_round(const DMesh& m, Ws<R, SH>& ws, WarpSm&
                     ws.ldir[2 * slot + 1] = c.dy;
                     ws.llen[slot] = c.len;
                 }
+                if (d < vd && d < rc) atomicMin(&sm.emin, __float_as_uint(__double2float_rd(d)));
                 if (d < vd && d < rc && !(ws.vflag[slot] & 1)) {
                     ws.vflag[slot] |= 1;
                     const int p = atomicAdd(&sm.nemit, 1);
@@ -1153,13 +1155,16 @@ __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm
     // never lands behind the entries still to be read)
     int n_wait = 0;
     int emitted = 0;
+    float wmin = INFINITY;   // smallest distance among the vertices left waiting
     for (int base = 0; base < ne; base += 32) {
         const int it = base + lane;
         int vs = -1;
         bool go = false;
         if (it < ne) {
             vs = ws.emit[it];
-            go = ws.vdist[vs] <= kmin;
+            const double dv0 = ws.vdist[vs];
+            go = dv0 <= kmin;
+            if (!go) wmin = fminf(wmin, __double2float_rd(dv0));
         }
         __syncwarp();
         const unsigned gm = __ballot_sync(CSS_FULL, go);
@@ -1266,8 +1271,11 @@ __device__ __noinline__ int emit_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm
         emitted += __popc(gm);
     }
     __syncwarp();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wmin = fminf(wmin, __shfl_xor_sync(CSS_FULL, wmin, o));
     if (lane == 0) {
         sm.nemit = n_wait;   // inserting windows never touches the vertex list
+        sm.emin = __float_as_uint(wmin);
         if (nstaged) *nstaged = staged;
     }
     __syncwarp();
@@ -1488,7 +1496,7 @@ template <class R, int SH>
 __device__ __forceinline__ void seed_source(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int f0, double qxd, double qyd,
                                             double rc, int lane) {
     ws_clear_shared<R>(ws, lane);
-    if (lane == 0) { sm.nwin = 0; sm.npend = 0; sm.nface = 0; sm.nemit = 0; sm.err = 0; }
+    if (lane == 0) { sm.nwin = 0; sm.npend = 0; sm.nface = 0; sm.nemit = 0; sm.err = 0; sm.emin = 0x7f800000u; }
     __syncwarp();
     if (lane == 0) face_add(ws, sm, f0);
     {   // the source's own pseudo-source corners
@@ -1708,9 +1716,12 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
         if (wave > max_waves) { if (lane == 0) atomicOr(&sm.err, css::ST_ITER_LIMIT); break; }
         float kmin, kmax;
         pending_range<R>(ws, npend, lane, kmin, kmax);
-        // vertices whose distance no queued window can improve emit first; their windows
-        // join the queue and the smallest keys are looked at again
-        if (sm.nemit > 0 && emit_round<R>(m, ws, sm, rc, npend ? (double)kmin : INFINITY, lane) > 0) continue;
+        // vertices whose distance no queued window can improve emit first (none can while the
+        // smallest queued distance bound exceeds kmin); their windows join the queue and the
+        // smallest keys are looked at again
+        if (sm.nemit > 0 && (!npend || __uint_as_float(sm.emin) <= kmin) &&
+            emit_round<R>(m, ws, sm, rc, npend ? (double)kmin : INFINITY, lane) > 0)
+            continue;
         if (npend == 0) continue;
         const int idx = select_wave<R>(ws, sm, npend, kmin, kmax, lane);
         Win<R> w;
@@ -2019,7 +2030,7 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
             } else {
                 float kmin, kmax;
                 pending_range<R>(ws, npend, lane, kmin, kmax);
-                if (sm.nemit > 0 &&
+                if (sm.nemit > 0 && (!npend || __uint_as_float(sm.emin) <= kmin) &&
                     emit_round<R>(m, ws, sm, rc, npend ? (double)kmin : INFINITY, lane, cst, 64 * W, &tm.nstaged) > 0)
                     act = tm.nstaged > 0 ? 3 : 1;
                 else if (npend == 0) act = 1;
