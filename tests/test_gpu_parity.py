@@ -6,7 +6,8 @@ import pytest
 
 import synth
 from oracle import oracle as O
-from tests._common import FP32_REL_DIAM, FP64_RTOL, compare_pairs, descent_checker, force_row_bounds
+from tests._common import (FP32_REL_DIAM, FP64_RTOL, compare_pairs, descent_checker, force_row_bounds,
+                           sample_sources, select_rows)
 
 css = pytest.importorskip("paper_2404_19751_gb300")
 pytestmark = pytest.mark.gpu
@@ -102,6 +103,39 @@ TINY = [
     ("tube6x3", lambda: synth.cylinder_tube(6, 3, 1.0, 2.0)),
     ("plane4_alt", lambda: synth.grid_plane(4, 4, alternate=True)),
 ]
+
+
+def test_dense_all_pairs_target_queue(ctx):
+    """700 particles, all pairs: each source has 699 targets, more than one warp's target queue
+    holds (512 entries in the FP32 form, 576 in the FP64 form), so its evaluation flushes the
+    queue more than once; one warp per source and a team of 4, both forms, against the oracle
+    on sampled rows, every row complete."""
+    m = synth.icosphere(2, 1.0, noise=0.05, seed=7)
+    n = 700
+    face, bary = synth.place_uniform(m, n, 21)
+    mesh, parts = _setup(ctx, m, face, bary)
+    src = sample_sources(n, 16, 5)
+    om = O.OracleMesh(m)
+    r = om.neighbors_gap(face, bary, math.inf, sources=src)
+    t32 = FP32_REL_DIAM * synth.bbox_diagonal(m)
+    walker = descent_checker(om, face, bary, math.inf)
+    before = ctx.get_launch()
+    try:
+        for shape in (dict(), dict(team=1, warps_per_cta=4)):
+            ctx.set_launch(**dict(before, **shape))
+            for prec in (css.FP64, css.FP32):
+                g = css.geodesic_neighbors(parts, math.inf, prec)
+                assert np.all(np.diff(g[0]) == n - 1)
+                gs = select_rows(g, src)
+                if prec == css.FP64:
+                    compare_pairs(gs, r, math.inf, FP64_RTOL, 1e-7)
+                else:
+                    compare_pairs(gs, r, math.inf, t32, 1e-5, rel=False, tie=t32,
+                                  walker=lambda i, j, d, t: walker(int(src[i]), j, d, t), land_tol=1e-7)
+    finally:
+        ctx.set_launch(**before)
+    parts.free()
+    mesh.free()
 
 
 @pytest.mark.parametrize("name,make", TINY, ids=[t[0] for t in TINY])
