@@ -109,6 +109,8 @@ struct Tie<float> {
 struct WarpSm {
     int nwin, npend, nface, nemit, err;
     unsigned emin;    // a lower bound on the distances of the queued emitting vertices (FP32 bits)
+    int ncar;         // children held over to the next wave's insertion rounds
+    unsigned cmin;    // a lower bound on their keys (FP32 bits)
     int sel[32];      // window ids picked for the current wave
 };
 
@@ -1110,9 +1112,14 @@ __device__ __noinline__ void vertex_round(const DMesh& m, Ws<R, SH>& ws, WarpSm&
     }
 }
 
+// Children on one edge go in one at a time.  With a carry buffer (room for 32), the second
+// and later ones on an edge wait there for the next wave's rounds instead of taking rounds
+// of their own now (most of such a round's lanes would idle); their smallest key joins the
+// bound below which vertices may emit, since their candidates are at least that key.
+constexpr int CARRY_CAP = 32;
 template <class R, int SH>
 __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, bool has, const Win<R>& c, double rc,
-                                         int lane) {
+                                         int lane, Win<R>* carry = nullptr) {
     if (!__any_sync(CSS_FULL, has)) return;
     bool claimed = false;
     int slot = -1;
@@ -1123,7 +1130,21 @@ __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& 
     if (claimed) ws.ehead[slot] = -1;
     __syncwarp();
     int rank;
-    const int rounds = group_rounds(has, slot, lane, rank);
+    int rounds = group_rounds(has, slot, lane, rank);
+    if (carry && rounds > 1) {
+        const unsigned later = __ballot_sync(CSS_FULL, has && rank > 0);
+        const int n0 = sm.ncar;
+        if (n0 + __popc(later) <= CARRY_CAP) {
+            if (has && rank > 0) {
+                carry[n0 + __popc(later & css::lanemask_lt())] = c;
+                atomicMin(&sm.cmin, __float_as_uint(__double2float_rd((double)win_key<R>(c))));
+                has = false;
+            }
+            __syncwarp();
+            if (lane == 0) sm.ncar = n0 + __popc(later);
+            rounds = 1;
+        }
+    }
     for (int q = 0; q < rounds; ++q) {
         insert_round<R>(m, ws, sm, has && rank == q, slot, c, rc, lane);
         __syncwarp();
@@ -1496,7 +1517,7 @@ template <class R, int SH>
 __device__ __forceinline__ void seed_source(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, int f0, double qxd, double qyd,
                                             double rc, int lane) {
     ws_clear_shared<R>(ws, lane);
-    if (lane == 0) { sm.nwin = 0; sm.npend = 0; sm.nface = 0; sm.nemit = 0; sm.err = 0; sm.emin = 0x7f800000u; }
+    if (lane == 0) { sm.nwin = 0; sm.npend = 0; sm.nface = 0; sm.nemit = 0; sm.err = 0; sm.emin = 0x7f800000u; sm.ncar = 0; sm.cmin = 0x7f800000u; }
     __syncwarp();
     if (lane == 0) face_add(ws, sm, f0);
     {   // the source's own pseudo-source corners
@@ -1688,12 +1709,16 @@ __device__ __forceinline__ int scan_owner(int incl, int t) {
 
 // Per-warp staging (shared memory) of a wave's vertex candidates and then of its children,
 // so that each round takes 32 of them whatever lane produced them; the two phases use the
-// buffer in turn, and after the waves it holds the source's targets.
+// union in turn, and after the waves it holds the source's targets.  The children held over
+// from one wave to the next sit beside it.
 template <class R>
-union WaveStage {
-    VCand<R, false> vc[3][32];
-    Win<R> ch[2][32];
-    int2 tq[2 * 32 * sizeof(Win<R>) / sizeof(int2)];   // (face, particle) targets, after the waves
+struct WaveStage {
+    union {
+        VCand<R, false> vc[3][32];
+        Win<R> ch[2][32];
+        int2 tq[2 * 32 * sizeof(Win<R>) / sizeof(int2)];   // (face, particle) targets, after the waves
+    };
+    Win<R> carry[CARRY_CAP];
 };
 
 template <class R, int SH>
@@ -1712,18 +1737,22 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
     for (int wave = 0;; ++wave) {
         __syncwarp();
         const int npend = min(sm.npend, ws.wcap);
-        if ((npend == 0 && sm.nemit == 0) || sm.err) break;
+        const int ncar = SH == 2 ? 0 : sm.ncar;
+        if ((npend == 0 && sm.nemit == 0 && ncar == 0) || sm.err) break;
         if (wave > max_waves) { if (lane == 0) atomicOr(&sm.err, css::ST_ITER_LIMIT); break; }
         float kmin, kmax;
         pending_range<R>(ws, npend, lane, kmin, kmax);
-        // vertices whose distance no queued window can improve emit first (none can while the
-        // smallest queued distance bound exceeds kmin); their windows join the queue and the
-        // smallest keys are looked at again
-        if (sm.nemit > 0 && (!npend || __uint_as_float(sm.emin) <= kmin) &&
-            emit_round<R>(m, ws, sm, rc, npend ? (double)kmin : INFINITY, lane) > 0)
+        // vertices whose distance no queued or held-over window can improve emit first (none
+        // can while the smallest queued distance bound exceeds the smallest key); their windows
+        // join the queue and the smallest keys are looked at again
+        float kemit = npend ? kmin : INFINITY;
+        if (ncar) kemit = fminf(kemit, __uint_as_float(sm.cmin));
+        if (sm.nemit > 0 && ((!npend && !ncar) || __uint_as_float(sm.emin) <= kemit) &&
+            emit_round<R>(m, ws, sm, rc, (double)kemit, lane) > 0)
             continue;
-        if (npend == 0) continue;
-        const int idx = select_wave<R>(ws, sm, npend, kmin, kmax, lane);
+        if (npend == 0 && ncar == 0) continue;
+        // with nothing queued the held-over children go in now, whatever their edges
+        const int idx = npend ? select_wave<R>(ws, sm, npend, kmin, kmax, lane) : -1;
         Win<R> w;
         bool act = false;
         if (idx >= 0) {
@@ -1764,22 +1793,29 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
                 vertex_round<R>(m, ws, sm, has, c, rc, lane);
             }
             __syncwarp();
-            // then its children (up to two a lane), 32 to a round
+            // then the children held over from the last wave and its own (up to two a lane), 32
+            // to a round; the held-over ones all fall in the first round
 #pragma unroll
             for (int q = 0; q < 2; ++q)
                 if (q < nch) stg->ch[q][lane] = ch[q];
             __syncwarp();
             const int ci = warp_incl_scan(nch, lane);
-            const int ct = __shfl_sync(CSS_FULL, ci, 31);
+            const int ct = __shfl_sync(CSS_FULL, ci, 31) + ncar;
 #pragma unroll 1
             for (int base = 0; base < ct; base += 32) {
                 const int t = base + lane;
-                const int owner = scan_owner(ci, t);
-                const int slot = t - (__shfl_sync(CSS_FULL, ci, owner) - __shfl_sync(CSS_FULL, nch, owner));
+                const int owner = scan_owner(ci, t - ncar);
+                const int slot = t - ncar - (__shfl_sync(CSS_FULL, ci, owner) - __shfl_sync(CSS_FULL, nch, owner));
                 Win<R> c;
                 const bool has = t < ct;
-                if (has) c = stg->ch[slot][owner];
-                child_round<R>(m, ws, sm, has, c, rc, lane);
+                if (t < ncar) c = stg->carry[t];
+                else if (has) c = stg->ch[slot][owner];
+                if (base == 0 && ncar) {
+                    __syncwarp();
+                    if (lane == 0) { sm.ncar = 0; sm.cmin = 0x7f800000u; }
+                    __syncwarp();
+                }
+                child_round<R>(m, ws, sm, has, c, rc, lane, npend ? stg->carry : nullptr);
             }
             __syncwarp();
         }
