@@ -109,8 +109,9 @@ struct Tie<float> {
 struct WarpSm {
     int nwin, npend, nface, nemit, err;
     unsigned emin;    // a lower bound on the distances of the queued emitting vertices (FP32 bits)
-    int ncar;         // children held over to the next wave's insertion rounds
+    int ncar;         // windows held over to the next wave's insertion rounds
     unsigned cmin;    // a lower bound on their keys (FP32 bits)
+    int nstg;         // windows an emission round left in a caller's buffer
     int sel[32];      // window ids picked for the current wave
 };
 
@@ -1743,15 +1744,36 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
         float kmin, kmax;
         pending_range<R>(ws, npend, lane, kmin, kmax);
         // vertices whose distance no queued or held-over window can improve emit first (none
-        // can while the smallest queued distance bound exceeds the smallest key); their windows
-        // join the queue and the smallest keys are looked at again
+        // can while the smallest queued distance bound exceeds the smallest key).  Their
+        // windows join the held-over ones, for this wave's insertion rounds, as far as there is
+        // room; the rest go in at once, and once the queue has changed its smallest keys are
+        // looked at again
         float kemit = npend ? kmin : INFINITY;
         if (ncar) kemit = fminf(kemit, __uint_as_float(sm.cmin));
-        if (sm.nemit > 0 && ((!npend && !ncar) || __uint_as_float(sm.emin) <= kemit) &&
-            emit_round<R>(m, ws, sm, rc, (double)kemit, lane) > 0)
-            continue;
-        if (npend == 0 && ncar == 0) continue;
-        // with nothing queued the held-over children go in now, whatever their edges
+        int ncar2 = ncar;
+        if constexpr (SH != 2) {
+            if (sm.nemit > 0 && ((!npend && !ncar) || __uint_as_float(sm.emin) <= kemit)) {
+                const int npraw = sm.npend;
+                emit_round<R>(m, ws, sm, rc, (double)kemit, lane, stg->carry + ncar, CARRY_CAP - ncar, &sm.nstg);
+                __syncwarp();
+                const int ns = sm.nstg;
+                if (ns > 0) {
+                    const float kk = lane < ns ? __double2float_rd((double)win_key<R>(stg->carry[ncar + lane])) : INFINITY;
+                    const float km = __uint_as_float(__reduce_min_sync(CSS_FULL, __float_as_uint(kk)));
+                    __syncwarp();
+                    if (lane == 0) { sm.ncar = ncar + ns; sm.cmin = min(sm.cmin, __float_as_uint(km)); }
+                    __syncwarp();
+                    ncar2 = ncar + ns;
+                }
+                if (sm.npend != npraw) continue;
+            }
+        } else {
+            if (sm.nemit > 0 && ((!npend && !ncar) || __uint_as_float(sm.emin) <= kemit) &&
+                emit_round<R>(m, ws, sm, rc, (double)kemit, lane) > 0)
+                continue;
+        }
+        if (npend == 0 && ncar2 == 0) continue;
+        // with nothing queued the held-over windows go in now, whatever their edges
         const int idx = npend ? select_wave<R>(ws, sm, npend, kmin, kmax, lane) : -1;
         Win<R> w;
         bool act = false;
@@ -1800,17 +1822,17 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
                 if (q < nch) stg->ch[q][lane] = ch[q];
             __syncwarp();
             const int ci = warp_incl_scan(nch, lane);
-            const int ct = __shfl_sync(CSS_FULL, ci, 31) + ncar;
+            const int ct = __shfl_sync(CSS_FULL, ci, 31) + ncar2;
 #pragma unroll 1
             for (int base = 0; base < ct; base += 32) {
                 const int t = base + lane;
-                const int owner = scan_owner(ci, t - ncar);
-                const int slot = t - ncar - (__shfl_sync(CSS_FULL, ci, owner) - __shfl_sync(CSS_FULL, nch, owner));
+                const int owner = scan_owner(ci, t - ncar2);
+                const int slot = t - ncar2 - (__shfl_sync(CSS_FULL, ci, owner) - __shfl_sync(CSS_FULL, nch, owner));
                 Win<R> c;
                 const bool has = t < ct;
-                if (t < ncar) c = stg->carry[t];
+                if (t < ncar2) c = stg->carry[t];
                 else if (has) c = stg->ch[slot][owner];
-                if (base == 0 && ncar) {
+                if (base == 0 && ncar2) {
                     __syncwarp();
                     if (lane == 0) { sm.ncar = 0; sm.cmin = 0x7f800000u; }
                     __syncwarp();

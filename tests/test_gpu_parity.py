@@ -120,12 +120,15 @@ def test_dense_all_pairs_target_queue(ctx):
     t32 = FP32_REL_DIAM * synth.bbox_diagonal(m)
     walker = descent_checker(om, face, bary, math.inf)
     before = ctx.get_launch()
+    full = []
     try:
         for shape in (dict(), dict(team=1, warps_per_cta=4)):
             ctx.set_launch(**dict(before, **shape))
             for prec in (css.FP64, css.FP32):
                 g = css.geodesic_neighbors(parts, math.inf, prec)
                 assert np.all(np.diff(g[0]) == n - 1)
+                if prec == css.FP64:
+                    full.append(g)
                 gs = select_rows(g, src)
                 if prec == css.FP64:
                     compare_pairs(gs, r, math.inf, FP64_RTOL, 1e-7)
@@ -134,6 +137,34 @@ def test_dense_all_pairs_target_queue(ctx):
                                   walker=lambda i, j, d, t: walker(int(src[i]), j, d, t), land_tol=1e-7)
     finally:
         ctx.set_launch(**before)
+    # every row: the one-warp form (children and emitted windows held over between waves)
+    # against the team form (inserted where they arise)
+    assert np.array_equal(full[0][1], full[1][1])
+    np.testing.assert_allclose(full[0][2], full[1][2], rtol=1e-13, atol=0)
+    parts.free()
+    mesh.free()
+
+
+def test_one_warp_and_team_forms_agree_on_every_row(ctx):
+    """A noisy sphere of 2562 vertices at a cutoff of a quarter of its circumference: wide
+    fronts, many vertices emitting at once (more windows than the held-over buffer takes).
+    The one-warp form against the team form, FP64, every pair and distance."""
+    m = synth.icosphere(4, 1.0, noise=0.03, seed=11)
+    face, bary = synth.place_uniform(m, 3000, 17)
+    mesh, parts = _setup(ctx, m, face, bary)
+    before = ctx.get_launch()
+    out = []
+    try:
+        for shape in (dict(team=0), dict(team=0, occupancy=2, shared_scale=0, window_capacity=8192),
+                      dict(team=1, warps_per_cta=4, shared_scale=0, window_capacity=8192)):
+            ctx.set_launch(**dict(before, **shape))
+            out.append(css.geodesic_neighbors(parts, 0.5 * math.pi, css.FP64))
+            assert ctx.last_counters()["sources"] == len(face)
+    finally:
+        ctx.set_launch(**before)
+    for g in out[1:]:
+        assert np.array_equal(g[0], out[0][0]) and np.array_equal(g[1], out[0][1])
+        np.testing.assert_allclose(g[2], out[0][2], rtol=1e-13, atol=0)
     parts.free()
     mesh.free()
 
