@@ -1113,14 +1113,15 @@ __device__ __noinline__ void vertex_round(const DMesh& m, Ws<R, SH>& ws, WarpSm&
     }
 }
 
-// Children on one edge go in one at a time.  With a carry buffer (room for 32), the second
-// and later ones on an edge wait there for the next wave's rounds instead of taking rounds
-// of their own now (most of such a round's lanes would idle); their smallest key joins the
-// bound below which vertices may emit, since their candidates are at least that key.
+// Children on one edge go in one at a time.  With a carry buffer (room for 32, its fill
+// count at ncar), the second and later ones on an edge wait there for the next wave's rounds
+// instead of taking rounds of their own now (most of such a round's lanes would idle); their
+// smallest key joins the bound below which vertices may emit, since their candidates are at
+// least that key.
 constexpr int CARRY_CAP = 32;
 template <class R, int SH>
 __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, bool has, const Win<R>& c, double rc,
-                                         int lane, Win<R>* carry = nullptr) {
+                                         int lane, Win<R>* carry = nullptr, int* ncar = nullptr) {
     if (!__any_sync(CSS_FULL, has)) return;
     bool claimed = false;
     int slot = -1;
@@ -1134,7 +1135,7 @@ __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& 
     int rounds = group_rounds(has, slot, lane, rank);
     if (carry && rounds > 1) {
         const unsigned later = __ballot_sync(CSS_FULL, has && rank > 0);
-        const int n0 = sm.ncar;
+        const int n0 = *ncar;
         if (n0 + __popc(later) <= CARRY_CAP) {
             if (has && rank > 0) {
                 carry[n0 + __popc(later & css::lanemask_lt())] = c;
@@ -1142,7 +1143,7 @@ __device__ __noinline__ void child_round(const DMesh& m, Ws<R, SH>& ws, WarpSm& 
                 has = false;
             }
             __syncwarp();
-            if (lane == 0) sm.ncar = n0 + __popc(later);
+            if (lane == 0) *ncar = n0 + __popc(later);
             rounds = 1;
         }
     }
@@ -1837,7 +1838,7 @@ __device__ void run_source(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& 
                     if (lane == 0) { sm.ncar = 0; sm.cmin = 0x7f800000u; }
                     __syncwarp();
                 }
-                child_round<R>(m, ws, sm, has, c, rc, lane, npend ? stg->carry : nullptr);
+                child_round<R>(m, ws, sm, has, c, rc, lane, npend ? stg->carry : nullptr, &sm.ncar);
             }
             __syncwarp();
         }
@@ -1956,17 +1957,20 @@ constexpr int MAX_TEAM = 8;
 
 struct TeamSm {
     int item;         // the team's current work item (>= nitems: none left)
-    int action;       // next step of the wave loop: 0 finished, 1 look again, 2 unfold nsel windows
+    int action;       // next step of the wave loop: 0 finished, 1 look again, 2 unfold nsel windows,
+                      // 3 insert the staged emitted windows and the held-over ones
     int nsel;
     int nstaged;      // emitted windows staged for the whole team to insert
     int npair;        // slots taken in the source's pair row
+    int ncar[MAX_TEAM];   // windows each warp holds over to the next wave
     double fx[MAX_TEAM], fy[MAX_TEAM], en[MAX_TEAM];
     unsigned long long nprop[MAX_TEAM];
     int sel[32 * MAX_TEAM];
 };
 
 // shared memory of a team besides the static part: its tables (shared placement), then the
-// staged children (64 per warp) and vertex candidates (96 per warp)
+// staged children (64 per warp), vertex candidates (96 per warp), the warps' owned-index
+// lists and their held-over windows (32 per warp)
 template <class R>
 __host__ __device__ inline size_t team_child_off(int shared_scale) {
     return al16(shared_scale ? sh_bytes_per_warp<R>(shared_scale) : 0);
@@ -1980,8 +1984,12 @@ __host__ __device__ inline size_t team_idx_off(int shared_scale, int W) {
     return team_vcand_off<R>(shared_scale, W) + al16((size_t)96 * W * sizeof(VCand<R, false>));
 }
 template <class R>
+__host__ __device__ inline size_t team_car_off(int shared_scale, int W) {
+    return team_idx_off<R>(shared_scale, W) + al16((size_t)96 * W * W * sizeof(int));
+}
+template <class R>
 __host__ __device__ inline size_t team_smem_bytes(int shared_scale, int W) {
-    return team_idx_off<R>(shared_scale, W) + (size_t)96 * W * W * sizeof(int);
+    return team_car_off<R>(shared_scale, W) + (size_t)CARRY_CAP * W * sizeof(Win<R>);
 }
 
 // The next wave of a team: as select_wave, with up to `cap` windows written to sel[]
@@ -2040,7 +2048,8 @@ __device__ int select_wave_cap(Ws<R, SH>& ws, WarpSm& sm, int npend, float kmin,
 // 32 to a round.
 template <class R, int SH>
 __device__ __forceinline__ void team_insert(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, const Win<R>* cst, int count,
-                                            int* ilist, int W, int wid, int lane, double rc) {
+                                            int* ilist, int W, int wid, int lane, double rc, Win<R>* wcar, int* ncar,
+                                            bool hold) {
     int nown = 0;
     for (int base = 0; base < count; base += 32) {
         const int s = base + lane;
@@ -2050,17 +2059,28 @@ __device__ __forceinline__ void team_insert(const DMesh& m, Ws<R, SH>& ws, WarpS
         nown += __popc(om);
     }
     __syncwarp();
-    for (int base = 0; base < nown; base += 32) {
+    // the windows this warp held over (all of them in the first round), then the staged ones
+    // on its edges; with hold, same-edge windows after the first wait for the next wave
+    const int nc = *ncar;
+    const int total = nc + nown;
+    for (int base = 0; base < total; base += 32) {
+        const int t = base + lane;
         Win<R> c;
-        const bool has = base + lane < nown;
-        if (has) c = cst[ilist[base + lane]];
-        child_round<R>(m, ws, sm, has, c, rc, lane);
+        const bool has = t < total;
+        if (t < nc) c = wcar[t];
+        else if (has) c = cst[ilist[t - nc]];
+        if (base == 0 && nc) {
+            __syncwarp();
+            if (lane == 0) *ncar = 0;
+            __syncwarp();
+        }
+        child_round<R>(m, ws, sm, has, c, rc, lane, hold ? wcar : nullptr, ncar);
     }
 }
 
 template <class R, int SH>
 __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, TeamSm& tm, Win<R>* cst,
-                                VCand<R, false>* vst, int* ilist, int W, int wid, int lane, int* status,
+                                VCand<R, false>* vst, int* ilist, Win<R>* wcar, int W, int wid, int lane, int* status,
                                 unsigned long long* counters, int item, int32_t* defer_list, int* defer_count) {
     const DMesh& m = J.m;
     const double rc = J.rc;
@@ -2072,6 +2092,7 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
         seed_source<R>(m, ws, sm, f0, qxd, qyd, rc, lane);
         if (lane == 0) tm.npair = 0;
     }
+    if (lane == 0) tm.ncar[wid] = 0;
     __syncthreads();
     unsigned long long n_prop = 0;
     const int max_waves = 4 * ws.wcap + 64;
@@ -2081,23 +2102,35 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
             __syncwarp();
             int act = 2;
             const int npend = min(sm.npend, ws.wcap);
-            if ((npend == 0 && sm.nemit == 0) || sm.err) act = 0;
+            int ncar = 0;   // windows the warps hold over
+            for (int w2 = 0; w2 < W; ++w2) ncar += tm.ncar[w2];
+            if ((npend == 0 && sm.nemit == 0 && ncar == 0) || sm.err) act = 0;
             else if (wave > max_waves) {
                 if (lane == 0) atomicOr(&sm.err, css::ST_ITER_LIMIT);
                 act = 0;
             } else {
                 float kmin, kmax;
                 pending_range<R>(ws, npend, lane, kmin, kmax);
-                if (sm.nemit > 0 && (!npend || __uint_as_float(sm.emin) <= kmin) &&
-                    emit_round<R>(m, ws, sm, rc, npend ? (double)kmin : INFINITY, lane, cst, 64 * W, &tm.nstaged) > 0)
+                float kemit = npend ? kmin : INFINITY;   // held-over windows bound it too
+                if (ncar) kemit = fminf(kemit, __uint_as_float(sm.cmin));
+                if (sm.nemit > 0 && ((!npend && !ncar) || __uint_as_float(sm.emin) <= kemit) &&
+                    emit_round<R>(m, ws, sm, rc, (double)kemit, lane, cst, 64 * W, &tm.nstaged) > 0)
                     act = tm.nstaged > 0 ? 3 : 1;
-                else if (npend == 0) act = 1;
-                else {
+                else if (npend == 0) {   // nothing queued: the held-over windows go in now
+                    act = ncar ? 3 : 1;
+                    if (ncar && lane == 0) tm.nstaged = 0;
+                } else {
                     const int taken = select_wave_cap<R>(ws, sm, npend, kmin, kmax, lane, 32 * W, tm.sel);
                     if (lane == 0) tm.nsel = taken;
                 }
             }
-            if (lane == 0) tm.action = act;
+            __syncwarp();
+            if (lane == 0) {
+                tm.action = act;
+                // every held-over window is taken up by this step's insertion; those held over
+                // again set the bound anew
+                if (act >= 2 && ncar) sm.cmin = 0x7f800000u;
+            }
         }
         __syncthreads();
         const int act = tm.action;
@@ -2107,7 +2140,7 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
         if (act == 0) break;
         if (act == 1) continue;
         if (act == 3) {   // the emitted windows warp 0 staged, inserted by their edges' owners
-            team_insert<R>(m, ws, sm, cst, nstaged, ilist, W, wid, lane, rc);
+            team_insert<R>(m, ws, sm, cst, nstaged, ilist, W, wid, lane, rc, wcar, &tm.ncar[wid], false);
             __syncthreads();
             continue;
         }
@@ -2158,7 +2191,7 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
         }
         __syncthreads();
         // and the staged children on the edges it owns (undirected edge id modulo W)
-        team_insert<R>(m, ws, sm, cst, 2 * nsel, ilist, W, wid, lane, rc);
+        team_insert<R>(m, ws, sm, cst, 2 * nsel, ilist, W, wid, lane, rc, wcar, &tm.ncar[wid], true);
         __syncthreads();
     }
     const int err = sm.err;
@@ -2239,6 +2272,7 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic_team(const __grid_constan
     Win<R>* cst = (Win<R>*)(dsm + team_child_off<R>(g.shared));
     VCand<R, false>* vst = (VCand<R, false>*)(dsm + team_vcand_off<R>(g.shared, W));
     int* ilist = (int*)(dsm + team_idx_off<R>(g.shared, W)) + (size_t)wid * 96 * W;   // this warp's list
+    Win<R>* wcar = (Win<R>*)(dsm + team_car_off<R>(g.shared, W)) + (size_t)wid * CARRY_CAP;
     uint32_t gen = 0;
     if (threadIdx.x == 0) {
         ws = ws_bind<R, SH>(g, team);
@@ -2263,8 +2297,8 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic_team(const __grid_constan
             ws.gen = gen;
         }
         __syncthreads();
-        run_source_team<R>(J, src, ws, sm, tm, cst, vst, ilist, W, wid, lane, status, counters, item, q.defer_list,
-                           q.defer_count);
+        run_source_team<R>(J, src, ws, sm, tm, cst, vst, ilist, wcar, W, wid, lane, status, counters, item,
+                           q.defer_list, q.defer_count);
         __syncthreads();   // the team's state is free before the next claim
     }
     if (threadIdx.x == 0) g.gen[team] = gen;
