@@ -52,9 +52,9 @@ DEFAULT_WORKLOAD = "noisy_ico8_n65536"
 # sources it was taken on; a kernel changed since then reports null
 TRAFFIC = {
     # k_geodesic<float, 2, 0> (128-register variant, global tables, 8 warps per CTA, pool of 32768
-    # windows) over 8192 of the 65536 sources on the same noisy L8 sphere: 5.792 GB read +
-    # 2.395 GB written in 8.56 ms (one ncu pass, dram__bytes_read.sum + dram__bytes_write.sum)
-    "noisy_ico8_n65536": {"bytes": 5792143616 + 2395297536, "sources": 8192, "kernel": "55f1a4befa91ed47"},
+    # windows) over 8192 of the 65536 sources on the same noisy L8 sphere: 5.829 GB read +
+    # 2.419 GB written in 8.72 ms (one ncu pass, dram__bytes_read.sum + dram__bytes_write.sum)
+    "noisy_ico8_n65536": {"bytes": 5828550400 + 2418572544, "sources": 8192, "kernel": "0c622ec7855f2012"},
 }
 KERNEL_SOURCES = ("paper_2404_19751_gb300/csrc/geodesic.cu", "paper_2404_19751_gb300/csrc/css_dev.cuh",
                   "paper_2404_19751_gb300/csrc/css_internal.h")

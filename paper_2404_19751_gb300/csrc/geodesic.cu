@@ -1957,10 +1957,11 @@ constexpr int MAX_TEAM = 8;
 
 struct TeamSm {
     int item;         // the team's current work item (>= nitems: none left)
-    int action;       // next step of the wave loop: 0 finished, 1 look again, 2 unfold nsel windows,
-                      // 3 insert the staged emitted windows and the held-over ones
+    int action;       // next step of the wave loop: 0 finished, 1 look again, 2 unfold nsel windows
+                      // (and insert the staged emitted windows with their children), 3 insert
+                      // the staged emitted windows and the held-over ones
     int nsel;
-    int nstaged;      // emitted windows staged for the whole team to insert
+    int nstaged;      // emitted windows staged (in their own area) for the whole team to insert
     int npair;        // slots taken in the source's pair row
     int ncar[MAX_TEAM];   // windows each warp holds over to the next wave
     double fx[MAX_TEAM], fy[MAX_TEAM], en[MAX_TEAM];
@@ -1970,7 +1971,7 @@ struct TeamSm {
 
 // shared memory of a team besides the static part: its tables (shared placement), then the
 // staged children (64 per warp), vertex candidates (96 per warp), the warps' owned-index
-// lists and their held-over windows (32 per warp)
+// lists, their held-over windows (32 per warp) and the staged emitted windows (32 per warp)
 template <class R>
 __host__ __device__ inline size_t team_child_off(int shared_scale) {
     return al16(shared_scale ? sh_bytes_per_warp<R>(shared_scale) : 0);
@@ -1988,8 +1989,12 @@ __host__ __device__ inline size_t team_car_off(int shared_scale, int W) {
     return team_idx_off<R>(shared_scale, W) + al16((size_t)96 * W * W * sizeof(int));
 }
 template <class R>
+__host__ __device__ inline size_t team_emit_off(int shared_scale, int W) {
+    return team_car_off<R>(shared_scale, W) + al16((size_t)CARRY_CAP * W * sizeof(Win<R>));
+}
+template <class R>
 __host__ __device__ inline size_t team_smem_bytes(int shared_scale, int W) {
-    return team_car_off<R>(shared_scale, W) + (size_t)CARRY_CAP * W * sizeof(Win<R>);
+    return team_emit_off<R>(shared_scale, W) + (size_t)32 * W * sizeof(Win<R>);
 }
 
 // The next wave of a team: as select_wave, with up to `cap` windows written to sel[]
@@ -2048,12 +2053,18 @@ __device__ int select_wave_cap(Ws<R, SH>& ws, WarpSm& sm, int npend, float kmin,
 // 32 to a round.
 template <class R, int SH>
 __device__ __forceinline__ void team_insert(const DMesh& m, Ws<R, SH>& ws, WarpSm& sm, const Win<R>* cst, int count,
-                                            int* ilist, int W, int wid, int lane, double rc, Win<R>* wcar, int* ncar,
-                                            bool hold) {
+                                            const Win<R>* est, int count2, int* ilist, int W, int wid, int lane,
+                                            double rc, Win<R>* wcar, int* ncar, bool hold) {
+    // staged entry s: the children cst[0, count), then the emitted windows est[0, count2)
     int nown = 0;
-    for (int base = 0; base < count; base += 32) {
+    const int all = count + count2;
+    for (int base = 0; base < all; base += 32) {
         const int s = base + lane;
-        const bool own = s < count && cst[s].he >= 0 && m.edge[cst[s].he] % W == wid;
+        bool own = false;
+        if (s < all) {
+            const int he = s < count ? cst[s].he : est[s - count].he;
+            own = he >= 0 && m.edge[he] % W == wid;
+        }
         const unsigned om = __ballot_sync(CSS_FULL, own);
         if (own) ilist[nown + __popc(om & css::lanemask_lt())] = s;
         nown += __popc(om);
@@ -2068,7 +2079,10 @@ __device__ __forceinline__ void team_insert(const DMesh& m, Ws<R, SH>& ws, WarpS
         Win<R> c;
         const bool has = t < total;
         if (t < nc) c = wcar[t];
-        else if (has) c = cst[ilist[t - nc]];
+        else if (has) {
+            const int s = ilist[t - nc];
+            c = s < count ? cst[s] : est[s - count];
+        }
         if (base == 0 && nc) {
             __syncwarp();
             if (lane == 0) *ncar = 0;
@@ -2080,7 +2094,8 @@ __device__ __forceinline__ void team_insert(const DMesh& m, Ws<R, SH>& ws, WarpS
 
 template <class R, int SH>
 __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, WarpSm& sm, TeamSm& tm, Win<R>* cst,
-                                VCand<R, false>* vst, int* ilist, Win<R>* wcar, int W, int wid, int lane, int* status,
+                                VCand<R, false>* vst, int* ilist, Win<R>* wcar, Win<R>* est, int W, int wid, int lane,
+                                int* status,
                                 unsigned long long* counters, int item, int32_t* defer_list, int* defer_count) {
     const DMesh& m = J.m;
     const double rc = J.rc;
@@ -2113,13 +2128,21 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
                 pending_range<R>(ws, npend, lane, kmin, kmax);
                 float kemit = npend ? kmin : INFINITY;   // held-over windows bound it too
                 if (ncar) kemit = fminf(kemit, __uint_as_float(sm.cmin));
-                if (sm.nemit > 0 && ((!npend && !ncar) || __uint_as_float(sm.emin) <= kemit) &&
-                    emit_round<R>(m, ws, sm, rc, (double)kemit, lane, cst, 64 * W, &tm.nstaged) > 0)
-                    act = tm.nstaged > 0 ? 3 : 1;
-                else if (npend == 0) {   // nothing queued: the held-over windows go in now
-                    act = ncar ? 3 : 1;
-                    if (ncar && lane == 0) tm.nstaged = 0;
-                } else {
+                // the emitted windows are staged for this step's insertion; those that do not
+                // fit go in at once, and once the queue has changed its smallest keys are
+                // looked at again
+                int nst = 0;
+                bool again = false;
+                if (sm.nemit > 0 && ((!npend && !ncar) || __uint_as_float(sm.emin) <= kemit)) {
+                    const int npraw = sm.npend;
+                    emit_round<R>(m, ws, sm, rc, (double)kemit, lane, est, 32 * W, &tm.nstaged);
+                    __syncwarp();
+                    nst = tm.nstaged;
+                    again = sm.npend != npraw;
+                } else if (lane == 0) tm.nstaged = 0;
+                if (again) act = nst > 0 ? 3 : 1;
+                else if (npend == 0) act = (ncar || nst) ? 3 : 1;   // nothing queued: they go in now
+                else {
                     const int taken = select_wave_cap<R>(ws, sm, npend, kmin, kmax, lane, 32 * W, tm.sel);
                     if (lane == 0) tm.nsel = taken;
                 }
@@ -2140,7 +2163,7 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
         if (act == 0) break;
         if (act == 1) continue;
         if (act == 3) {   // the emitted windows warp 0 staged, inserted by their edges' owners
-            team_insert<R>(m, ws, sm, cst, nstaged, ilist, W, wid, lane, rc, wcar, &tm.ncar[wid], false);
+            team_insert<R>(m, ws, sm, cst, 0, est, nstaged, ilist, W, wid, lane, rc, wcar, &tm.ncar[wid], false);
             __syncthreads();
             continue;
         }
@@ -2191,7 +2214,7 @@ __device__ void run_source_team(const cssi::GeoJob& J, int i, Ws<R, SH>& ws, War
         }
         __syncthreads();
         // and the staged children on the edges it owns (undirected edge id modulo W)
-        team_insert<R>(m, ws, sm, cst, 2 * nsel, ilist, W, wid, lane, rc, wcar, &tm.ncar[wid], true);
+        team_insert<R>(m, ws, sm, cst, 2 * nsel, est, nstaged, ilist, W, wid, lane, rc, wcar, &tm.ncar[wid], true);
         __syncthreads();
     }
     const int err = sm.err;
@@ -2273,6 +2296,7 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic_team(const __grid_constan
     VCand<R, false>* vst = (VCand<R, false>*)(dsm + team_vcand_off<R>(g.shared, W));
     int* ilist = (int*)(dsm + team_idx_off<R>(g.shared, W)) + (size_t)wid * 96 * W;   // this warp's list
     Win<R>* wcar = (Win<R>*)(dsm + team_car_off<R>(g.shared, W)) + (size_t)wid * CARRY_CAP;
+    Win<R>* est = (Win<R>*)(dsm + team_emit_off<R>(g.shared, W));
     uint32_t gen = 0;
     if (threadIdx.x == 0) {
         ws = ws_bind<R, SH>(g, team);
@@ -2297,7 +2321,7 @@ __global__ void __launch_bounds__(256, OCC) k_geodesic_team(const __grid_constan
             ws.gen = gen;
         }
         __syncthreads();
-        run_source_team<R>(J, src, ws, sm, tm, cst, vst, ilist, wcar, W, wid, lane, status, counters, item,
+        run_source_team<R>(J, src, ws, sm, tm, cst, vst, ilist, wcar, est, W, wid, lane, status, counters, item,
                            q.defer_list, q.defer_count);
         __syncthreads();   // the team's state is free before the next claim
     }
